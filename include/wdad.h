@@ -1,0 +1,128 @@
+/*
+ * wdad.h — C ABI of libwdad: wavelet-reduced local anomaly detection on one GPU.
+ *
+ * Method: Zare Baghbidi, Jamshidi, Naghsh Nilchi, Homayouni, "Improvement of
+ * anomaly detection algorithms in hyperspectral images using discrete wavelet
+ * transform", SIPIJ 2(4), 2011.  Every pixel spectrum of an H x W x L cube goes
+ * through a Daubechies DWT along the band axis, only the approximation
+ * coefficients are kept (Sec. 4, Eq. 7/9, Fig. 1), and the local detectors LRX
+ * (Sec. 2.1, Eq. 1), DWRX (Sec. 2.3, Eq. 5) and DWEST (Sec. 2.2, Eq. 2-4) run on
+ * that reduced cube or on the full-band cube.
+ *
+ * Conventions shared by every entry point
+ *   - Cubes are float32, band-interleaved-by-pixel: element (y, x, l) sits at
+ *     ((y * W) + x) * L + l.  Score maps are float32 [H][W] row-major.
+ *   - All array pointers are DEVICE pointers owned by the caller unless the
+ *     comment says host; the library never frees them.  Inputs are read-only.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Compute calls
+ *     are asynchronous on that stream; the caller synchronises before reading
+ *     outputs.  Argument errors are detected on the host before anything is
+ *     enqueued and return synchronously.
+ *   - Every function returns a wdad_status; no C++ exception crosses the ABI.
+ *     wdad_last_error_detail() gives a one-line reason for the last failure on
+ *     a handle.
+ *   - A handle binds one CUDA device and owns a grow-only device workspace and
+ *     plan caches.  Calls on one handle must not run concurrently from several
+ *     host threads; use one handle per thread.
+ */
+#ifndef WDAD_H
+#define WDAD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    WDAD_OK = 0,
+    WDAD_ERR_ARG = 1,         /* invalid argument (checked on the host) */
+    WDAD_ERR_CUDA = 2,        /* a CUDA runtime call or launch failed */
+    WDAD_ERR_NOMEM = 3,       /* device workspace allocation failed */
+    WDAD_ERR_NUMERIC = 4,     /* reported by status readers: non-finite result */
+    WDAD_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+    WDAD_ERR_UNSUPPORTED = 6  /* valid but not implemented shape or mode */
+} wdad_status;
+
+typedef enum { WDAD_LRX = 0, WDAD_DWRX = 1, WDAD_DWEST = 2 } wdad_detector;
+
+typedef enum {
+    WDAD_PREC_FP32 = 0,   /* FP32 statistics and solves */
+    WDAD_PREC_MIXED = 1,  /* full band: BF16 tensor-core Gram, FP32 solve, FP64 re-solve above cond_gate */
+    WDAD_PREC_FP64 = 2    /* full band: FP64 statistics and solves for every pixel */
+} wdad_precision;
+
+/* Detection parameters.  Fill with wdad_default_params() and override. */
+typedef struct {
+    int wavelet_taps;  /* 8 = db4, "Daubechies4" of Sec. 4 (default); 4 = D4 */
+    int level;         /* -1 = smallest J whose approximation length is <= 4 (Sec. 4) */
+    int inner, outer;  /* odd window sides, 1 <= inner < outer <= 63 (Sec. 2.2, Sec. 5.2) */
+    float loading;     /* LRX/DWRX diagonal loading delta = loading * trace(C_o) / dim; default 1e-3 */
+    float cond_gate;   /* MIXED: re-solve in FP64 where the estimated condition number exceeds this; 1e6 */
+    int border;        /* 0 = reflect-101 (default), 1 = NaN where the outer window leaves the image */
+    int dwest_mode;    /* 0 = |sum_k v_k^T m_diff| with each v_k's largest-|.| entry positive (Eq. 4);
+                          1 = ||V_S^T m_diff|| (sign free) */
+    int precision;     /* wdad_precision, used by the full-band path */
+    float dwest_tau;   /* DWEST keeps eigenvalues > dwest_tau * max|lambda|; default 1e-6 */
+} wdad_params;
+
+typedef struct wdad_ctx* wdad_handle;
+
+/* Defaults: taps 8, level -1, windows 3/11, loading 1e-3, cond_gate 1e6, reflect-101,
+ * dwest_mode 0, FP32, dwest_tau 1e-6. */
+void wdad_default_params(wdad_params* p);
+
+/* Create a handle on CUDA device `device`.  Allocates nothing on the device yet. */
+wdad_status wdad_create(wdad_handle* h, int device);
+/* Release the handle and its workspace (synchronises the device first). */
+wdad_status wdad_destroy(wdad_handle h);
+/* Copy the last error text of `h` (NUL-terminated, truncated to len). */
+wdad_status wdad_last_error_detail(wdad_handle h, char* buf, int len);
+
+/* Number of approximation coefficients K for L bands and a level (-1 = auto, Sec. 4):
+ * K = L halved (rounding up) J times.  Returns -1 for invalid input. */
+int wdad_query_K(int L, int taps, int level);
+
+/* A1 — approximation matrix (Sec. 4; Eq. 9 cascaded J times, Fig. 1, details discarded).
+ * cube: [H][W][L] float32; approx: [H][W][K] float32 (caller allocates H*W*K floats);
+ * K_out (host, nullable) receives K.  Periodic extension, odd lengths padded by
+ * repeating the last sample.  L <= 1024 when L % 4 == 0, else L <= 256. */
+wdad_status wdad_dwt_approx(wdad_handle h, const float* cube, int H, int W, int L,
+                            const wdad_params* p, float* approx, int* K_out, void* stream);
+
+/* A2-A6 — one detector on every pixel (Sec. 2, Eq. 1-5).
+ * reduce = 1: DWT-reduced path (A1 into the handle's workspace, then the detector
+ * on K bands — "DWT-LRX/DWRX/DWEST" of Sec. 5.2); reduce = 0: the detector on
+ * the L-band cube as given.  score: [H][W] float32.
+ * flags (nullable): [H][W] uint8 per pixel; bit 0 = re-solved in FP64 (MIXED),
+ * bit 1 = covariance not positive definite (score NaN), bit 2 = outside the
+ * valid region (border = 1). */
+wdad_status wdad_detect(wdad_handle h, const float* cube, int H, int W, int L,
+                        int detector, int reduce, const wdad_params* p,
+                        float* score, uint8_t* flags, void* stream);
+
+/* All three detectors in one pass over the shared window statistics.
+ * scores: [3][H][W] float32 in the order LRX, DWRX, DWEST.  flags as above (OR of the three). */
+wdad_status wdad_detect_all(wdad_handle h, const float* cube, int H, int W, int L,
+                            int reduce, const wdad_params* p,
+                            float* scores, uint8_t* flags, void* stream);
+
+/* A2 — window census computed by the same tile loader and box-sum code as the
+ * reduced detectors, with an integer payload: for every pixel, over the
+ * background annulus and over the inner window (Sec. 2.2 dual window with
+ * reflect-101 borders): count, sum of linear pixel indices, sum of their squares.
+ * out: [H][W][6] int64 (nb, sum_b, sumsq_b, ni, sum_i, sumsq_i); -1 entries
+ * outside the valid region when border = 1.  Exact integer results. */
+wdad_status wdad_window_census(wdad_handle h, int H, int W, const wdad_params* p,
+                               int64_t* out, void* stream);
+
+/* A10 — pixel-level ROC AUC of a score map against a truth mask (Sec. 5.3.1):
+ * Mann-Whitney U with ties counted one half.  HOST pointers; NaN scores rank lowest.
+ * Writes NaN when the mask has no positive or no negative pixel. */
+wdad_status wdad_auc(const float* score, const uint8_t* mask, int64_t n, double* auc);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WDAD_H */

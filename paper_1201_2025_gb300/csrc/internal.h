@@ -1,0 +1,74 @@
+// Internal C++ interfaces between the C-ABI layer (capi.cu) and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/wdad.h"
+
+namespace wdad {
+
+// Device-side reflect-101 (-1 -> 1, n -> n-2), valid for any integer i.
+__host__ __device__ __forceinline__ int reflect101(int i, int n) {
+    if (n == 1) return 0;
+    const int period = 2 * (n - 1);
+    int r = i % period;
+    if (r < 0) r += period;
+    return r < n ? r : period - r;
+}
+
+// Number of approximation coefficients after J halvings; level < 0 = auto (K <= 4).
+inline int dwt_levels(int L, int level, int* K) {
+    int n = L, J = 0;
+    if (level < 0) {
+        while (n > 4) { n = (n + 1) / 2; ++J; }
+    } else {
+        for (J = 0; J < level; ++J) n = (n + 1) / 2;
+    }
+    if (K) *K = n;
+    return J;
+}
+
+// Daubechies scaling filters (sum = sqrt 2): taps 8 = db4, taps 4 = D4.
+bool filter_coeffs(int taps, double* h);
+
+// ---- A1: DWT approximation ---------------------------------------------------
+// Builds the K x L approximation matrix (row-major) by running the Eq. 9
+// cascade on the L unit spectra on the GPU (FP64, rounded once to float).
+cudaError_t build_dwt_matrix(int L, int taps, int J, int K, float* A, double* scratch, cudaStream_t s);
+// approx[P][K] = A x for every pixel spectrum of cube[P][L].
+cudaError_t launch_dwt_approx(const float* cube, int64_t P, int L, const float* A, int K, float* approx,
+                              int num_sms, cudaStream_t s);
+bool dwt_shape_supported(int L, int K);
+
+// ---- A2-A5: detectors on few bands (dim <= 8, the DWT-reduced cube) ---------
+struct DetectArgs {
+    const float* x;   // [H][W][D]
+    int H, W, D;
+    int inner, outer;
+    float loading;
+    int border;
+    int dwest_mode;
+    float dwest_tau;
+    float* out[3];    // LRX, DWRX, DWEST maps (nullptr = not wanted)
+    uint8_t* flags;   // nullable
+};
+cudaError_t launch_detect_small(const DetectArgs& a, int tile_h, cudaStream_t s);
+cudaError_t launch_window_census(int H, int W, int inner, int outer, int border, int64_t* out,
+                                 cudaStream_t s);
+size_t detect_small_smem(int D, int inner, int outer, int tile_h);
+
+// ---- full-band detectors (dim > 8) -------------------------------------------
+struct FullArgs {
+    const float* x;   // [H][W][D]
+    int H, W, D;
+    int inner, outer;
+    float loading, cond_gate;
+    int border, dwest_mode, precision;
+    float dwest_tau;
+    float* out[3];
+    uint8_t* flags;
+};
+size_t fullband_workspace_bytes(const FullArgs& a, int num_sms);
+cudaError_t launch_detect_full(const FullArgs& a, void* ws, size_t ws_bytes, int num_sms, cudaStream_t s);
+
+}  // namespace wdad

@@ -1,0 +1,521 @@
+// A2-A5 on few bands (dim D <= 8, the DWT approximation matrix of Sec. 4):
+// dual-window statistics, regularised solve and eigen-decomposition, fused in
+// one kernel per output tile.
+//
+//  stage 0  the tile plus a halo of outer/2 pixels is loaded into shared memory,
+//           every index reflected at the image border (reflect-101);
+//  stage 1  (float payload) a tile reference spectrum c = mean of the loaded
+//           pixels is subtracted, so the second moments below are sums of
+//           (x - c)(x - c)^T with little cancellation;
+//  stage 2  horizontal box sums over the outer and the inner window width of the
+//           D first-order and D(D+1)/2 second-order channels, per halo row;
+//  stage 3  vertical box sums of those, per output pixel: sums over the outer
+//           square and over the inner square; the background annulus is outer
+//           minus inner (Sec. 2.2 dual window);
+//  stage 4  per pixel: mu_o, C_o (1/N), mu_i, C_i (1/n_i); LRX (Eq. 1) and DWRX
+//           (Eq. 5) through a Cholesky factor of C_o + delta I, delta =
+//           loading * trace(C_o) / D; DWEST (Eq. 2-4) through a cyclic Jacobi
+//           eigen-decomposition of C_i - C_o.
+//
+// Stages 0, 2 and 3 are templated on the payload so that the window census
+// (integer pixel indices instead of spectra) runs exactly the indexing code of
+// the detectors and can be checked bit for bit.
+#include <float.h>
+
+#include "internal.h"
+
+namespace wdad {
+
+constexpr int TW = 32;          // tile width = one warp across
+constexpr int kMaxSmem = 227 * 1024;
+
+struct TileGeom {
+    int H, W, ro, ri, th;        // image, radii, tile height
+    int ty0, tx0;                // tile origin
+    int HR, WR;                  // halo region rows / cols
+    __device__ TileGeom(int H_, int W_, int inner, int outer, int th_)
+        : H(H_), W(W_), ro(outer / 2), ri(inner / 2), th(th_) {
+        ty0 = blockIdx.y * th;
+        tx0 = blockIdx.x * TW;
+        HR = th + 2 * ro;
+        WR = TW + 2 * ro;
+    }
+};
+
+// ---------------------------------------------------------------- payloads
+template <int D>
+struct SpecPayload {                          // D-band spectra, float
+    using T = float;
+    static constexpr int DP = (D <= 4) ? 4 : 8;  // padded pixel stride in floats
+    static constexpr int NC = D + D * (D + 1) / 2;
+    static constexpr int WORDS = DP;             // 4-byte words per halo pixel
+    // first- then second-order channels of one shifted spectrum
+    static __device__ __forceinline__ void channels(const float* v, float (&ch)[NC]) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) ch[k] = v[k];
+        int q = D;
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+            for (int b = a; b < D; ++b) ch[q++] = v[a] * v[b];
+    }
+};
+
+struct CensusPayload {                        // linear pixel index, int64
+    using T = long long;
+    static constexpr int NC = 3;                 // 1, q, q^2
+    static constexpr int WORDS = 2;
+};
+
+// ---------------------------------------------------------------- stage 0: reflected halo load
+template <int D>
+__device__ __forceinline__ void load_halo_spec(const TileGeom& g, const float* __restrict__ x, float* xs,
+                                               float* part /* D per thread */) {
+    using P = SpecPayload<D>;
+    const int n = g.HR * g.WR;
+#pragma unroll
+    for (int k = 0; k < D; ++k) part[k] = 0.f;
+    for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
+        const int r = idx / g.WR, c = idx - r * g.WR;
+        const int gy = reflect101(g.ty0 - g.ro + r, g.H);
+        const int gx = reflect101(g.tx0 - g.ro + c, g.W);
+        const float* src = x + ((size_t)gy * g.W + gx) * D;
+        float* dst = xs + (size_t)idx * P::DP;
+        if constexpr (D == 4) {
+            const float4 v = __ldg(reinterpret_cast<const float4*>(src));
+            *reinterpret_cast<float4*>(dst) = v;
+            part[0] += v.x; part[1] += v.y; part[2] += v.z; part[3] += v.w;
+        } else {
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const float v = __ldg(src + k);
+                dst[k] = v;
+                part[k] += v;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void load_halo_census(const TileGeom& g, long long* xs) {
+    const int n = g.HR * g.WR;
+    for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
+        const int r = idx / g.WR, c = idx - r * g.WR;
+        const int gy = reflect101(g.ty0 - g.ro + r, g.H);
+        const int gx = reflect101(g.tx0 - g.ro + c, g.W);
+        xs[idx] = (long long)gy * g.W + gx;
+    }
+}
+
+// ---------------------------------------------------------------- stage 2: horizontal sums
+// hso[ch][r][j] = sum over the outer width of channel ch at halo row r, output column j;
+// hsi[ch][r'][j] = the same over the inner width for the th + 2 ri rows the inner squares use.
+template <class P, class ChanFn>
+__device__ __forceinline__ void horizontal_sums(const TileGeom& g, ChanFn chan, typename P::T* hso,
+                                                typename P::T* hsi) {
+    using T = typename P::T;
+    constexpr int NC = P::NC;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int wo = 2 * g.ro + 1, i0 = g.ro - g.ri, i1 = g.ro + g.ri;  // inner columns dc in [i0, i1]
+    const int rin0 = g.ro - g.ri, nin = g.th + 2 * g.ri;               // inner halo rows
+    const int plane_o = g.HR * TW, plane_i = nin * TW;
+    for (int r = warp; r < g.HR; r += nw) {
+        T so[NC], si[NC];
+#pragma unroll
+        for (int q = 0; q < NC; ++q) { so[q] = T(0); si[q] = T(0); }
+        const bool need_inner = (r >= rin0) && (r < rin0 + nin);
+        for (int dc = 0; dc < wo; ++dc) {
+            T ch[NC];
+            chan(r, lane + dc, ch);
+#pragma unroll
+            for (int q = 0; q < NC; ++q) so[q] += ch[q];
+            if (need_inner && dc >= i0 && dc <= i1) {
+#pragma unroll
+                for (int q = 0; q < NC; ++q) si[q] += ch[q];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NC; ++q) hso[q * plane_o + r * TW + lane] = so[q];
+        if (need_inner) {
+#pragma unroll
+            for (int q = 0; q < NC; ++q) hsi[q * plane_i + (r - rin0) * TW + lane] = si[q];
+        }
+    }
+}
+
+// ---------------------------------------------------------------- stage 3: vertical sums
+template <class P>
+__device__ __forceinline__ void vertical_sums(const TileGeom& g, int i, int j, const typename P::T* hso,
+                                              const typename P::T* hsi, typename P::T (&So)[P::NC],
+                                              typename P::T (&Si)[P::NC]) {
+    using T = typename P::T;
+    constexpr int NC = P::NC;
+    const int wo = 2 * g.ro + 1, wi = 2 * g.ri + 1;
+    const int plane_o = g.HR * TW, plane_i = (g.th + 2 * g.ri) * TW;
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+        T s = T(0);
+        for (int dr = 0; dr < wo; ++dr) s += hso[q * plane_o + (i + dr) * TW + j];
+        So[q] = s;
+        T t = T(0);
+        for (int dr = 0; dr < wi; ++dr) t += hsi[q * plane_i + (i + dr) * TW + j];
+        Si[q] = t;
+    }
+}
+
+// ---------------------------------------------------------------- small dense algebra in registers
+// Fails when a pivot is not above `floor` (a multiple of the FP32 rounding level of
+// the moments the matrix was formed from), so exactly singular covariances are
+// reported instead of factorised from rounding noise.
+template <int D>
+__device__ __forceinline__ bool chol_inplace(float (&G)[D][D], float floor) {
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        float s = G[j][j];
+#pragma unroll
+        for (int k = 0; k < j; ++k) s = fmaf(-G[j][k], G[j][k], s);
+        if (!(s > floor)) return false;
+        const float gjj = sqrtf(s), inv = 1.0f / gjj;
+        G[j][j] = gjj;
+#pragma unroll
+        for (int i = j + 1; i < D; ++i) {
+            float t = G[i][j];
+#pragma unroll
+            for (int k = 0; k < j; ++k) t = fmaf(-G[i][k], G[j][k], t);
+            G[i][j] = t * inv;
+        }
+    }
+    return true;
+}
+
+// ||G^{-1} d||^2 = d^T (G G^T)^{-1} d
+template <int D>
+__device__ __forceinline__ float chol_quad(const float (&G)[D][D], const float (&d)[D]) {
+    float y[D];
+    float q = 0.f;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        float t = d[i];
+#pragma unroll
+        for (int k = 0; k < i; ++k) t = fmaf(-G[i][k], y[k], t);
+        y[i] = t / G[i][i];
+        q = fmaf(y[i], y[i], q);
+    }
+    return q;
+}
+
+// Cyclic Jacobi on a symmetric D x D matrix (symmetric Schur rotations).
+// On return A's diagonal holds the eigenvalues and V's columns the eigenvectors.
+template <int D>
+__device__ __forceinline__ void jacobi_inplace(float (&A)[D][D], float (&V)[D][D]) {
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = 0; b < D; ++b) V[a][b] = (a == b) ? 1.f : 0.f;
+    constexpr int kSweeps = (D <= 4) ? 10 : 15;
+    for (int sweep = 0; sweep < kSweeps; ++sweep) {
+        float off = 0.f, dia = 0.f;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            dia = fmaf(A[a][a], A[a][a], dia);
+#pragma unroll
+            for (int b = a + 1; b < D; ++b) off = fmaf(A[a][b], A[a][b], off);
+        }
+        if (off <= 1e-16f * (dia + 2.f * off) || off == 0.f) break;
+#pragma unroll
+        for (int p = 0; p < D - 1; ++p)
+#pragma unroll
+            for (int q = p + 1; q < D; ++q) {
+                const float apq = A[p][q];
+                if (apq == 0.f) continue;
+                const float theta = (A[q][q] - A[p][p]) / (2.f * apq);
+                const float t = copysignf(1.f, theta) / (fabsf(theta) + sqrtf(fmaf(theta, theta, 1.f)));
+                const float c = rsqrtf(fmaf(t, t, 1.f)), s = t * c;
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    const float akp = A[k][p], akq = A[k][q];
+                    A[k][p] = c * akp - s * akq;
+                    A[k][q] = s * akp + c * akq;
+                }
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    const float apk = A[p][k], aqk = A[q][k];
+                    A[p][k] = c * apk - s * aqk;
+                    A[q][k] = s * apk + c * aqk;
+                }
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    const float vkp = V[k][p], vkq = V[k][q];
+                    V[k][p] = c * vkp - s * vkq;
+                    V[k][q] = s * vkp + c * vkq;
+                }
+            }
+    }
+}
+
+// ---------------------------------------------------------------- detector kernel
+template <int D>
+__global__ void __launch_bounds__(512) detect_small_kernel(DetectArgs a, int th) {
+    using P = SpecPayload<D>;
+    constexpr int NC = P::NC;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const TileGeom g(a.H, a.W, a.inner, a.outer, th);
+    const int nin = th + 2 * g.ri;
+    float* xs = reinterpret_cast<float*>(smem_raw);
+    float* hso = xs + (size_t)g.HR * g.WR * P::DP;
+    float* hsi = hso + (size_t)NC * g.HR * TW;
+    __shared__ float red[16][8];
+    __shared__ float cref[8];
+
+    // stage 0 + tile reference
+    float part[D];
+    load_halo_spec<D>(g, a.x, xs, part);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        float v = part[k];
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < D) {
+        float s = 0.f;
+        for (int w = 0; w < nw; ++w) s += red[w][threadIdx.x];
+        cref[threadIdx.x] = s / (float)(g.HR * g.WR);
+    }
+    __syncthreads();
+    // stage 1: shift in place
+    {
+        float c[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) c[k] = cref[k];
+        const int n = g.HR * g.WR;
+        for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
+            float* v = xs + (size_t)idx * P::DP;
+#pragma unroll
+            for (int k = 0; k < D; ++k) v[k] -= c[k];
+        }
+    }
+    __syncthreads();
+    // stage 2
+    auto chan = [&](int r, int col, float (&ch)[NC]) {
+        const float* v = xs + ((size_t)r * g.WR + col) * P::DP;
+        float t[D];
+        if constexpr (D == 4) {
+            const float4 q = *reinterpret_cast<const float4*>(v);
+            t[0] = q.x; t[1] = q.y; t[2] = q.z; t[3] = q.w;
+        } else {
+#pragma unroll
+            for (int k = 0; k < D; ++k) t[k] = v[k];
+        }
+        P::channels(t, ch);
+    };
+    horizontal_sums<P>(g, chan, hso, hsi);
+    __syncthreads();
+
+    // stages 3 + 4, one pixel per thread and step
+    const int N = (2 * g.ro + 1) * (2 * g.ro + 1) - (2 * g.ri + 1) * (2 * g.ri + 1);
+    const int ni = (2 * g.ri + 1) * (2 * g.ri + 1);
+    const float invN = 1.0f / (float)N, invni = 1.0f / (float)ni;
+    for (int pix = threadIdx.x; pix < th * TW; pix += blockDim.x) {
+        const int i = pix / TW, j = pix - i * TW;
+        const int y = g.ty0 + i, xq = g.tx0 + j;
+        if (y >= a.H || xq >= a.W) continue;
+        const size_t o = (size_t)y * a.W + xq;
+        if (a.border == 1 && (y - g.ro < 0 || y + g.ro >= a.H || xq - g.ro < 0 || xq + g.ro >= a.W)) {
+#pragma unroll
+            for (int t = 0; t < 3; ++t)
+                if (a.out[t]) a.out[t][o] = __int_as_float(0x7fc00000);
+            if (a.flags) a.flags[o] = 4;
+            continue;
+        }
+        float So[NC], Si[NC];
+        vertical_sums<P>(g, i, j, hso, hsi, So, Si);
+        (void)nin;
+        float mo[D], mi[D], Co[D][D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            mo[k] = (So[k] - Si[k]) * invN;
+            mi[k] = Si[k] * invni;
+        }
+        {
+            int q = D;
+#pragma unroll
+            for (int u = 0; u < D; ++u)
+#pragma unroll
+                for (int v = u; v < D; ++v) {
+                    const float cov = fmaf(-mo[u], mo[v], (So[q] - Si[q]) * invN);
+                    Co[u][v] = cov; Co[v][u] = cov;
+                    ++q;
+                }
+        }
+        uint8_t flag = 0;
+        if (a.out[0] || a.out[1]) {
+            float tr = 0.f, smax = 0.f;
+            {
+                int q = D;
+#pragma unroll
+                for (int u = 0; u < D; ++u) {
+                    tr += Co[u][u];
+                    smax = fmaxf(smax, (So[q] - Si[q]) * invN);  // uncentred second moment of the shifted data
+                    q += D - u;
+                }
+            }
+            const float delta = a.loading * tr / (float)D;
+            float G[D][D];
+#pragma unroll
+            for (int u = 0; u < D; ++u)
+#pragma unroll
+                for (int v = 0; v < D; ++v) G[u][v] = Co[u][v] + ((u == v) ? delta : 0.f);
+            const bool ok = chol_inplace<D>(G, 16.f * FLT_EPSILON * smax);
+            if (!ok) flag |= 2;
+            if (a.out[0]) {
+                const float* rc = xs + ((size_t)(i + g.ro) * g.WR + (j + g.ro)) * P::DP;  // shifted centre pixel
+                float d[D];
+#pragma unroll
+                for (int k = 0; k < D; ++k) d[k] = rc[k] - mo[k];
+                a.out[0][o] = ok ? chol_quad<D>(G, d) : __int_as_float(0x7fc00000);
+            }
+            if (a.out[1]) {
+                float d[D];
+#pragma unroll
+                for (int k = 0; k < D; ++k) d[k] = mi[k] - mo[k];
+                a.out[1][o] = ok ? fabsf(chol_quad<D>(G, d)) : __int_as_float(0x7fc00000);
+            }
+        }
+        if (a.out[2]) {
+            float Cd[D][D], V[D][D];
+            {
+                int q = D;
+#pragma unroll
+                for (int u = 0; u < D; ++u)
+#pragma unroll
+                    for (int v = u; v < D; ++v) {
+                        const float ci = fmaf(-mi[u], mi[v], Si[q] * invni);
+                        Cd[u][v] = ci - Co[u][v];  // Eq. 2
+                        Cd[v][u] = Cd[u][v];
+                        ++q;
+                    }
+            }
+            jacobi_inplace<D>(Cd, V);
+            float lmax = 0.f;
+#pragma unroll
+            for (int k = 0; k < D; ++k) lmax = fmaxf(lmax, fabsf(Cd[k][k]));
+            const float tau = a.dwest_tau * lmax;
+            float acc = 0.f, acc2 = 0.f;
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                if (!(Cd[k][k] > tau)) continue;
+                float best = -1.f, sg = 1.f, proj = 0.f;
+#pragma unroll
+                for (int u = 0; u < D; ++u) {
+                    const float v = V[u][k];
+                    if (fabsf(v) > best) { best = fabsf(v); sg = (v >= 0.f) ? 1.f : -1.f; }
+                    proj = fmaf(v, mi[u] - mo[u], proj);  // v^T m_diff (Eq. 3, 4)
+                }
+                acc = fmaf(sg, proj, acc);
+                acc2 = fmaf(proj, proj, acc2);
+            }
+            a.out[2][o] = (a.dwest_mode == 0) ? fabsf(acc) : sqrtf(acc2);
+        }
+        if (a.flags) a.flags[o] = flag;
+    }
+}
+
+// ---------------------------------------------------------------- census kernel
+__global__ void __launch_bounds__(512) census_kernel(int H, int W, int inner, int outer, int border, int th,
+                                                     long long* __restrict__ out) {
+    using P = CensusPayload;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const TileGeom g(H, W, inner, outer, th);
+    long long* xs = reinterpret_cast<long long*>(smem_raw);
+    long long* hso = xs + (size_t)g.HR * g.WR;
+    long long* hsi = hso + (size_t)P::NC * g.HR * TW;
+    load_halo_census(g, xs);
+    __syncthreads();
+    auto chan = [&](int r, int col, long long (&ch)[3]) {
+        const long long q = xs[(size_t)r * g.WR + col];
+        ch[0] = 1; ch[1] = q; ch[2] = q * q;
+    };
+    horizontal_sums<P>(g, chan, hso, hsi);
+    __syncthreads();
+    for (int pix = threadIdx.x; pix < th * TW; pix += blockDim.x) {
+        const int i = pix / TW, j = pix - i * TW;
+        const int y = g.ty0 + i, xq = g.tx0 + j;
+        if (y >= H || xq >= W) continue;
+        long long* o = out + ((size_t)y * W + xq) * 6;
+        if (border == 1 && (y - g.ro < 0 || y + g.ro >= H || xq - g.ro < 0 || xq + g.ro >= W)) {
+            for (int t = 0; t < 6; ++t) o[t] = -1;
+            continue;
+        }
+        long long So[3], Si[3];
+        vertical_sums<P>(g, i, j, hso, hsi, So, Si);
+        o[0] = So[0] - Si[0]; o[1] = So[1] - Si[1]; o[2] = So[2] - Si[2];
+        o[3] = Si[0]; o[4] = Si[1]; o[5] = Si[2];
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+static size_t smem_bytes(int words_per_px, int nc, int tsize, int inner, int outer, int th) {
+    const int ro = outer / 2, ri = inner / 2;
+    const size_t HR = th + 2 * ro, WR = TW + 2 * ro;
+    return HR * WR * words_per_px * 4 + (size_t)nc * HR * TW * tsize + (size_t)nc * (th + 2 * ri) * TW * tsize;
+}
+
+static int spec_nc(int D) { return D + D * (D + 1) / 2; }
+static int spec_dp(int D) { return D <= 4 ? 4 : 8; }
+
+size_t detect_small_smem(int D, int inner, int outer, int tile_h) {
+    return smem_bytes(spec_dp(D), spec_nc(D), 4, inner, outer, tile_h);
+}
+
+static int pick_th(int D, int inner, int outer, int want) {
+    for (int th = want; th >= 1; th >>= 1)
+        if (detect_small_smem(D, inner, outer, th) <= (size_t)kMaxSmem) return th;
+    return 0;
+}
+
+template <int D>
+static cudaError_t launch_d(const DetectArgs& a, int th, cudaStream_t s) {
+    const size_t smem = detect_small_smem(D, a.inner, a.outer, th);
+    cudaError_t e = cudaFuncSetAttribute(detect_small_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((a.W + TW - 1) / TW, (a.H + th - 1) / th);
+    const int threads = th >= 16 ? 512 : 256;
+    detect_small_kernel<D><<<grid, threads, smem, s>>>(a, th);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_detect_small(const DetectArgs& a, int tile_h, cudaStream_t s) {
+    if ((int64_t)a.H * a.W == 0) return cudaSuccess;
+    const int th = pick_th(a.D, a.inner, a.outer, tile_h > 0 ? tile_h : 16);
+    if (th == 0) return cudaErrorInvalidValue;
+    switch (a.D) {
+        case 1: return launch_d<1>(a, th, s);
+        case 2: return launch_d<2>(a, th, s);
+        case 3: return launch_d<3>(a, th, s);
+        case 4: return launch_d<4>(a, th, s);
+        case 5: return launch_d<5>(a, th, s);
+        case 6: return launch_d<6>(a, th, s);
+        case 7: return launch_d<7>(a, th, s);
+        case 8: return launch_d<8>(a, th, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_window_census(int H, int W, int inner, int outer, int border, int64_t* out, cudaStream_t s) {
+    if ((int64_t)H * W == 0) return cudaSuccess;
+    int th = 16;
+    while (th > 1 && smem_bytes(CensusPayload::WORDS, 3, 8, inner, outer, th) > (size_t)kMaxSmem) th >>= 1;
+    const size_t smem = smem_bytes(CensusPayload::WORDS, 3, 8, inner, outer, th);
+    if (smem > (size_t)kMaxSmem) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(census_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((W + TW - 1) / TW, (H + th - 1) / th);
+    census_kernel<<<grid, th >= 16 ? 512 : 256, smem, s>>>(H, W, inner, outer, border, th,
+                                                           reinterpret_cast<long long*>(out));
+    return cudaGetLastError();
+}
+
+}  // namespace wdad

@@ -1,0 +1,28 @@
+"""Shared parity helpers for the GPU-vs-oracle tests."""
+import numpy as np
+
+# FP32 paths: per-pixel relative error |s - s_ref| / max(|s_ref|, 1e-6 median|s_ref|) <= 1e-4;
+# DWT coefficients 1e-5; indices and census bit-exact.
+TOL_SCORE = 1e-4
+TOL_DWT = 1e-5
+
+
+def relerr(got, want):
+    got = np.asarray(got, dtype=np.float64)
+    want = np.asarray(want, dtype=np.float64)
+    floor = 1e-6 * np.median(np.abs(want[np.isfinite(want)])) if np.isfinite(want).any() else 0.0
+    den = np.maximum(np.abs(want), max(floor, 1e-300))
+    e = np.abs(got - want) / den
+    both_nan = np.isnan(got) & np.isnan(want)
+    e[both_nan] = 0.0
+    e[np.isnan(got) ^ np.isnan(want)] = np.inf
+    return e
+
+
+def dwest_ok_mask(aux, sel_margin=1e-4, sign_margin=1e-3, gap=1e-3):
+    """Pixels whose DWEST score is well determined in FP32: no eigenvalue within
+    sel_margin * max|lambda| of the threshold, the two largest entries of every
+    selected eigenvector apart by sign_margin, and selected eigenvalues separated
+    by gap * max|lambda|.  The others are counted, not compared."""
+    a = np.asarray(aux)
+    return (a[..., 0] >= sel_margin) & (a[..., 1] >= sign_margin) & (a[..., 2] >= gap)

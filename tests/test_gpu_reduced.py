@@ -1,0 +1,213 @@
+"""GPU parity of the DWT-reduced path (A1-A6 on the approximation matrix) against
+the FP64 oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+from parity import TOL_DWT, TOL_SCORE, dwest_ok_mask, relerr
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def wd():
+    from paper_1201_2025_gb300 import wdad
+    wdad.lib()
+    return wdad
+
+
+@pytest.fixture(scope="module")
+def synth():
+    from paper_1201_2025_gb300 import synth
+    return synth
+
+
+@pytest.fixture(scope="module")
+def scene48(synth):
+    return synth.scene_48x48(0)
+
+
+def _gpu(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+# ---------------------------------------------------------------- A1 DWT
+@pytest.mark.parametrize("shape", [(48, 48, 224), (7, 13, 188), (5, 9, 189), (33, 17, 128), (1, 1, 224),
+                                   (3, 5, 97), (2, 3, 4), (4, 4, 1000), (3, 3, 250)])
+@pytest.mark.parametrize("taps", [8, 4])
+def test_dwt_parity(wd, synth, shape, taps):
+    H, W, L = shape
+    rng = np.random.default_rng(H * 1000 + L + taps)
+    cube = (0.3 + 0.1 * rng.standard_normal(shape)).astype(np.float32)
+    got = wd.wdad_dwt_approx(_gpu(cube), wavelet_taps=taps).cpu().numpy()
+    want = oracle.dwt_approx(cube, taps=taps)
+    assert got.shape == want.shape
+    scale = np.maximum(np.abs(want), np.sqrt(np.mean(want ** 2)))
+    assert np.max(np.abs(got - want) / scale) <= TOL_DWT
+
+
+@pytest.mark.parametrize("level", [0, 1, 2, 5])
+def test_dwt_explicit_level(wd, level):
+    cube = (0.3 + 0.1 * np.random.default_rng(level).standard_normal((6, 10, 224))).astype(np.float32)
+    K = wd.wdad_query_K(224, 8, level)
+    if K > 8:
+        with pytest.raises(wd.WdadError):
+            wd.wdad_dwt_approx(_gpu(cube), level=level)
+        return
+    got = wd.wdad_dwt_approx(_gpu(cube), level=level).cpu().numpy()
+    want = oracle.dwt_approx(cube, level=level)
+    assert np.max(np.abs(got - want) / np.maximum(np.abs(want), 1e-3)) <= TOL_DWT
+
+
+def test_dwt_scene_and_ragged_pixel_count(wd, scene48):
+    cube = scene48.cube[:, :47]  # 2256 pixels: not a multiple of the 8-pixel warp step
+    got = wd.wdad_dwt_approx(_gpu(cube)).cpu().numpy()
+    want = oracle.dwt_approx(np.ascontiguousarray(cube))
+    assert np.max(np.abs(got - want) / np.abs(want)) <= TOL_DWT
+
+
+# ---------------------------------------------------------------- A2 windows, bit-exact
+@pytest.mark.parametrize("H,W", [(48, 48), (5, 7), (1, 40), (40, 1), (37, 70), (100, 33), (2, 2)])
+@pytest.mark.parametrize("win", [(1, 3), (3, 9), (3, 11), (5, 15), (7, 21), (5, 13), (1, 15)])
+@pytest.mark.parametrize("border", [0, 1])
+def test_window_census_bit_exact(wd, H, W, win, border):
+    got = wd.wdad_window_census(H, W, inner=win[0], outer=win[1], border=border).cpu().numpy().reshape(-1, 6)
+    want = oracle.window_census(H, W, win[0], win[1], border=border)
+    assert np.array_equal(got, want)
+
+
+# ---------------------------------------------------------------- A3-A6 detectors on the reduced cube
+def _check_scene(wd, cube, win, loading=1e-3, dwest_mode=0, label=""):
+    x = _gpu(cube)
+    got = wd.wdad_detect_all(x, reduce=True, inner=win[0], outer=win[1], loading=loading,
+                             dwest_mode=dwest_mode).cpu().numpy()
+    a = oracle.dwt_approx(cube)
+    for det in (0, 1):
+        want = oracle.detect(a, det, win[0], win[1], loading=loading)
+        e = relerr(got[det], want)
+        assert e.max() <= TOL_SCORE, f"{label} det {det} win {win}: max rel err {e.max():.3g}"
+    want, aux = oracle.detect(a, 2, win[0], win[1], dwest_mode=dwest_mode, want_aux=True)
+    ok = dwest_ok_mask(aux)
+    e = relerr(got[2], want)
+    assert ok.mean() > 0.9, f"{label}: only {ok.mean():.3f} of DWEST pixels are well determined"
+    assert e[ok].max() <= TOL_SCORE, f"{label} DWEST win {win}: max rel err {e[ok].max():.3g} ({(~ok).sum()} excluded)"
+    return got
+
+
+@pytest.mark.parametrize("win", [(3, 11), (3, 9), (5, 15), (7, 21)])
+def test_reduced_detectors_scene48(wd, scene48, win):
+    _check_scene(wd, scene48.cube, win, label="48x48")
+
+
+def test_reduced_dwest_projection_norm(wd, scene48):
+    _check_scene(wd, scene48.cube, (3, 11), dwest_mode=1, label="mode1")
+
+
+@pytest.mark.parametrize("shape,win", [((60, 100, 189), (5, 13)), ((100, 100, 189), (3, 13)),
+                                       ((37, 53, 224), (1, 15)), ((19, 70, 128), (5, 15))])
+def test_reduced_detectors_paper_shapes(wd, synth, shape, win):
+    sc = synth.make_scene(*shape, seed=shape[0], n_anom=5, margin=3)
+    _check_scene(wd, sc.cube, win, label=str(shape))
+
+
+def test_single_detector_equals_fused(wd, scene48):
+    x = _gpu(scene48.cube)
+    allv = wd.wdad_detect_all(x, reduce=True, inner=3, outer=9).cpu().numpy()
+    for det in range(3):
+        one = wd.wdad_detect(x, det, reduce=True, inner=3, outer=9).cpu().numpy()
+        assert np.array_equal(one, allv[det])
+
+
+@pytest.mark.parametrize("D", [1, 2, 3, 4, 5, 6, 7, 8])
+def test_few_band_cube_direct(wd, D):
+    # reduce=0 on a D-band cube runs the same kernel for every template dimension
+    rng = np.random.default_rng(D)
+    H, W = 29, 45
+    cube = (rng.standard_normal((H, W, D)) @ rng.standard_normal((D, D)) * 0.2 + 1.0).astype(np.float32)
+    got = wd.wdad_detect_all(_gpu(cube), reduce=False, inner=3, outer=9).cpu().numpy()
+    for det in (0, 1):
+        want = oracle.detect(cube, det, 3, 9)
+        e = relerr(got[det], want)
+        assert e.max() <= TOL_SCORE, (D, det, e.max())
+    want, aux = oracle.detect(cube, 2, 3, 9, want_aux=True)
+    ok = dwest_ok_mask(aux)
+    assert ok.mean() > 0.8
+    assert relerr(got[2], want)[ok].max() <= TOL_SCORE
+
+
+def test_valid_border_mode(wd, scene48):
+    x = _gpu(scene48.cube)
+    flags = torch.zeros((48, 48), dtype=torch.uint8, device="cuda")
+    got = wd.wdad_detect_all(x, reduce=True, inner=3, outer=11, border=1, flags=flags).cpu().numpy()
+    f = flags.cpu().numpy()
+    invalid = np.ones((48, 48), bool)
+    invalid[5:-5, 5:-5] = False
+    assert np.isnan(got[:, invalid]).all() and np.isfinite(got[:, ~invalid]).all()
+    assert np.all(f[invalid] == 4) and np.all(f[~invalid] == 0)
+    a = oracle.dwt_approx(scene48.cube)
+    want = oracle.detect(a, 0, 3, 11, border=1)
+    assert relerr(got[0], want)[~invalid].max() <= TOL_SCORE
+
+
+def test_zero_loading_singular_background_flags_nan(wd):
+    # K=4 bands but the background is a constant spectrum: C_o = 0 and no loading -> not PD
+    cube = np.full((16, 16, 128), 0.25, np.float32)
+    flags = torch.zeros((16, 16), dtype=torch.uint8, device="cuda")
+    got = wd.wdad_detect(_gpu(cube), 0, reduce=True, inner=1, outer=5, loading=0.0, flags=flags).cpu().numpy()
+    assert np.isnan(got).all() and np.all(flags.cpu().numpy() & 2)
+
+
+def test_empty_and_invalid_inputs(wd):
+    e = torch.empty((0, 5, 224), device="cuda")
+    assert wd.wdad_detect(e, 0).shape == (0, 5)
+    x = torch.rand((8, 8, 224), device="cuda")
+    with pytest.raises(wd.WdadError) as ei:
+        wd.wdad_detect(x, 0, inner=4, outer=9)
+    assert ei.value.status == wd.WDAD_ERR_ARG
+    with pytest.raises(wd.WdadError) as ei:
+        wd.wdad_detect(x, 0, inner=9, outer=9)
+    assert ei.value.status == wd.WDAD_ERR_ARG
+    with pytest.raises(wd.WdadError) as ei:
+        wd.wdad_detect(x, 0, wavelet_taps=6)
+    assert ei.value.status == wd.WDAD_ERR_ARG
+    with pytest.raises(wd.WdadError) as ei:
+        wd.wdad_detect(x, 7)
+    assert ei.value.status == wd.WDAD_ERR_ARG
+    with pytest.raises(wd.WdadError) as ei:  # shared memory cannot hold a 61/63 dual window tile
+        wd.wdad_detect(x, 0, inner=61, outer=63)
+    assert ei.value.status == wd.WDAD_ERR_UNSUPPORTED
+
+
+def test_auc_matches_oracle_and_paper_direction(wd, scene48):
+    x = _gpu(scene48.cube)
+    got = wd.wdad_detect_all(x, reduce=True, inner=3, outer=11).cpu().numpy()
+    a = oracle.dwt_approx(scene48.cube)
+    for det in range(3):
+        want = oracle.detect(a, det, 3, 11)
+        assert abs(wd.wdad_auc(got[det], scene48.mask) - oracle.auc(want, scene48.mask)) <= 0.002
+
+
+# ---------------------------------------------------------------- full-size workload, sampled
+@pytest.fixture(scope="module")
+def scene512(synth):
+    return synth.scene_512x512(0)
+
+
+@pytest.mark.parametrize("win", [(3, 9), (5, 15), (7, 21)])
+def test_reduced_detectors_512_sampled(wd, scene512, win):
+    cube = scene512.cube
+    H, W, _ = cube.shape
+    got = wd.wdad_detect_all(_gpu(cube), reduce=True, inner=win[0], outer=win[1]).cpu().numpy()
+    rng = np.random.default_rng(win[1])
+    pix = np.unique(np.concatenate([rng.choice(H * W, 4096, replace=False), np.flatnonzero(scene512.mask),
+                                    [0, W - 1, H * W - 1, (H - 1) * W, W * (H // 2) + W // 2]]))
+    a = oracle.dwt_approx(cube)
+    for det in (0, 1):
+        want = oracle.detect(a, det, win[0], win[1], pixels=pix)
+        e = relerr(got[det].ravel()[pix], want)
+        assert e.max() <= TOL_SCORE, (det, e.max())
+    want, aux = oracle.detect(a, 2, win[0], win[1], pixels=pix, want_aux=True)
+    ok = dwest_ok_mask(aux)
+    assert ok.mean() > 0.9
+    assert relerr(got[2].ravel()[pix], want)[ok].max() <= TOL_SCORE
