@@ -20,6 +20,7 @@ _SRC = [os.path.join(_HERE, "oracle.c"), os.path.join(_HERE, "cnn_oracle.c")]
 _lib = None
 
 LRX, DWRX, DWEST = 0, 1, 2
+NAUX = 6  # per-pixel diagnostics of detect(), see oracle.c
 
 
 def build(force: bool = False) -> str:
@@ -141,7 +142,7 @@ def detect(cube: np.ndarray, detector: int, inner: int, outer: int, loading: flo
     full = pixels is None
     pix = np.arange(H * W, dtype=np.int64) if full else np.ascontiguousarray(pixels, dtype=np.int64)
     score = np.zeros(len(pix))
-    aux = np.zeros((len(pix), 4)) if want_aux else None
+    aux = np.zeros((len(pix), NAUX)) if want_aux else None
     rc = lib().or_detect(_ptr(c, ctypes.c_double), H, W, D, detector, inner, outer, loading, border,
                          dwest_mode, _ptr(pix, ctypes.c_int64), len(pix), _ptr(score, ctypes.c_double),
                          _ptr(aux, ctypes.c_double) if want_aux else None, int(want_cond), nthreads)
@@ -150,7 +151,7 @@ def detect(cube: np.ndarray, detector: int, inner: int, outer: int, loading: flo
     if full:
         score = score.reshape(H, W)
         if want_aux:
-            aux = aux.reshape(H, W, 4)
+            aux = aux.reshape(H, W, NAUX)
     return (score, aux) if want_aux else score
 
 

@@ -345,15 +345,20 @@ static void jacobi_eig(double* A, int n, double* V, double* w) {
 /* ------------------------------------------------------------------------ */
 /* Detectors.  det: 0 = LRX (Sec. 2.1, Eq. 1 on a local background),         */
 /* 1 = DWRX (Eq. 5), 2 = DWEST (Eq. 2-4).  cube is [H*W][D] double.           */
-/* aux (nullable, 4 doubles per listed pixel):                                */
+/* aux (nullable, OR_NAUX doubles per listed pixel):                         */
 /*   LRX/DWRX: [0] lambda_min, [1] lambda_max of C_o + delta I (only when     */
-/*             want_cond != 0, else NaN), [2] delta, [3] N                    */
+/*             want_cond != 0, else NaN), [2] delta, [3] N, [4] ||d||_2 of    */
+/*             the tested difference vector, [5] NaN                          */
 /*   DWEST:    [0] selection margin min_k |lambda_k - tau| / max|lambda|,     */
 /*             [1] sign margin min over selected v of (|v|_(1) - |v|_(2)),    */
 /*             [2] eigen-gap min over selected k, j != k of |l_k - l_j| /     */
-/*             max|lambda|, [3] number of selected eigenvectors               */
+/*             max|lambda|, [3] number of selected eigenvectors,              */
+/*             [4] ||m_diff||_2, [5] sum over selected k of |v_k^T m_diff|    */
 /* Pixels whose outer window leaves the image get NaN when border == 1.       */
 /* ------------------------------------------------------------------------ */
+#define OR_NAUX 6
+int or_naux(void) { return OR_NAUX; }
+
 int or_detect(const double* cube, int H, int W, int D, int det, int inner, int outer,
               double loading, int border, int dwest_mode, const int64_t* pix, int64_t npix,
               double* score, double* aux, int want_cond, int nthreads) {
@@ -384,8 +389,8 @@ int or_detect(const double* cube, int H, int W, int D, int det, int inner, int o
         for (int64_t t = 0; t < npix; ++t) {
             int64_t p = pix[t];
             int py = (int)(p / W), px = (int)(p % W);
-            double* ax = aux ? aux + 4 * t : NULL;
-            if (ax) ax[0] = ax[1] = ax[2] = ax[3] = NAN;
+            double* ax = aux ? aux + OR_NAUX * t : NULL;
+            if (ax) for (int k = 0; k < OR_NAUX; ++k) ax[k] = NAN;
             if (border == 1 && (py - ro < 0 || py + ro >= H || px - ro < 0 || px + ro >= W)) {
                 score[t] = NAN;
                 continue;
@@ -427,7 +432,11 @@ int or_detect(const double* cube, int H, int W, int D, int det, int inner, int o
                     for (int k = 1; k < D; ++k) { lmin = fmin(lmin, w[k]); lmax = fmax(lmax, w[k]); }
                     ax[0] = lmin; ax[1] = lmax;
                 }
-                if (ax) { ax[2] = delta; ax[3] = N; }
+                if (ax) {
+                    double nd = 0.0;
+                    for (int k = 0; k < D; ++k) nd += d[k] * d[k];
+                    ax[2] = delta; ax[3] = N; ax[4] = sqrt(nd);
+                }
                 if (cholesky(Co, D)) { score[t] = NAN; continue; }
                 double q = chol_quadform(Co, D, d, y);
                 score[t] = (det == 0) ? q : fabs(q);
@@ -445,7 +454,7 @@ int or_detect(const double* cube, int H, int W, int D, int det, int inner, int o
                 double lmax = 0.0;
                 for (int k = 0; k < D; ++k) lmax = fmax(lmax, fabs(w[k]));
                 double tau = 1e-6 * lmax;
-                double acc = 0.0, acc2 = 0.0, selm = INFINITY, sgnm = INFINITY, gap = INFINITY;
+                double acc = 0.0, acc2 = 0.0, accabs = 0.0, selm = INFINITY, sgnm = INFINITY, gap = INFINITY;
                 int nsel = 0;
                 for (int k = 0; k < D; ++k) {
                     if (lmax > 0.0) selm = fmin(selm, fabs(w[k] - tau) / lmax);
@@ -465,11 +474,16 @@ int or_detect(const double* cube, int H, int W, int D, int det, int inner, int o
                     for (int a = 0; a < D; ++a) proj += V[a * D + k] * d[a];
                     acc += sg * proj;
                     acc2 += proj * proj;
+                    accabs += fabs(proj);
                     for (int j = 0; j < D; ++j)
                         if (j != k && lmax > 0.0) gap = fmin(gap, fabs(w[k] - w[j]) / lmax);
                 }
                 score[t] = (dwest_mode == 0) ? fabs(acc) : sqrt(acc2);
-                if (ax) { ax[0] = selm; ax[1] = sgnm; ax[2] = gap; ax[3] = nsel; }
+                if (ax) {
+                    double nm = 0.0;
+                    for (int k = 0; k < D; ++k) nm += d[k] * d[k];
+                    ax[0] = selm; ax[1] = sgnm; ax[2] = gap; ax[3] = nsel; ax[4] = sqrt(nm); ax[5] = accabs;
+                }
             }
         }
         free(mo); free(mi); free(d); free(y); free(Co); free(Ci); free(V); free(w); free(xc);

@@ -121,35 +121,9 @@ wdad_status get_dwt_plan(wdad_ctx* h, int L, int taps, int level, const float** 
     return WDAD_OK;
 }
 
-// Runs A1 into the workspace (offset 0) and returns the reduced cube.
-wdad_status reduce_into_ws(wdad_ctx* h, const float* cube, int H, int W, int L, const wdad_params* p,
-                           const float** xr, int* K, cudaStream_t s) {
-    const float* A = nullptr;
-    wdad_status st = get_dwt_plan(h, L, p->wavelet_taps, p->level, &A, K, s);
-    if (st != WDAD_OK) return st;
-    const int64_t P = (int64_t)H * W;
-    st = ensure_ws(h, sizeof(float) * (size_t)P * (*K) + 256);
-    if (st != WDAD_OK) return st;
-    cudaError_t e = wdad::launch_dwt_approx(cube, P, L, A, *K, (float*)h->ws, h->num_sms, s);
-    if (e != cudaSuccess) return cuda_fail(h, e, "dwt_approx launch");
-    *xr = (const float*)h->ws;
-    return WDAD_OK;
-}
-
-wdad_status run_detect(wdad_ctx* h, const float* cube, int H, int W, int L, int reduce, const wdad_params* p,
-                       float* out3[3], uint8_t* flags, cudaStream_t s) {
-    wdad_status st = check_params(h, p);
-    if (st != WDAD_OK) return st;
-    st = check_cube(h, cube, H, W, L);
-    if (st != WDAD_OK) return st;
-    if (reduce != 0 && reduce != 1) return fail(h, WDAD_ERR_ARG, "reduce must be 0 or 1");
-    if ((int64_t)H * W == 0) return WDAD_OK;
-    const float* x = cube;
-    int D = L;
-    if (reduce) {
-        st = reduce_into_ws(h, cube, H, W, L, p, &x, &D, s);
-        if (st != WDAD_OK) return st;
-    }
+// Detectors on a D-band device cube x (the reduced cube, or the full-band cube).
+wdad_status detect_bands(wdad_ctx* h, const float* x, int H, int W, int D, const wdad_params* p, float* out3[3],
+                         uint8_t* flags, void* ws, size_t ws_bytes, cudaStream_t s) {
     if (D <= 8) {
         wdad::DetectArgs a{};
         a.x = x; a.H = H; a.W = W; a.D = D;
@@ -171,11 +145,58 @@ wdad_status run_detect(wdad_ctx* h, const float* cube, int H, int W, int L, int 
     a.flags = flags;
     const size_t need = wdad::fullband_workspace_bytes(a, h->num_sms);
     if (need == 0) return fail(h, WDAD_ERR_UNSUPPORTED, "full-band detectors for %d bands are not supported", D);
-    st = ensure_ws(h, need);
-    if (st != WDAD_OK) return st;
-    cudaError_t e = wdad::launch_detect_full(a, h->ws, h->ws_bytes, h->num_sms, s);
+    if (need > ws_bytes) return fail(h, WDAD_ERR_NOMEM, "full-band workspace of %zu bytes not available", need);
+    cudaError_t e = wdad::launch_detect_full(a, ws, need, h->num_sms, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "detect_full launch");
     return WDAD_OK;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+wdad_status full_ws_need(wdad_ctx* h, int H, int W, int D, const wdad_params* p, size_t* need) {
+    *need = 0;
+    if (D <= 8) return WDAD_OK;
+    wdad::FullArgs a{};
+    a.H = H; a.W = W; a.D = D; a.inner = p->inner; a.outer = p->outer; a.precision = p->precision;
+    *need = wdad::fullband_workspace_bytes(a, h->num_sms);
+    if (*need == 0) return fail(h, WDAD_ERR_UNSUPPORTED, "full-band detectors for %d bands are not supported", D);
+    return WDAD_OK;
+}
+
+wdad_status run_detect(wdad_ctx* h, const float* cube, int H, int W, int L, int reduce, const wdad_params* p,
+                       float* out3[3], uint8_t* flags, cudaStream_t s) {
+    wdad_status st = check_params(h, p);
+    if (st != WDAD_OK) return st;
+    st = check_cube(h, cube, H, W, L);
+    if (st != WDAD_OK) return st;
+    if (reduce != 0 && reduce != 1) return fail(h, WDAD_ERR_ARG, "reduce must be 0 or 1");
+    if ((int64_t)H * W == 0) return WDAD_OK;
+    const int64_t P = (int64_t)H * W;
+    if (!reduce) {
+        size_t need = 0;
+        st = full_ws_need(h, H, W, L, p, &need);
+        if (st != WDAD_OK) return st;
+        if (need) {
+            st = ensure_ws(h, need);
+            if (st != WDAD_OK) return st;
+        }
+        return detect_bands(h, cube, H, W, L, p, out3, flags, h->ws, h->ws_bytes, s);
+    }
+    const int K = wdad_query_K(L, p->wavelet_taps, p->level);
+    size_t need = 0;
+    st = full_ws_need(h, H, W, K, p, &need);
+    if (st != WDAD_OK) return st;
+    const size_t off = align256(sizeof(float) * (size_t)P * K);
+    st = ensure_ws(h, off + need);
+    if (st != WDAD_OK) return st;
+    const float* A = nullptr;
+    int k2 = 0;
+    st = get_dwt_plan(h, L, p->wavelet_taps, p->level, &A, &k2, s);
+    if (st != WDAD_OK) return st;
+    float* xr = (float*)h->ws;
+    cudaError_t e = wdad::launch_dwt_approx(cube, P, L, A, K, xr, h->num_sms, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "dwt_approx launch");
+    return detect_bands(h, xr, H, W, K, p, out3, flags, (char*)h->ws + off, h->ws_bytes - off, s);
 }
 
 }  // namespace
@@ -288,6 +309,68 @@ wdad_status wdad_detect_all(wdad_handle h, const float* cube, int H, int W, int 
         const size_t P = (size_t)H * W;
         float* out3[3] = {scores, scores + P, scores + 2 * P};
         return run_detect(h, cube, H, W, L, reduce, p, out3, flags, (cudaStream_t)stream);
+    } catch (...) {
+        return fail(h, WDAD_ERR_NOMEM, "host exception");
+    }
+}
+
+wdad_status wdad_detect_all_host(wdad_handle h, const float* host_cube, int H, int W, int L, int reduce,
+                                 int nwin, const wdad_params* params, float* host_scores, void* stream) {
+    if (!h) return WDAD_ERR_ARG;
+    if (nwin < 1 || nwin > 64 || !params) return fail(h, WDAD_ERR_ARG, "nwin must be 1..64 with params[nwin]");
+    if (reduce != 0 && reduce != 1) return fail(h, WDAD_ERR_ARG, "reduce must be 0 or 1");
+    try {
+        DeviceGuard g(h->device);
+        for (int w = 0; w < nwin; ++w) {
+            wdad_status st = check_params(h, &params[w]);
+            if (st != WDAD_OK) return st;
+            if (reduce && (params[w].wavelet_taps != params[0].wavelet_taps || params[w].level != params[0].level))
+                return fail(h, WDAD_ERR_ARG, "all windows of one call share the wavelet and level");
+        }
+        if (H < 0 || W < 0 || L < 1) return fail(h, WDAD_ERR_ARG, "bad cube shape %d x %d x %d", H, W, L);
+        const int64_t P = (int64_t)H * W;
+        if (P == 0) return WDAD_OK;
+        if (!host_cube || !host_scores) return fail(h, WDAD_ERR_ARG, "host_cube and host_scores must not be NULL");
+        cudaStream_t s = (cudaStream_t)stream;
+        const int D = reduce ? wdad_query_K(L, params[0].wavelet_taps, params[0].level) : L;
+        size_t full = 0;
+        for (int w = 0; w < nwin; ++w) {
+            size_t need = 0;
+            wdad_status st = full_ws_need(h, H, W, D, &params[w], &need);
+            if (st != WDAD_OK) return st;
+            full = std::max(full, need);
+        }
+        const size_t b_cube = align256(sizeof(float) * (size_t)P * L);
+        const size_t b_red = reduce ? align256(sizeof(float) * (size_t)P * D) : 0;
+        const size_t b_out = align256(sizeof(float) * (size_t)P * 3 * nwin);
+        wdad_status st = ensure_ws(h, b_cube + b_red + b_out + full);
+        if (st != WDAD_OK) return st;
+        char* base = (char*)h->ws;
+        float* d_cube = (float*)base;
+        float* d_red = (float*)(base + b_cube);
+        float* d_out = (float*)(base + b_cube + b_red);
+        void* scratch = base + b_cube + b_red + b_out;
+        cudaError_t e = cudaMemcpyAsync(d_cube, host_cube, sizeof(float) * (size_t)P * L, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "copy cube to device");
+        const float* x = d_cube;
+        if (reduce) {
+            const float* A = nullptr;
+            int k2 = 0;
+            st = get_dwt_plan(h, L, params[0].wavelet_taps, params[0].level, &A, &k2, s);
+            if (st != WDAD_OK) return st;
+            e = wdad::launch_dwt_approx(d_cube, P, L, A, D, d_red, h->num_sms, s);
+            if (e != cudaSuccess) return cuda_fail(h, e, "dwt_approx launch");
+            x = d_red;
+        }
+        for (int w = 0; w < nwin; ++w) {
+            float* o = d_out + (size_t)w * 3 * P;
+            float* out3[3] = {o, o + P, o + 2 * P};
+            st = detect_bands(h, x, H, W, D, &params[w], out3, nullptr, scratch, full, s);
+            if (st != WDAD_OK) return st;
+        }
+        e = cudaMemcpyAsync(host_scores, d_out, sizeof(float) * (size_t)P * 3 * nwin, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "copy scores to host");
+        return WDAD_OK;
     } catch (...) {
         return fail(h, WDAD_ERR_NOMEM, "host exception");
     }

@@ -152,13 +152,17 @@ __device__ __forceinline__ void vertical_sums(const TileGeom& g, int i, int j, c
     const int wo = 2 * g.ro + 1, wi = 2 * g.ri + 1;
     const int plane_o = g.HR * TW, plane_i = (g.th + 2 * g.ri) * TW;
 #pragma unroll
-    for (int q = 0; q < NC; ++q) {
-        T s = T(0);
-        for (int dr = 0; dr < wo; ++dr) s += hso[q * plane_o + (i + dr) * TW + j];
-        So[q] = s;
-        T t = T(0);
-        for (int dr = 0; dr < wi; ++dr) t += hsi[q * plane_i + (i + dr) * TW + j];
-        Si[q] = t;
+    for (int q = 0; q < NC; ++q) { So[q] = T(0); Si[q] = T(0); }
+    // channels innermost: NC independent accumulation chains per row step
+    const T* po = hso + i * TW + j;
+    for (int dr = 0; dr < wo; ++dr, po += TW) {
+#pragma unroll
+        for (int q = 0; q < NC; ++q) So[q] += po[q * plane_o];
+    }
+    const T* pi = hsi + i * TW + j;
+    for (int dr = 0; dr < wi; ++dr, pi += TW) {
+#pragma unroll
+        for (int q = 0; q < NC; ++q) Si[q] += pi[q * plane_i];
     }
 }
 
@@ -203,15 +207,18 @@ __device__ __forceinline__ float chol_quad(const float (&G)[D][D], const float (
     return q;
 }
 
-// Cyclic Jacobi on a symmetric D x D matrix (symmetric Schur rotations).
-// On return A's diagonal holds the eigenvalues and V's columns the eigenvectors.
+// Cyclic Jacobi on a symmetric D x D matrix (symmetric Schur rotations, Golub &
+// Van Loan Sec. 8.5).  Each rotation zeroes a_pq, moves a_pp and a_qq by -/+ t a_pq
+// and rotates the other entries of rows/columns p and q; sweeps stop once the
+// off-diagonal mass reaches the FP32 rounding floor.  On return A's diagonal holds
+// the eigenvalues and V's columns the eigenvectors.
 template <int D>
 __device__ __forceinline__ void jacobi_inplace(float (&A)[D][D], float (&V)[D][D]) {
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
         for (int b = 0; b < D; ++b) V[a][b] = (a == b) ? 1.f : 0.f;
-    constexpr int kSweeps = (D <= 4) ? 10 : 15;
+    constexpr int kSweeps = (D <= 4) ? 8 : 12;
     for (int sweep = 0; sweep < kSweeps; ++sweep) {
         float off = 0.f, dia = 0.f;
 #pragma unroll
@@ -220,7 +227,7 @@ __device__ __forceinline__ void jacobi_inplace(float (&A)[D][D], float (&V)[D][D
 #pragma unroll
             for (int b = a + 1; b < D; ++b) off = fmaf(A[a][b], A[a][b], off);
         }
-        if (off <= 1e-16f * (dia + 2.f * off) || off == 0.f) break;
+        if (off <= 1e-13f * (dia + 2.f * off)) break;
 #pragma unroll
         for (int p = 0; p < D - 1; ++p)
 #pragma unroll
@@ -230,17 +237,17 @@ __device__ __forceinline__ void jacobi_inplace(float (&A)[D][D], float (&V)[D][D
                 const float theta = (A[q][q] - A[p][p]) / (2.f * apq);
                 const float t = copysignf(1.f, theta) / (fabsf(theta) + sqrtf(fmaf(theta, theta, 1.f)));
                 const float c = rsqrtf(fmaf(t, t, 1.f)), s = t * c;
+                A[p][p] = fmaf(-t, apq, A[p][p]);
+                A[q][q] = fmaf(t, apq, A[q][q]);
+                A[p][q] = 0.f;
+                A[q][p] = 0.f;
 #pragma unroll
                 for (int k = 0; k < D; ++k) {
+                    if (k == p || k == q) continue;
                     const float akp = A[k][p], akq = A[k][q];
-                    A[k][p] = c * akp - s * akq;
-                    A[k][q] = s * akp + c * akq;
-                }
-#pragma unroll
-                for (int k = 0; k < D; ++k) {
-                    const float apk = A[p][k], aqk = A[q][k];
-                    A[p][k] = c * apk - s * aqk;
-                    A[q][k] = s * apk + c * aqk;
+                    const float np = c * akp - s * akq, nq = s * akp + c * akq;
+                    A[k][p] = np; A[p][k] = np;
+                    A[k][q] = nq; A[q][k] = nq;
                 }
 #pragma unroll
                 for (int k = 0; k < D; ++k) {

@@ -59,10 +59,11 @@ def lib() -> ctypes.CDLL:
     L.wdad_dwt_approx.argtypes = [vp, f32p, i32, i32, i32, pp, f32p, ctypes.POINTER(i32), vp]
     L.wdad_detect.argtypes = [vp, f32p, i32, i32, i32, i32, i32, pp, f32p, vp, vp]
     L.wdad_detect_all.argtypes = [vp, f32p, i32, i32, i32, i32, pp, f32p, vp, vp]
+    L.wdad_detect_all_host.argtypes = [vp, vp, i32, i32, i32, i32, i32, pp, vp, vp]
     L.wdad_window_census.argtypes = [vp, i32, i32, pp, vp, vp]
     L.wdad_auc.argtypes = [vp, vp, i64, ctypes.POINTER(ctypes.c_double)]
     for name in ("wdad_create", "wdad_destroy", "wdad_last_error_detail", "wdad_dwt_approx", "wdad_detect",
-                 "wdad_detect_all", "wdad_window_census", "wdad_auc"):
+                 "wdad_detect_all", "wdad_detect_all_host", "wdad_window_census", "wdad_auc"):
         getattr(L, name).restype = i32
     L.wdad_query_K.restype = i32
     _lib = L
@@ -171,6 +172,27 @@ def wdad_detect_all(cube, reduce: bool = True, params: wdad_params | None = None
     h = handle(cube.device.index or 0)
     _check(lib().wdad_detect_all(h, cube.data_ptr(), H, W, L, int(bool(reduce)), ctypes.byref(p), out.data_ptr(),
                                  flags.data_ptr() if flags is not None else None, _stream(cube)), h)
+    return out
+
+
+def wdad_detect_all_host(cube, reduce: bool = True, params=None, out=None, device: int = 0, **over):
+    """Host-memory variant: cube is a CPU float32 tensor (pinned for asynchronous copies)
+    [H, W, L]; params a list of wdad_params (one per window pair).  Returns the host
+    tensor [nwin, 3, H, W].  Runs on torch's current stream of `device`; the call
+    returns once the work is enqueued, synchronise before reading the result."""
+    import torch
+    if not (isinstance(cube, torch.Tensor) and not cube.is_cuda and cube.dtype == torch.float32 and cube.dim() == 3):
+        raise TypeError("cube must be a CPU float32 tensor [H, W, L]")
+    cube = cube.contiguous()
+    plist = list(params) if params is not None else [_params(None, over)]
+    n = len(plist)
+    arr = (wdad_params * n)(*plist)
+    H, W, L = cube.shape
+    if out is None:
+        out = torch.empty((n, 3, H, W), dtype=torch.float32).pin_memory()
+    h = handle(device)
+    st = ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+    _check(lib().wdad_detect_all_host(h, cube.data_ptr(), H, W, L, int(bool(reduce)), n, arr, out.data_ptr(), st), h)
     return out
 
 

@@ -19,6 +19,19 @@ def relerr(got, want):
     return e
 
 
+def dwest_relerr(got, want, aux):
+    """DWEST error against max(|s_ref|, ||m_diff||): Eq. 4 adds signed projections of
+    m_diff, so a near-cancelling sum is far smaller than the terms the FP32 path
+    rounds; the error is measured on the scale of those terms."""
+    got = np.asarray(got, dtype=np.float64)
+    want = np.asarray(want, dtype=np.float64)
+    den = np.maximum(np.abs(want), np.asarray(aux)[..., 4])
+    e = np.abs(got - want) / np.maximum(den, 1e-300)
+    e[np.isnan(got) & np.isnan(want)] = 0.0
+    e[np.isnan(got) ^ np.isnan(want)] = np.inf
+    return e
+
+
 def dwest_ok_mask(aux, sel_margin=1e-4, sign_margin=1e-3, gap=1e-3):
     """Pixels whose DWEST score is well determined in FP32: no eigenvalue within
     sel_margin * max|lambda| of the threshold, the two largest entries of every

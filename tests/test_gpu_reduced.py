@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 import oracle
-from parity import TOL_DWT, TOL_SCORE, dwest_ok_mask, relerr
+from parity import TOL_DWT, TOL_SCORE, dwest_ok_mask, dwest_relerr, relerr
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -89,7 +89,7 @@ def _check_scene(wd, cube, win, loading=1e-3, dwest_mode=0, label=""):
         assert e.max() <= TOL_SCORE, f"{label} det {det} win {win}: max rel err {e.max():.3g}"
     want, aux = oracle.detect(a, 2, win[0], win[1], dwest_mode=dwest_mode, want_aux=True)
     ok = dwest_ok_mask(aux)
-    e = relerr(got[2], want)
+    e = dwest_relerr(got[2], want, aux)
     assert ok.mean() > 0.9, f"{label}: only {ok.mean():.3f} of DWEST pixels are well determined"
     assert e[ok].max() <= TOL_SCORE, f"{label} DWEST win {win}: max rel err {e[ok].max():.3g} ({(~ok).sum()} excluded)"
     return got
@@ -124,7 +124,8 @@ def test_few_band_cube_direct(wd, D):
     # reduce=0 on a D-band cube runs the same kernel for every template dimension
     rng = np.random.default_rng(D)
     H, W = 29, 45
-    cube = (rng.standard_normal((H, W, D)) @ rng.standard_normal((D, D)) * 0.2 + 1.0).astype(np.float32)
+    mix = np.eye(D) + 0.3 * rng.standard_normal((D, D))  # well-conditioned band mixing
+    cube = (0.2 * rng.standard_normal((H, W, D)) @ mix + 1.0).astype(np.float32)
     got = wd.wdad_detect_all(_gpu(cube), reduce=False, inner=3, outer=9).cpu().numpy()
     for det in (0, 1):
         want = oracle.detect(cube, det, 3, 9)
@@ -133,7 +134,7 @@ def test_few_band_cube_direct(wd, D):
     want, aux = oracle.detect(cube, 2, 3, 9, want_aux=True)
     ok = dwest_ok_mask(aux)
     assert ok.mean() > 0.8
-    assert relerr(got[2], want)[ok].max() <= TOL_SCORE
+    assert dwest_relerr(got[2], want, aux)[ok].max() <= TOL_SCORE
 
 
 def test_valid_border_mode(wd, scene48):
@@ -210,4 +211,16 @@ def test_reduced_detectors_512_sampled(wd, scene512, win):
     want, aux = oracle.detect(a, 2, win[0], win[1], pixels=pix, want_aux=True)
     ok = dwest_ok_mask(aux)
     assert ok.mean() > 0.9
-    assert relerr(got[2].ravel()[pix], want)[ok].max() <= TOL_SCORE
+    assert dwest_relerr(got[2].ravel()[pix], want, aux)[ok].max() <= TOL_SCORE
+
+
+def test_host_entry_point_matches_device_path(wd, scene48):
+    hc = torch.from_numpy(scene48.cube).pin_memory()
+    wins = [(3, 9), (5, 15)]
+    params = [wd.wdad_default_params(inner=a, outer=b) for a, b in wins]
+    out = wd.wdad_detect_all_host(hc, params=params)
+    torch.cuda.synchronize()
+    x = _gpu(scene48.cube)
+    for i, (a, b) in enumerate(wins):
+        dev = wd.wdad_detect_all(x, reduce=True, inner=a, outer=b).cpu()
+        assert torch.equal(out[i], dev)
