@@ -106,18 +106,24 @@ def _dist():
     return ws, rank, local
 
 
-def cpu_oracle_sample(cube: np.ndarray, rows: int):
-    """Time the FP64 oracle (as it stands) on the first `rows` rows of the cube:
-    DWT plus the three detectors at the three windows.  Returns (pixel-windows/s, seconds)."""
+def cpu_oracle_sample(cube: np.ndarray, rows: int, min_seconds: float = 0.0):
+    """Time the FP64 oracle (as it stands) on the first `rows` rows of the cube: DWT
+    plus the three detectors at the three windows, repeated until min_seconds have
+    passed.  Returns (pixel-windows/s, seconds, repetitions)."""
     import oracle
     sub = np.ascontiguousarray(cube[:rows])
     t0 = time.perf_counter()
-    a = oracle.dwt_approx(sub)
-    for wi, wo in WINDOWS:
-        for det in range(3):
-            oracle.detect(a, det, wi, wo)
-    dt = time.perf_counter() - t0
-    return 3 * sub.shape[0] * sub.shape[1] / dt, dt
+    reps = 0
+    while True:
+        a = oracle.dwt_approx(sub)
+        for wi, wo in WINDOWS:
+            for det in range(3):
+                oracle.detect(a, det, wi, wo)
+        reps += 1
+        dt = time.perf_counter() - t0
+        if dt >= min_seconds:
+            break
+    return reps * 3 * sub.shape[0] * sub.shape[1] / dt, dt, reps
 
 
 def run_reference(args):
@@ -132,7 +138,7 @@ def run_reference(args):
         cpu_oracle_sample(sc.cube, rows)
     times = []
     for _ in range(args.steps):
-        _, dt = cpu_oracle_sample(sc.cube, rows)
+        _, dt, _ = cpu_oracle_sample(sc.cube, rows)
         times.append(dt)
     per_step = sum(times) / len(times)
     v = 3 * rows * W / per_step / 1e6
@@ -257,10 +263,10 @@ def run_ours(args):
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         import oracle
-        v, dt = cpu_oracle_sample(sc.cube, args.cpu_rows)
+        v, dt, reps = cpu_oracle_sample(sc.cube, args.cpu_rows, args.cpu_seconds)
         cpu = {"value": v / 1e6, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-               "sample": f"rows 0..{args.cpu_rows - 1} of the cube ({args.cpu_rows * W} px), 3 windows x 3 "
-                         f"detectors, FP64, {dt:.1f} s"}
+               "sample": f"rows 0..{args.cpu_rows - 1} of the cube ({args.cpu_rows * W} px) x {reps} repetitions, "
+                         f"DWT + 3 windows x 3 detectors, FP64, {dt:.1f} s"}
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -284,7 +290,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=40)
-    ap.add_argument("--cpu-rows", type=int, default=128)
+    ap.add_argument("--cpu-rows", type=int, default=512)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-rows", type=int, default=16)
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()

@@ -8,10 +8,13 @@
 //           pixels is subtracted, so the second moments below are sums of
 //           (x - c)(x - c)^T with little cancellation;
 //  stage 2  horizontal box sums over the outer and the inner window width of the
-//           D first-order and D(D+1)/2 second-order channels, per halo row;
-//  stage 3  vertical box sums of those, per output pixel: sums over the outer
-//           square and over the inner square; the background annulus is outer
-//           minus inner (Sec. 2.2 dual window);
+//           D first-order and D(D+1)/2 second-order channels: one thread per halo
+//           row and 8-column segment, a direct sum for the first column and a
+//           sliding update (add the entering, subtract the leaving column) after;
+//  stage 3  vertical box sums of those, one thread per (channel, column) sliding
+//           down the tile rows, written in place over the horizontal sums: sums
+//           over the outer square and over the inner square; the background
+//           annulus is outer minus inner (Sec. 2.2 dual window);
 //  stage 4  per pixel: mu_o, C_o (1/N), mu_i, C_i (1/n_i); LRX (Eq. 1) and DWRX
 //           (Eq. 5) through a Cholesky factor of C_o + delta I, delta =
 //           loading * trace(C_o) / D; DWEST (Eq. 2-4) through a cyclic Jacobi
@@ -29,16 +32,24 @@ namespace wdad {
 constexpr int TW = 32;          // tile width = one warp across
 constexpr int kMaxSmem = 227 * 1024;
 
+constexpr int SEG = 8;          // output columns per stage-2 thread
+constexpr int HP = TW + 1;      // row pitch of the sum planes (words): conflict-free column access
+
+__host__ __device__ __forceinline__ int halo_pitch(int WR) { return WR | 1; }  // odd pixel pitch
+
 struct TileGeom {
     int H, W, ro, ri, th;        // image, radii, tile height
     int ty0, tx0;                // tile origin
-    int HR, WR;                  // halo region rows / cols
+    int HR, WR, XP;              // halo region rows / cols, halo row pitch in pixels
+    int nin;                     // halo rows that carry inner sums
     __device__ TileGeom(int H_, int W_, int inner, int outer, int th_)
         : H(H_), W(W_), ro(outer / 2), ri(inner / 2), th(th_) {
         ty0 = blockIdx.y * th;
         tx0 = blockIdx.x * TW;
         HR = th + 2 * ro;
         WR = TW + 2 * ro;
+        XP = halo_pitch(WR);
+        nin = th + 2 * ri;
     }
 };
 
@@ -80,7 +91,7 @@ __device__ __forceinline__ void load_halo_spec(const TileGeom& g, const float* _
         const int gy = reflect101(g.ty0 - g.ro + r, g.H);
         const int gx = reflect101(g.tx0 - g.ro + c, g.W);
         const float* src = x + ((size_t)gy * g.W + gx) * D;
-        float* dst = xs + (size_t)idx * P::DP;
+        float* dst = xs + ((size_t)r * g.XP + c) * P::DP;
         if constexpr (D == 4) {
             const float4 v = __ldg(reinterpret_cast<const float4*>(src));
             *reinterpret_cast<float4*>(dst) = v;
@@ -102,67 +113,87 @@ __device__ __forceinline__ void load_halo_census(const TileGeom& g, long long* x
         const int r = idx / g.WR, c = idx - r * g.WR;
         const int gy = reflect101(g.ty0 - g.ro + r, g.H);
         const int gx = reflect101(g.tx0 - g.ro + c, g.W);
-        xs[idx] = (long long)gy * g.W + gx;
+        xs[(size_t)r * g.XP + c] = (long long)gy * g.W + gx;
     }
 }
 
 // ---------------------------------------------------------------- stage 2: horizontal sums
 // hso[ch][r][j] = sum over the outer width of channel ch at halo row r, output column j;
-// hsi[ch][r'][j] = the same over the inner width for the th + 2 ri rows the inner squares use.
+// hsi[ch][r'][j] = the same over the inner width for the th + 2 ri halo rows the inner
+// squares use (r' = r - (ro - ri)).  Thread (r, seg) owns SEG consecutive output columns
+// of one halo row: a direct sum for the first, then sliding updates.
 template <class P, class ChanFn>
 __device__ __forceinline__ void horizontal_sums(const TileGeom& g, ChanFn chan, typename P::T* hso,
                                                 typename P::T* hsi) {
     using T = typename P::T;
     constexpr int NC = P::NC;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int wo = 2 * g.ro + 1, i0 = g.ro - g.ri, i1 = g.ro + g.ri;  // inner columns dc in [i0, i1]
-    const int rin0 = g.ro - g.ri, nin = g.th + 2 * g.ri;               // inner halo rows
-    const int plane_o = g.HR * TW, plane_i = nin * TW;
-    for (int r = warp; r < g.HR; r += nw) {
-        T so[NC], si[NC];
+    const int rin0 = g.ro - g.ri;
+    const int plane_o = g.HR * HP, plane_i = g.nin * HP;
+    const int nwork = g.HR * (TW / SEG);
+    for (int t = threadIdx.x; t < nwork; t += blockDim.x) {
+        const int r = t % g.HR, j0 = (t / g.HR) * SEG;
+        const bool inner_row = (r >= rin0) && (r < rin0 + g.nin);
+        T so[NC], si[NC], ch[NC], c2[NC];
 #pragma unroll
         for (int q = 0; q < NC; ++q) { so[q] = T(0); si[q] = T(0); }
-        const bool need_inner = (r >= rin0) && (r < rin0 + nin);
         for (int dc = 0; dc < wo; ++dc) {
-            T ch[NC];
-            chan(r, lane + dc, ch);
+            chan(r, j0 + dc, ch);
 #pragma unroll
             for (int q = 0; q < NC; ++q) so[q] += ch[q];
-            if (need_inner && dc >= i0 && dc <= i1) {
+            if (inner_row && dc >= i0 && dc <= i1) {
 #pragma unroll
                 for (int q = 0; q < NC; ++q) si[q] += ch[q];
             }
         }
+        T* po = hso + r * HP + j0;
+        T* pi = hsi + (r - rin0) * HP + j0;
 #pragma unroll
-        for (int q = 0; q < NC; ++q) hso[q * plane_o + r * TW + lane] = so[q];
-        if (need_inner) {
+        for (int q = 0; q < NC; ++q) po[q * plane_o] = so[q];
+        if (inner_row) {
 #pragma unroll
-            for (int q = 0; q < NC; ++q) hsi[q * plane_i + (r - rin0) * TW + lane] = si[q];
+            for (int q = 0; q < NC; ++q) pi[q * plane_i] = si[q];
+        }
+        for (int jj = 1; jj < SEG; ++jj) {
+            const int j = j0 + jj;
+            chan(r, j + wo - 1, ch);  // entering column
+            chan(r, j - 1, c2);       // leaving column
+#pragma unroll
+            for (int q = 0; q < NC; ++q) { so[q] += ch[q]; so[q] -= c2[q]; po[q * plane_o + jj] = so[q]; }
+            if (inner_row) {
+                chan(r, j + i1, ch);
+                chan(r, j - 1 + i0, c2);
+#pragma unroll
+                for (int q = 0; q < NC; ++q) { si[q] += ch[q]; si[q] -= c2[q]; pi[q * plane_i + jj] = si[q]; }
+            }
         }
     }
 }
 
-// ---------------------------------------------------------------- stage 3: vertical sums
+// ---------------------------------------------------------------- stage 3: vertical sums, in place
+// Thread (ch, j) slides down the tile rows: afterwards hso[ch][i][j] holds the sum over
+// the outer square of output pixel (i, j) and hsi[ch][i][j] the sum over its inner square.
 template <class P>
-__device__ __forceinline__ void vertical_sums(const TileGeom& g, int i, int j, const typename P::T* hso,
-                                              const typename P::T* hsi, typename P::T (&So)[P::NC],
-                                              typename P::T (&Si)[P::NC]) {
+__device__ __forceinline__ void vertical_sums_inplace(const TileGeom& g, typename P::T* hso, typename P::T* hsi) {
     using T = typename P::T;
     constexpr int NC = P::NC;
     const int wo = 2 * g.ro + 1, wi = 2 * g.ri + 1;
-    const int plane_o = g.HR * TW, plane_i = (g.th + 2 * g.ri) * TW;
-#pragma unroll
-    for (int q = 0; q < NC; ++q) { So[q] = T(0); Si[q] = T(0); }
-    // channels innermost: NC independent accumulation chains per row step
-    const T* po = hso + i * TW + j;
-    for (int dr = 0; dr < wo; ++dr, po += TW) {
-#pragma unroll
-        for (int q = 0; q < NC; ++q) So[q] += po[q * plane_o];
-    }
-    const T* pi = hsi + i * TW + j;
-    for (int dr = 0; dr < wi; ++dr, pi += TW) {
-#pragma unroll
-        for (int q = 0; q < NC; ++q) Si[q] += pi[q * plane_i];
+    const int plane_o = g.HR * HP, plane_i = g.nin * HP;
+    for (int t = threadIdx.x; t < 2 * NC * TW; t += blockDim.x) {
+        const int j = t % TW, qq = t / TW;
+        const bool outer = qq < NC;
+        const int q = outer ? qq : qq - NC;
+        T* h = outer ? hso + q * plane_o + j : hsi + q * plane_i + j;
+        const int w = outer ? wo : wi;
+        T s = T(0);
+        for (int dr = 0; dr < w; ++dr) s += h[dr * HP];
+        for (int i = 1; i < g.th; ++i) {
+            const T leave = h[(i - 1) * HP], enter = h[(i + w - 1) * HP];
+            h[(i - 1) * HP] = s;
+            s += enter;
+            s -= leave;
+        }
+        h[(g.th - 1) * HP] = s;
     }
 }
 
@@ -209,8 +240,9 @@ __device__ __forceinline__ float chol_quad(const float (&G)[D][D], const float (
 
 // Cyclic Jacobi on a symmetric D x D matrix (symmetric Schur rotations, Golub &
 // Van Loan Sec. 8.5).  Each rotation zeroes a_pq, moves a_pp and a_qq by -/+ t a_pq
-// and rotates the other entries of rows/columns p and q; sweeps stop once the
-// off-diagonal mass reaches the FP32 rounding floor.  On return A's diagonal holds
+// and rotates the other entries of rows/columns p and q.  Off-diagonal entries at or
+// below the FP32 rounding level of the matrix (2^-22 ||A||_F) are left alone, and the
+// sweeps end with the first sweep that rotates nothing.  On return A's diagonal holds
 // the eigenvalues and V's columns the eigenvectors.
 template <int D>
 __device__ __forceinline__ void jacobi_inplace(float (&A)[D][D], float (&V)[D][D]) {
@@ -218,24 +250,24 @@ __device__ __forceinline__ void jacobi_inplace(float (&A)[D][D], float (&V)[D][D
     for (int a = 0; a < D; ++a)
 #pragma unroll
         for (int b = 0; b < D; ++b) V[a][b] = (a == b) ? 1.f : 0.f;
+    float fro = 0.f;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = 0; b < D; ++b) fro = fmaf(A[a][b], A[a][b], fro);
+    const float tol = 2.384185791e-7f * sqrtf(fro);  // 2^-22 ||A||_F
     constexpr int kSweeps = (D <= 4) ? 8 : 12;
     for (int sweep = 0; sweep < kSweeps; ++sweep) {
-        float off = 0.f, dia = 0.f;
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-            dia = fmaf(A[a][a], A[a][a], dia);
-#pragma unroll
-            for (int b = a + 1; b < D; ++b) off = fmaf(A[a][b], A[a][b], off);
-        }
-        if (off <= 1e-13f * (dia + 2.f * off)) break;
+        bool rotated = false;
 #pragma unroll
         for (int p = 0; p < D - 1; ++p)
 #pragma unroll
             for (int q = p + 1; q < D; ++q) {
                 const float apq = A[p][q];
-                if (apq == 0.f) continue;
-                const float theta = (A[q][q] - A[p][p]) / (2.f * apq);
-                const float t = copysignf(1.f, theta) / (fabsf(theta) + sqrtf(fmaf(theta, theta, 1.f)));
+                if (!(fabsf(apq) > tol)) continue;
+                rotated = true;
+                const float theta = (A[q][q] - A[p][p]) * __frcp_rn(2.f * apq);
+                const float t = copysignf(__frcp_rn(fabsf(theta) + sqrtf(fmaf(theta, theta, 1.f))), theta);
                 const float c = rsqrtf(fmaf(t, t, 1.f)), s = t * c;
                 A[p][p] = fmaf(-t, apq, A[p][p]);
                 A[q][q] = fmaf(t, apq, A[q][q]);
@@ -256,6 +288,7 @@ __device__ __forceinline__ void jacobi_inplace(float (&A)[D][D], float (&V)[D][D
                     V[k][q] = s * vkp + c * vkq;
                 }
             }
+        if (!rotated) break;
     }
 }
 
@@ -266,10 +299,9 @@ __global__ void __launch_bounds__(512) detect_small_kernel(DetectArgs a, int th)
     constexpr int NC = P::NC;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const TileGeom g(a.H, a.W, a.inner, a.outer, th);
-    const int nin = th + 2 * g.ri;
     float* xs = reinterpret_cast<float*>(smem_raw);
-    float* hso = xs + (size_t)g.HR * g.WR * P::DP;
-    float* hsi = hso + (size_t)NC * g.HR * TW;
+    float* hso = xs + (size_t)g.HR * g.XP * P::DP;
+    float* hsi = hso + (size_t)NC * g.HR * HP;
     __shared__ float red[16][8];
     __shared__ float cref[8];
 
@@ -298,7 +330,8 @@ __global__ void __launch_bounds__(512) detect_small_kernel(DetectArgs a, int th)
         for (int k = 0; k < D; ++k) c[k] = cref[k];
         const int n = g.HR * g.WR;
         for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-            float* v = xs + (size_t)idx * P::DP;
+            const int r = idx / g.WR, cc = idx - r * g.WR;
+            float* v = xs + ((size_t)r * g.XP + cc) * P::DP;
 #pragma unroll
             for (int k = 0; k < D; ++k) v[k] -= c[k];
         }
@@ -306,7 +339,7 @@ __global__ void __launch_bounds__(512) detect_small_kernel(DetectArgs a, int th)
     __syncthreads();
     // stage 2
     auto chan = [&](int r, int col, float (&ch)[NC]) {
-        const float* v = xs + ((size_t)r * g.WR + col) * P::DP;
+        const float* v = xs + ((size_t)r * g.XP + col) * P::DP;
         float t[D];
         if constexpr (D == 4) {
             const float4 q = *reinterpret_cast<const float4*>(v);
@@ -319,8 +352,10 @@ __global__ void __launch_bounds__(512) detect_small_kernel(DetectArgs a, int th)
     };
     horizontal_sums<P>(g, chan, hso, hsi);
     __syncthreads();
+    vertical_sums_inplace<P>(g, hso, hsi);
+    __syncthreads();
 
-    // stages 3 + 4, one pixel per thread and step
+    // stage 4, one pixel per thread and step
     const int N = (2 * g.ro + 1) * (2 * g.ro + 1) - (2 * g.ri + 1) * (2 * g.ri + 1);
     const int ni = (2 * g.ri + 1) * (2 * g.ri + 1);
     const float invN = 1.0f / (float)N, invni = 1.0f / (float)ni;
@@ -337,8 +372,11 @@ __global__ void __launch_bounds__(512) detect_small_kernel(DetectArgs a, int th)
             continue;
         }
         float So[NC], Si[NC];
-        vertical_sums<P>(g, i, j, hso, hsi, So, Si);
-        (void)nin;
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+            So[q] = hso[q * g.HR * HP + i * HP + j];
+            Si[q] = hsi[q * g.nin * HP + i * HP + j];
+        }
         float mo[D], mi[D], Co[D][D];
 #pragma unroll
         for (int k = 0; k < D; ++k) {
@@ -377,7 +415,7 @@ __global__ void __launch_bounds__(512) detect_small_kernel(DetectArgs a, int th)
             const bool ok = chol_inplace<D>(G, 16.f * FLT_EPSILON * smax);
             if (!ok) flag |= 2;
             if (a.out[0]) {
-                const float* rc = xs + ((size_t)(i + g.ro) * g.WR + (j + g.ro)) * P::DP;  // shifted centre pixel
+                const float* rc = xs + ((size_t)(i + g.ro) * g.XP + (j + g.ro)) * P::DP;  // shifted centre pixel
                 float d[D];
 #pragma unroll
                 for (int k = 0; k < D; ++k) d[k] = rc[k] - mo[k];
@@ -436,15 +474,17 @@ __global__ void __launch_bounds__(512) census_kernel(int H, int W, int inner, in
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const TileGeom g(H, W, inner, outer, th);
     long long* xs = reinterpret_cast<long long*>(smem_raw);
-    long long* hso = xs + (size_t)g.HR * g.WR;
-    long long* hsi = hso + (size_t)P::NC * g.HR * TW;
+    long long* hso = xs + (size_t)g.HR * g.XP;
+    long long* hsi = hso + (size_t)P::NC * g.HR * HP;
     load_halo_census(g, xs);
     __syncthreads();
     auto chan = [&](int r, int col, long long (&ch)[3]) {
-        const long long q = xs[(size_t)r * g.WR + col];
+        const long long q = xs[(size_t)r * g.XP + col];
         ch[0] = 1; ch[1] = q; ch[2] = q * q;
     };
     horizontal_sums<P>(g, chan, hso, hsi);
+    __syncthreads();
+    vertical_sums_inplace<P>(g, hso, hsi);
     __syncthreads();
     for (int pix = threadIdx.x; pix < th * TW; pix += blockDim.x) {
         const int i = pix / TW, j = pix - i * TW;
@@ -456,7 +496,10 @@ __global__ void __launch_bounds__(512) census_kernel(int H, int W, int inner, in
             continue;
         }
         long long So[3], Si[3];
-        vertical_sums<P>(g, i, j, hso, hsi, So, Si);
+        for (int q = 0; q < 3; ++q) {
+            So[q] = hso[q * g.HR * HP + i * HP + j];
+            Si[q] = hsi[q * g.nin * HP + i * HP + j];
+        }
         o[0] = So[0] - Si[0]; o[1] = So[1] - Si[1]; o[2] = So[2] - Si[2];
         o[3] = Si[0]; o[4] = Si[1]; o[5] = Si[2];
     }
@@ -465,8 +508,8 @@ __global__ void __launch_bounds__(512) census_kernel(int H, int W, int inner, in
 // ---------------------------------------------------------------- launchers
 static size_t smem_bytes(int words_per_px, int nc, int tsize, int inner, int outer, int th) {
     const int ro = outer / 2, ri = inner / 2;
-    const size_t HR = th + 2 * ro, WR = TW + 2 * ro;
-    return HR * WR * words_per_px * 4 + (size_t)nc * HR * TW * tsize + (size_t)nc * (th + 2 * ri) * TW * tsize;
+    const size_t HR = th + 2 * ro, XP = halo_pitch(TW + 2 * ro);
+    return HR * XP * words_per_px * 4 + (size_t)nc * HR * HP * tsize + (size_t)nc * (th + 2 * ri) * HP * tsize;
 }
 
 static int spec_nc(int D) { return D + D * (D + 1) / 2; }

@@ -32,7 +32,7 @@ def dwest_relerr(got, want, aux):
     return e
 
 
-def dwest_ok_mask(aux, sel_margin=1e-4, sign_margin=1e-3, gap=1e-3):
+def dwest_ok_mask(aux, sel_margin=1e-4, sign_margin=1e-3, gap=1e-2):
     """Pixels whose DWEST score is well determined in FP32: no eigenvalue within
     sel_margin * max|lambda| of the threshold, the two largest entries of every
     selected eigenvector apart by sign_margin, and selected eigenvalues separated
