@@ -9,6 +9,7 @@ namespace wdad {
 
 // Device-side reflect-101 (-1 -> 1, n -> n-2), valid for any integer i.
 __host__ __device__ __forceinline__ int reflect101(int i, int n) {
+    if ((unsigned)i < (unsigned)n) return i;  // interior: no arithmetic
     if (n == 1) return 0;
     const int period = 2 * (n - 1);
     int r = i % period;

@@ -238,18 +238,31 @@ __device__ __forceinline__ float chol_quad(const float (&G)[D][D], const float (
     return q;
 }
 
-// Cyclic Jacobi on a symmetric D x D matrix (symmetric Schur rotations, Golub &
-// Van Loan Sec. 8.5).  Each rotation zeroes a_pq, moves a_pp and a_qq by -/+ t a_pq
-// and rotates the other entries of rows/columns p and q.  Off-diagonal entries at or
-// below the FP32 rounding level of the matrix (2^-22 ||A||_F) are left alone, and the
-// sweeps end with the first sweep that rotates nothing.  On return A's diagonal holds
-// the eigenvalues and V's columns the eigenvectors.
+// Round-robin (circle method) pairing of D indices, D padded to an even count E:
+// round r pairs slot 0 with slot 1 + r and slot 1 + (r + k) % (E - 1) with slot
+// 1 + (r - k + E - 1) % (E - 1), k = 1 .. E/2 - 1.  Index E - 1 >= D is a bye.
+__host__ __device__ constexpr int rr_first(int E, int r, int k) { return k == 0 ? 0 : 1 + (r + k) % (E - 1); }
+__host__ __device__ constexpr int rr_second(int E, int r, int k) {
+    return k == 0 ? 1 + r : 1 + (r - k + E - 1) % (E - 1);
+}
+
+// Parallel-order Jacobi on a symmetric D x D matrix (symmetric Schur rotations,
+// Golub & Van Loan Sec. 8.5; the round-robin ordering lets the rotations of one
+// round, which act on disjoint index pairs, be computed and applied together).
+// Each rotation zeroes a_pq and moves a_pp, a_qq by -/+ t a_pq; the blocks between
+// two pairs transform as R_i^T B R_j.  Entries at or below the FP32 rounding level of
+// the matrix (2^-22 ||A||_F) are left alone; sweeps end with the first sweep that
+// rotates nothing.  On return A's diagonal holds the eigenvalues, V's columns the
+// eigenvectors.
 template <int D>
 __device__ __forceinline__ void jacobi_inplace(float (&A)[D][D], float (&V)[D][D]) {
+    constexpr int E = D + (D & 1);
+    constexpr int M = E / 2;
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
         for (int b = 0; b < D; ++b) V[a][b] = (a == b) ? 1.f : 0.f;
+    if constexpr (D == 1) return;
     float fro = 0.f;
 #pragma unroll
     for (int a = 0; a < D; ++a)
@@ -260,34 +273,73 @@ __device__ __forceinline__ void jacobi_inplace(float (&A)[D][D], float (&V)[D][D
     for (int sweep = 0; sweep < kSweeps; ++sweep) {
         bool rotated = false;
 #pragma unroll
-        for (int p = 0; p < D - 1; ++p)
+        for (int r = 0; r < E - 1; ++r) {
+            float c[M], sn[M];
+            // rotation parameters of every pair of the round, from the same A
 #pragma unroll
-            for (int q = p + 1; q < D; ++q) {
+            for (int k = 0; k < M; ++k) {
+                const int p0 = rr_first(E, r, k), q0 = rr_second(E, r, k);
+                const int p = p0 < q0 ? p0 : q0, q = p0 < q0 ? q0 : p0;
+                c[k] = 1.f; sn[k] = 0.f;
+                if (q >= D) continue;
                 const float apq = A[p][q];
                 if (!(fabsf(apq) > tol)) continue;
                 rotated = true;
                 const float theta = (A[q][q] - A[p][p]) * __frcp_rn(2.f * apq);
                 const float t = copysignf(__frcp_rn(fabsf(theta) + sqrtf(fmaf(theta, theta, 1.f))), theta);
-                const float c = rsqrtf(fmaf(t, t, 1.f)), s = t * c;
+                c[k] = rsqrtf(fmaf(t, t, 1.f));
+                sn[k] = t * c[k];
                 A[p][p] = fmaf(-t, apq, A[p][p]);
                 A[q][q] = fmaf(t, apq, A[q][q]);
                 A[p][q] = 0.f;
                 A[q][p] = 0.f;
+            }
+            // blocks between two pairs: B <- R_i^T B R_j (and the transposed block)
 #pragma unroll
-                for (int k = 0; k < D; ++k) {
-                    if (k == p || k == q) continue;
-                    const float akp = A[k][p], akq = A[k][q];
-                    const float np = c * akp - s * akq, nq = s * akp + c * akq;
-                    A[k][p] = np; A[p][k] = np;
-                    A[k][q] = nq; A[q][k] = nq;
+            for (int i = 0; i < M; ++i)
+#pragma unroll
+                for (int j = i + 1; j < M; ++j) {
+                    const int pi0 = rr_first(E, r, i), qi0 = rr_second(E, r, i);
+                    const int pj0 = rr_first(E, r, j), qj0 = rr_second(E, r, j);
+                    const int pi = pi0 < qi0 ? pi0 : qi0, qi = pi0 < qi0 ? qi0 : pi0;
+                    const int pj = pj0 < qj0 ? pj0 : qj0, qj = pj0 < qj0 ? qj0 : pj0;
+                    if (qi >= D && qj >= D) continue;
+                    if (qi >= D) {  // pi is single: row vector A[pi][{pj,qj}] <- . R_j
+                        const float x = A[pi][pj], y = A[pi][qj];
+                        const float nx = c[j] * x - sn[j] * y, ny = sn[j] * x + c[j] * y;
+                        A[pi][pj] = nx; A[pj][pi] = nx; A[pi][qj] = ny; A[qj][pi] = ny;
+                        continue;
+                    }
+                    if (qj >= D) {  // pj is single: column A[{pi,qi}][pj] <- R_i^T .
+                        const float x = A[pi][pj], y = A[qi][pj];
+                        const float nx = c[i] * x - sn[i] * y, ny = sn[i] * x + c[i] * y;
+                        A[pi][pj] = nx; A[pj][pi] = nx; A[qi][pj] = ny; A[pj][qi] = ny;
+                        continue;
+                    }
+                    const float b00 = A[pi][pj], b01 = A[pi][qj], b10 = A[qi][pj], b11 = A[qi][qj];
+                    // columns: B R_j
+                    const float e00 = c[j] * b00 - sn[j] * b01, e01 = sn[j] * b00 + c[j] * b01;
+                    const float e10 = c[j] * b10 - sn[j] * b11, e11 = sn[j] * b10 + c[j] * b11;
+                    // rows: R_i^T (B R_j)
+                    const float f00 = c[i] * e00 - sn[i] * e10, f10 = sn[i] * e00 + c[i] * e10;
+                    const float f01 = c[i] * e01 - sn[i] * e11, f11 = sn[i] * e01 + c[i] * e11;
+                    A[pi][pj] = f00; A[pj][pi] = f00; A[pi][qj] = f01; A[qj][pi] = f01;
+                    A[qi][pj] = f10; A[pj][qi] = f10; A[qi][qj] = f11; A[qj][qi] = f11;
                 }
+            // eigenvectors: V <- V J
 #pragma unroll
-                for (int k = 0; k < D; ++k) {
-                    const float vkp = V[k][p], vkq = V[k][q];
-                    V[k][p] = c * vkp - s * vkq;
-                    V[k][q] = s * vkp + c * vkq;
+            for (int k = 0; k < M; ++k) {
+                const int p0 = rr_first(E, r, k), q0 = rr_second(E, r, k);
+                const int p = p0 < q0 ? p0 : q0, q = p0 < q0 ? q0 : p0;
+                if (q >= D) continue;
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    const float vp = V[a][p], vq = V[a][q];
+                    V[a][p] = c[k] * vp - sn[k] * vq;
+                    V[a][q] = sn[k] * vp + c[k] * vq;
                 }
             }
+        }
         if (!rotated) break;
     }
 }
@@ -519,7 +571,11 @@ size_t detect_small_smem(int D, int inner, int outer, int tile_h) {
     return smem_bytes(spec_dp(D), spec_nc(D), 4, inner, outer, tile_h);
 }
 
+// Tallest tile (<= want) that lets two CTAs share an SM; else the tallest that fits one.
 static int pick_th(int D, int inner, int outer, int want) {
+    constexpr size_t kTwoPerSm = 113 * 1024;
+    for (int th = want; th >= 8; th >>= 1)
+        if (detect_small_smem(D, inner, outer, th) <= kTwoPerSm) return th;
     for (int th = want; th >= 1; th >>= 1)
         if (detect_small_smem(D, inner, outer, th) <= (size_t)kMaxSmem) return th;
     return 0;
