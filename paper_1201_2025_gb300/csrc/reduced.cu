@@ -86,17 +86,39 @@ __device__ __forceinline__ void load_halo_spec(const TileGeom& g, const float* _
     const int n = g.HR * g.WR;
 #pragma unroll
     for (int k = 0; k < D; ++k) part[k] = 0.f;
-    for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-        const int r = idx / g.WR, c = idx - r * g.WR;
-        const int gy = reflect101(g.ty0 - g.ro + r, g.H);
-        const int gx = reflect101(g.tx0 - g.ro + c, g.W);
-        const float* src = x + ((size_t)gy * g.W + gx) * D;
-        float* dst = xs + ((size_t)r * g.XP + c) * P::DP;
-        if constexpr (D == 4) {
-            const float4 v = __ldg(reinterpret_cast<const float4*>(src));
-            *reinterpret_cast<float4*>(dst) = v;
-            part[0] += v.x; part[1] += v.y; part[2] += v.z; part[3] += v.w;
-        } else {
+    if constexpr (D == 4) {
+        // eight 16-byte loads in flight per thread before any is stored
+        constexpr int B = 8;
+        for (int base = threadIdx.x; base < n; base += B * blockDim.x) {
+            float4 v[B];
+            int dsti[B];
+#pragma unroll
+            for (int u = 0; u < B; ++u) {
+                const int idx = base + u * blockDim.x;
+                dsti[u] = -1;
+                v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (idx < n) {
+                    const int r = idx / g.WR, c = idx - r * g.WR;
+                    const int gy = reflect101(g.ty0 - g.ro + r, g.H);
+                    const int gx = reflect101(g.tx0 - g.ro + c, g.W);
+                    v[u] = __ldg(reinterpret_cast<const float4*>(x + ((size_t)gy * g.W + gx) * 4));
+                    dsti[u] = r * g.XP + c;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < B; ++u)
+                if (dsti[u] >= 0) {
+                    *reinterpret_cast<float4*>(xs + (size_t)dsti[u] * P::DP) = v[u];
+                    part[0] += v[u].x; part[1] += v[u].y; part[2] += v[u].z; part[3] += v[u].w;
+                }
+        }
+    } else {
+        for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
+            const int r = idx / g.WR, c = idx - r * g.WR;
+            const int gy = reflect101(g.ty0 - g.ro + r, g.H);
+            const int gx = reflect101(g.tx0 - g.ro + c, g.W);
+            const float* src = x + ((size_t)gy * g.W + gx) * D;
+            float* dst = xs + ((size_t)r * g.XP + c) * P::DP;
 #pragma unroll
             for (int k = 0; k < D; ++k) {
                 const float v = __ldg(src + k);
@@ -122,51 +144,78 @@ __device__ __forceinline__ void load_halo_census(const TileGeom& g, long long* x
 // hsi[ch][r'][j] = the same over the inner width for the th + 2 ri halo rows the inner
 // squares use (r' = r - (ro - ri)).  Thread (r, seg) owns SEG consecutive output columns
 // of one halo row: a direct sum for the first, then sliding updates.
-template <class P, class ChanFn>
-__device__ __forceinline__ void horizontal_sums(const TileGeom& g, ChanFn chan, typename P::T* hso,
-                                                typename P::T* hsi) {
+template <class P, int Q0, int Q1, class ChanFn>
+__device__ __forceinline__ void horizontal_sums_part(const TileGeom& g, ChanFn chan, typename P::T* hso,
+                                                     typename P::T* hsi, int t) {
     using T = typename P::T;
     constexpr int NC = P::NC;
+    constexpr int NQ = Q1 - Q0;
     const int wo = 2 * g.ro + 1, i0 = g.ro - g.ri, i1 = g.ro + g.ri;  // inner columns dc in [i0, i1]
     const int rin0 = g.ro - g.ri;
     const int plane_o = g.HR * HP, plane_i = g.nin * HP;
-    const int nwork = g.HR * (TW / SEG);
-    for (int t = threadIdx.x; t < nwork; t += blockDim.x) {
-        const int r = t % g.HR, j0 = (t / g.HR) * SEG;
-        const bool inner_row = (r >= rin0) && (r < rin0 + g.nin);
-        T so[NC], si[NC], ch[NC], c2[NC];
+    const int r = t % g.HR, j0 = (t / g.HR) * SEG;
+    const bool inner_row = (r >= rin0) && (r < rin0 + g.nin);
+    T so[NQ], si[NQ], ch[NC], c2[NC];
 #pragma unroll
-        for (int q = 0; q < NC; ++q) { so[q] = T(0); si[q] = T(0); }
-        for (int dc = 0; dc < wo; ++dc) {
-            chan(r, j0 + dc, ch);
+    for (int q = 0; q < NQ; ++q) { so[q] = T(0); si[q] = T(0); }
+    for (int dc = 0; dc < wo; ++dc) {
+        chan(r, j0 + dc, ch);
 #pragma unroll
-            for (int q = 0; q < NC; ++q) so[q] += ch[q];
-            if (inner_row && dc >= i0 && dc <= i1) {
+        for (int q = 0; q < NQ; ++q) so[q] += ch[Q0 + q];
+        if (inner_row && dc >= i0 && dc <= i1) {
 #pragma unroll
-                for (int q = 0; q < NC; ++q) si[q] += ch[q];
-            }
+            for (int q = 0; q < NQ; ++q) si[q] += ch[Q0 + q];
         }
-        T* po = hso + r * HP + j0;
-        T* pi = hsi + (r - rin0) * HP + j0;
+    }
+    T* po = hso + Q0 * plane_o + r * HP + j0;
+    T* pi = hsi + Q0 * plane_i + (r - rin0) * HP + j0;
 #pragma unroll
-        for (int q = 0; q < NC; ++q) po[q * plane_o] = so[q];
+    for (int q = 0; q < NQ; ++q) po[q * plane_o] = so[q];
+    if (inner_row) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) pi[q * plane_i] = si[q];
+    }
+    for (int jj = 1; jj < SEG; ++jj) {
+        const int j = j0 + jj;
+        chan(r, j + wo - 1, ch);  // entering column
+        chan(r, j - 1, c2);       // leaving column
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            so[q] += ch[Q0 + q];
+            so[q] -= c2[Q0 + q];
+            po[q * plane_o + jj] = so[q];
+        }
         if (inner_row) {
+            chan(r, j + i1, ch);
+            chan(r, j - 1 + i0, c2);
 #pragma unroll
-            for (int q = 0; q < NC; ++q) pi[q * plane_i] = si[q];
-        }
-        for (int jj = 1; jj < SEG; ++jj) {
-            const int j = j0 + jj;
-            chan(r, j + wo - 1, ch);  // entering column
-            chan(r, j - 1, c2);       // leaving column
-#pragma unroll
-            for (int q = 0; q < NC; ++q) { so[q] += ch[q]; so[q] -= c2[q]; po[q * plane_o + jj] = so[q]; }
-            if (inner_row) {
-                chan(r, j + i1, ch);
-                chan(r, j - 1 + i0, c2);
-#pragma unroll
-                for (int q = 0; q < NC; ++q) { si[q] += ch[q]; si[q] -= c2[q]; pi[q * plane_i + jj] = si[q]; }
+            for (int q = 0; q < NQ; ++q) {
+                si[q] += ch[Q0 + q];
+                si[q] -= c2[Q0 + q];
+                pi[q * plane_i + jj] = si[q];
             }
         }
+    }
+}
+
+// hso[ch][r][j] = sum over the outer width of channel ch at halo row r, output column j;
+// hsi[ch][r'][j] = the same over the inner width for the th + 2 ri halo rows the inner
+// squares use (r' = r - (ro - ri)).  Work item (r, seg, half) owns SEG consecutive output
+// columns of one halo row and one half of the channels: a direct sum for the first
+// column, then sliding updates.  The channel halves run in different warps.
+template <class P, class ChanFn>
+__device__ __forceinline__ void horizontal_sums(const TileGeom& g, ChanFn chan, typename P::T* hso,
+                                                typename P::T* hsi) {
+    constexpr int NC = P::NC;
+    constexpr int NH = NC / 2;
+    const int nwork = g.HR * (TW / SEG);
+    const int nwork_pad = (nwork + 31) & ~31;  // each half starts on a warp boundary
+    for (int t = threadIdx.x; t < 2 * nwork_pad; t += blockDim.x) {
+        const int half = t >= nwork_pad;
+        const int u = t - half * nwork_pad;
+        if (u >= nwork) continue;
+        if (half == 0) horizontal_sums_part<P, 0, NH>(g, chan, hso, hsi, u);
+        else horizontal_sums_part<P, NH, NC>(g, chan, hso, hsi, u);
     }
 }
 
@@ -179,21 +228,25 @@ __device__ __forceinline__ void vertical_sums_inplace(const TileGeom& g, typenam
     constexpr int NC = P::NC;
     const int wo = 2 * g.ro + 1, wi = 2 * g.ri + 1;
     const int plane_o = g.HR * HP, plane_i = g.nin * HP;
-    for (int t = threadIdx.x; t < 2 * NC * TW; t += blockDim.x) {
-        const int j = t % TW, qq = t / TW;
-        const bool outer = qq < NC;
-        const int q = outer ? qq : qq - NC;
-        T* h = outer ? hso + q * plane_o + j : hsi + q * plane_i + j;
-        const int w = outer ? wo : wi;
-        T s = T(0);
-        for (int dr = 0; dr < w; ++dr) s += h[dr * HP];
+    for (int t = threadIdx.x; t < NC * TW; t += blockDim.x) {
+        const int j = t % TW, q = t / TW;
+        T* ho = hso + q * plane_o + j;
+        T* hi = hsi + q * plane_i + j;
+        T so = T(0), si = T(0);
+        for (int dr = 0; dr < wi; ++dr) { so += ho[dr * HP]; si += hi[dr * HP]; }
+        for (int dr = wi; dr < wo; ++dr) so += ho[dr * HP];
         for (int i = 1; i < g.th; ++i) {
-            const T leave = h[(i - 1) * HP], enter = h[(i + w - 1) * HP];
-            h[(i - 1) * HP] = s;
-            s += enter;
-            s -= leave;
+            const T lo = ho[(i - 1) * HP], eo = ho[(i + wo - 1) * HP];
+            const T li = hi[(i - 1) * HP], ei = hi[(i + wi - 1) * HP];
+            ho[(i - 1) * HP] = so;
+            hi[(i - 1) * HP] = si;
+            so += eo;
+            so -= lo;
+            si += ei;
+            si -= li;
         }
-        h[(g.th - 1) * HP] = s;
+        ho[(g.th - 1) * HP] = so;
+        hi[(g.th - 1) * HP] = si;
     }
 }
 
