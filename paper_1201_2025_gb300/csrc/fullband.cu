@@ -1,7 +1,788 @@
-// Full-band detectors (dim > 8): placeholder until the CTA-per-pixel path lands.
+// A3-A5 on the full-band cube (dim D > 8, e.g. L = 224): one CTA per pixel,
+// persistent over the pixel list.
+//
+// Statistics (Sec. 2.1 / 2.2): the background annulus and inner square samples are
+// gathered from the cube (reflect-101 borders), their means computed, and the
+// centred Gram  sum (x - mu)(x - mu)^T  accumulated into a symmetric matrix stored
+// as 4x4 tiles of its lower triangle ("tile-packed").
+//   LRX / DWRX (Eq. 1, 5): C_o + delta I, delta = loading * trace(C_o) / D, blocked
+//     Cholesky on the tiles, one forward solve for the two right-hand sides
+//     r - mu_o and mu_i - mu_o, score = ||L^-1 d||^2.
+//   DWEST (Eq. 2-4): C_diff = C_i - C_o; Householder tridiagonalisation; the
+//     eigenvalues above tau = dwest_tau * max|lambda| by Sturm-count bisection (a
+//     warp evaluates 32 points per step); their eigenvectors by inverse iteration on
+//     the tridiagonal matrix (partial pivoting), re-orthogonalised inside clusters;
+//     back-transformation through the stored reflectors, one warp per vector; each
+//     vector's largest-|.| entry made positive; score |sum_k v_k^T m_diff|
+//     (dwest_mode 0) or ||V^T m_diff|| (mode 1).
+// T = float (the FP32 path, matrix in shared memory) or double (FP64 path, matrix in
+// the per-CTA slab of the workspace).
+#include <float.h>
+
 #include "internal.h"
 
 namespace wdad {
-size_t fullband_workspace_bytes(const FullArgs&, int) { return 0; }
-cudaError_t launch_detect_full(const FullArgs&, void*, size_t, int, cudaStream_t) { return cudaErrorNotSupported; }
+namespace {
+
+constexpr int FB_THREADS = 512;
+constexpr int FB_WARPS = FB_THREADS / 32;
+
+template <typename T> struct Num;
+template <> struct Num<float> {
+    static constexpr float eps = 1.1920929e-7f;
+    static constexpr int bisect_steps = 6;  // 32-point sections: 6 x 5 = 30 bits
+    static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+};
+template <> struct Num<double> {
+    static constexpr double eps = 2.220446049250313e-16;
+    static constexpr int bisect_steps = 12;  // 60 bits
+    static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+};
+
+// ---- tile-packed symmetric storage: tile (I, K), I >= K, holds rows 4I.., cols 4K..
+__host__ __device__ __forceinline__ int ntiles_of(int nt) { return nt * (nt + 1) / 2; }
+__device__ __forceinline__ int tile_off(int I, int K) { return ((I * (I + 1)) / 2 + K) * 16; }
+template <typename T>
+__device__ __forceinline__ T& el(T* A, int a, int b) {  // requires a >= b
+    return A[tile_off(a >> 2, b >> 2) + ((a & 3) << 2) + (b & 3)];
+}
+template <typename T>
+__device__ __forceinline__ T sym(const T* A, int a, int b) {
+    return a >= b ? A[tile_off(a >> 2, b >> 2) + ((a & 3) << 2) + (b & 3)]
+                  : A[tile_off(b >> 2, a >> 2) + ((b & 3) << 2) + (a & 3)];
+}
+// linear index u of a lower-triangular tile grid -> (row, col), u = row(row+1)/2 + col
+__device__ __forceinline__ void tri_rc(int u, int& r, int& c) {
+    r = (int)((sqrtf(8.f * (float)u + 1.f) - 1.f) * 0.5f);
+    while ((r + 1) * (r + 2) / 2 <= u) ++r;
+    while (r * (r + 1) / 2 > u) --r;
+    c = u - r * (r + 1) / 2;
+}
+
+// ---- window sample offsets in row-major order (background = outer square minus inner)
+__device__ __forceinline__ void bg_offset(int s, int ro, int ri, int& dy, int& dx) {
+    const int wo = 2 * ro + 1, wi = 2 * ri + 1, side = ro - ri;
+    const int top = side * wo;
+    if (s < top) { dy = -ro + s / wo; dx = -ro + s % wo; return; }
+    s -= top;
+    const int band = wi * (wo - wi);
+    if (s < band) {
+        const int row = s / (wo - wi), c = s % (wo - wi);
+        dy = -ri + row;
+        dx = (c < side) ? -ro + c : ri + 1 + (c - side);
+        return;
+    }
+    s -= band;
+    dy = ri + 1 + s / wo;
+    dx = -ro + s % wo;
+}
+__device__ __forceinline__ void in_offset(int s, int ri, int& dy, int& dx) {
+    const int wi = 2 * ri + 1;
+    dy = -ri + s / wi;
+    dx = -ri + s % wi;
+}
+
+template <typename T>
+__device__ T block_sum(T v, T* red) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    T s = T(0);
+#pragma unroll
+    for (int w = 0; w < FB_WARPS; ++w) s += red[w];
+    __syncthreads();
+    return s;
+}
+template <typename T>
+__device__ T block_max(T v, T* red) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    T s = red[0];
+#pragma unroll
+    for (int w = 1; w < FB_WARPS; ++w) s = max(s, red[w]);
+    __syncthreads();
+    return s;
+}
+
+// ---- shared-memory layout
+template <typename T>
+struct Smem {
+    T* A;     // tile-packed matrix (shared or global)
+    T* xs;    // sample chunk [S][Dp]
+    T* mu_o;  // [Dp]
+    T* mu_i;  // [Dp]
+    T* r1;    // [Dp] right-hand side 1 (r - mu_o), then its solution
+    T* r2;    // [Dp] right-hand side 2 (mu_i - mu_o), then its solution
+    T* v;     // [Dp] Householder vector / scratch
+    T* p;     // [Dp]
+    T* dd;    // [Dp] tridiagonal diagonal
+    T* ee;    // [Dp] tridiagonal off-diagonal
+    T* lam;   // [mcap] selected eigenvalues
+    T* res;   // [mcap * 2] per-vector sign*projection, projection
+    T* red;   // [FB_WARPS]
+    int* flag;
+};
+
+struct Geo {
+    int D, Dp, nt, S, mcap;
+    bool a_in_smem;
+};
+
+__host__ __device__ inline int fb_chunk(int elem_size) { return elem_size == 4 ? 32 : 8; }
+
+template <typename T>
+__host__ __device__ inline size_t fb_smem_vectors_bytes(int Dp, int S, int mcap) {
+    return sizeof(T) * ((size_t)S * Dp + 8 * (size_t)Dp + 3 * (size_t)mcap + FB_WARPS) + 16;
+}
+
+// ---- statistics ---------------------------------------------------------------
+// mean over a sample list (kind 0 = background, 1 = inner) into out[0..Dp)
+template <typename T>
+__device__ void sample_mean(const float* __restrict__ x, int H, int W, int D, int Dp, int py, int px, int kind,
+                            int n, int ro, int ri, T* out) {
+    for (int b = threadIdx.x; b < Dp; b += FB_THREADS) {
+        T acc = T(0);
+        if (b < D) {
+            for (int s = 0; s < n; ++s) {
+                int dy, dx;
+                if (kind == 0) bg_offset(s, ro, ri, dy, dx); else in_offset(s, ri, dy, dx);
+                const size_t q = (size_t)reflect101(py + dy, H) * W + reflect101(px + dx, W);
+                acc += (T)__ldg(x + q * D + b);
+            }
+            acc /= (T)n;
+        }
+        out[b] = acc;
+    }
+}
+
+// A += sum over samples of (sc (x - mu)) (sc (x - mu))^T, tile by tile, S samples per chunk
+template <typename T>
+__device__ void gram_accumulate(const float* __restrict__ x, int H, int W, const Geo& g, int py, int px, int kind,
+                                int n, int ro, int ri, const T* mu, T sc, T* A, T* xs) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ntl = ntiles_of(g.nt);
+    for (int s0 = 0; s0 < n; s0 += g.S) {
+        __syncthreads();
+        for (int ss = warp; ss < g.S; ss += FB_WARPS) {
+            T* dst = xs + (size_t)ss * g.Dp;
+            const int s = s0 + ss;
+            if (s < n) {
+                int dy, dx;
+                if (kind == 0) bg_offset(s, ro, ri, dy, dx); else in_offset(s, ri, dy, dx);
+                const float* src = x + ((size_t)reflect101(py + dy, H) * W + reflect101(px + dx, W)) * g.D;
+                for (int b = lane; b < g.Dp; b += 32) dst[b] = b < g.D ? ((T)__ldg(src + b) - mu[b]) * sc : T(0);
+            } else {
+                for (int b = lane; b < g.Dp; b += 32) dst[b] = T(0);
+            }
+        }
+        __syncthreads();
+        const int ns = min(g.S, n - s0);
+        for (int u = threadIdx.x; u < ntl; u += FB_THREADS) {
+            int I, K;
+            tri_rc(u, I, K);
+            T acc[16];
+            T* t = A + (size_t)u * 16;
+#pragma unroll
+            for (int e = 0; e < 16; ++e) acc[e] = t[e];
+            for (int s = 0; s < ns; ++s) {
+                const T* row = xs + (size_t)s * g.Dp;
+                T ai[4], bk[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) { ai[e] = row[4 * I + e]; bk[e] = row[4 * K + e]; }
+#pragma unroll
+                for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+                    for (int cc = 0; cc < 4; ++cc) acc[rr * 4 + cc] += ai[rr] * bk[cc];
+            }
+#pragma unroll
+            for (int e = 0; e < 16; ++e) t[e] = acc[e];
+        }
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__device__ void mat_zero(T* A, const Geo& g) {
+    const int n = ntiles_of(g.nt) * 16;
+    for (int i = threadIdx.x; i < n; i += FB_THREADS) A[i] = T(0);
+    __syncthreads();
+}
+
+template <typename T>
+__device__ void mat_scale(T* A, const Geo& g, T s) {
+    const int n = ntiles_of(g.nt) * 16;
+    for (int i = threadIdx.x; i < n; i += FB_THREADS) A[i] *= s;
+    __syncthreads();
+}
+
+// ---- blocked Cholesky on the tiles (padding rows are identity).  Returns false if a
+// pivot is not above `floor`.
+template <typename T>
+__device__ bool cholesky_tiles(T* A, const Geo& g, T floor, int* flag) {
+    if (threadIdx.x == 0) *flag = 0;
+    for (int b = g.D + threadIdx.x; b < g.Dp; b += FB_THREADS) el(A, b, b) = T(1);
+    __syncthreads();
+    for (int J = 0; J < g.nt; ++J) {
+        if (threadIdx.x == 0) {
+            T* t = A + tile_off(J, J);
+            bool ok = true;
+            for (int j = 0; j < 4 && ok; ++j) {
+                T s = t[j * 4 + j];
+                for (int k = 0; k < j; ++k) s -= t[j * 4 + k] * t[j * 4 + k];
+                if (!(s > floor)) { ok = false; break; }
+                const T l = Num<T>::sqrt_(s);
+                t[j * 4 + j] = l;
+                for (int i = j + 1; i < 4; ++i) {
+                    T v = t[i * 4 + j];
+                    for (int k = 0; k < j; ++k) v -= t[i * 4 + k] * t[j * 4 + k];
+                    t[i * 4 + j] = v / l;
+                }
+            }
+            if (!ok) *flag = 1;
+        }
+        __syncthreads();
+        if (*flag) return false;
+        // panel: A_IJ <- A_IJ L_JJ^-T
+        for (int I = J + 1 + threadIdx.x; I < g.nt; I += FB_THREADS) {
+            const T* l = A + tile_off(J, J);
+            T* b = A + tile_off(I, J);
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    T v = b[r * 4 + c];
+#pragma unroll
+                    for (int k = 0; k < c; ++k) v -= b[r * 4 + k] * l[c * 4 + k];
+                    b[r * 4 + c] = v / l[c * 4 + c];
+                }
+        }
+        __syncthreads();
+        // trailing: A_IK -= A_IJ A_KJ^T, I >= K > J
+        const int m = g.nt - J - 1;
+        for (int u = threadIdx.x; u < ntiles_of(m); u += FB_THREADS) {
+            int i2, k2;
+            tri_rc(u, i2, k2);
+            const int I = J + 1 + i2, K = J + 1 + k2;
+            const T* a = A + tile_off(I, J);
+            const T* b = A + tile_off(K, J);
+            T* c = A + tile_off(I, K);
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) {
+                    T v = c[r * 4 + cc];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) v -= a[r * 4 + k] * b[cc * 4 + k];
+                    c[r * 4 + cc] = v;
+                }
+        }
+        __syncthreads();
+    }
+    return true;
+}
+
+// y <- L^-1 y for two right-hand sides (tile forward substitution)
+template <typename T>
+__device__ void forward_solve2(const T* A, const Geo& g, T* y1, T* y2) {
+    for (int J = 0; J < g.nt; ++J) {
+        if (threadIdx.x < 2) {
+            T* y = threadIdx.x == 0 ? y1 : y2;
+            const T* l = A + tile_off(J, J);
+            for (int r = 0; r < 4; ++r) {
+                T v = y[4 * J + r];
+                for (int k = 0; k < r; ++k) v -= l[r * 4 + k] * y[4 * J + k];
+                y[4 * J + r] = v / l[r * 4 + r];
+            }
+        }
+        __syncthreads();
+        for (int u = J + 1 + threadIdx.x / 2; u < g.nt; u += FB_THREADS / 2) {
+            T* y = (threadIdx.x & 1) ? y2 : y1;
+            const T* l = A + tile_off(u, J);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                T v = y[4 * u + r];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) v -= l[r * 4 + k] * y[4 * J + k];
+                y[4 * u + r] = v;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---- Householder tridiagonalisation (in place; reflector k stored in column k below
+// the sub-diagonal, unit norm, H_k = I - 2 v v^T).  dd / ee receive the tridiagonal.
+// v and p are absolute-index vectors of length Dp, zero outside the trailing block, so
+// tile-level products need no masks.
+template <typename T>
+__device__ void tridiagonalise(T* A, const Geo& g, T* v, T* p, T* dd, T* ee, T* red) {
+    const int D = g.D, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = 0; k < D - 2; ++k) {
+        T part = T(0);
+        for (int b = threadIdx.x; b < g.Dp; b += FB_THREADS) {
+            const T xb = (b > k && b < D) ? el(A, b, k) : T(0);
+            v[b] = xb;
+            if (b > k + 1) part += xb * xb;
+        }
+        const T rest = block_sum(part, red);
+        const T x0 = v[k + 1];
+        const bool reflect = rest > T(0);
+        T alpha = x0;
+        if (reflect) {
+            const T nrm = Num<T>::sqrt_(x0 * x0 + rest);
+            alpha = (x0 >= T(0)) ? -nrm : nrm;
+            const T v0 = x0 - alpha;
+            const T inv = T(1) / Num<T>::sqrt_(v0 * v0 + rest);
+            if (threadIdx.x == 0) v[k + 1] = v0;
+            __syncthreads();
+            for (int b = k + 1 + threadIdx.x; b < D; b += FB_THREADS) v[b] *= inv;
+            __syncthreads();
+            // p = A v over the trailing block: one warp per tile row, lanes over tile columns
+            const int T0 = (k + 1) >> 2;
+            for (int I = T0 + warp; I < g.nt; I += FB_WARPS) {
+                T s4[4] = {T(0), T(0), T(0), T(0)};
+                for (int K = T0 + lane; K < g.nt; K += 32) {
+                    const bool low = K <= I;
+                    const T* t = low ? A + tile_off(I, K) : A + tile_off(K, I);
+                    T vk[4];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) vk[c] = v[4 * K + c];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) s4[r] += (low ? t[r * 4 + c] : t[c * 4 + r]) * vk[c];
+                }
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int o = 16; o >= 1; o >>= 1) s4[r] += __shfl_xor_sync(0xffffffffu, s4[r], o);
+                if (lane < 4) {
+                    const int row = 4 * I + lane;
+                    p[row] = (row > k && row < D) ? s4[lane] : T(0);
+                }
+            }
+            for (int b = threadIdx.x; b < 4 * T0; b += FB_THREADS) p[b] = T(0);
+            __syncthreads();
+            T kp = T(0);
+            for (int b = k + 1 + threadIdx.x; b < D; b += FB_THREADS) kp += v[b] * p[b];
+            const T K = block_sum(kp, red);
+            for (int b = k + 1 + threadIdx.x; b < D; b += FB_THREADS) p[b] = T(2) * p[b] - T(2) * K * v[b];  // q
+            __syncthreads();
+            // rank-2 update of the trailing lower triangle: A -= v q^T + q v^T
+            const int m = g.nt - T0;
+            for (int u = threadIdx.x; u < ntiles_of(m); u += FB_THREADS) {
+                int i2, k2;
+                tri_rc(u, i2, k2);
+                const int I = T0 + i2, Kt = T0 + k2;
+                T* t = A + tile_off(I, Kt);
+                T va[4], qa[4], vb[4], qb[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    va[r] = v[4 * I + r]; qa[r] = p[4 * I + r];
+                    vb[r] = v[4 * Kt + r]; qb[r] = p[4 * Kt + r];
+                }
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) t[r * 4 + c] -= va[r] * qb[c] + qa[r] * vb[c];
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) { dd[k] = el(A, k, k); ee[k] = alpha; }
+        for (int b = k + 1 + threadIdx.x; b < D; b += FB_THREADS) el(A, b, k) = reflect ? v[b] : T(0);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        dd[D - 2] = el(A, D - 2, D - 2);
+        dd[D - 1] = el(A, D - 1, D - 1);
+        ee[D - 2] = el(A, D - 1, D - 2);
+        el(A, D - 1, D - 2) = T(0);  // no reflector for the last column
+    }
+    __syncthreads();
+}
+
+// reciprocal used by the Sturm recurrence
+__device__ __forceinline__ float sturm_div(float a, float q) { return a * __frcp_rn(q); }
+__device__ __forceinline__ double sturm_div(double a, double q) { return a / q; }
+
+// number of eigenvalues of the tridiagonal (dd, ee) below x (Sturm sequence)
+template <typename T>
+__device__ int sturm_below(const T* dd, const T* ee, int n, T x, T pivmin) {
+    int c = 0;
+    T q = dd[0] - x;
+    if (q < T(0)) ++c;
+    for (int i = 1; i < n; ++i) {
+        if (fabs(q) < pivmin) q = (q < T(0)) ? -pivmin : pivmin;
+        q = (dd[i] - x) - sturm_div(ee[i - 1] * ee[i - 1], q);
+        if (q < T(0)) ++c;
+    }
+    return c;
+}
+
+// j-th smallest eigenvalue (0-based) by warp-parallel 32-section of [lo, hi]
+template <typename T>
+__device__ T warp_bisect(const T* dd, const T* ee, int n, int j, T lo, T hi, T pivmin) {
+    const int lane = threadIdx.x & 31;
+    for (int it = 0; it < Num<T>::bisect_steps; ++it) {
+        const T h = (hi - lo) / T(32);
+        const T x = lo + h * T(lane + 1);  // lanes probe lo + h, ..., lo + 32 h = hi
+        const int c = sturm_below(dd, ee, n, x, pivmin);
+        // first probe with more than j eigenvalues below it bounds lambda_j from above
+        const unsigned ballot = __ballot_sync(0xffffffffu, c > j);
+        const int f = ballot ? __ffs(ballot) - 1 : 31;
+        const T nlo = lo + h * T(f), nhi = lo + h * T(f + 1);
+        lo = nlo;
+        hi = nhi;
+    }
+    return T(0.5) * (lo + hi);
+}
+
+// inverse iteration on (T - lambda I): one thread per eigenvalue, scratch in [i][slot] layout
+template <typename T>
+__device__ void inverse_iterate(const T* dd, const T* ee, int n, T lam, T pert, int slot, int nslot, T* Ld, T* Lu,
+                                T* Lu2, T* Lf, T* Lb, int* piv, T* y /* column of n */, bool fresh) {
+    // factor: diag d, super du, super2 du2, multipliers f, pivots
+#define IX(i) ((size_t)(i) * nslot + slot)
+    for (int i = 0; i < n; ++i) {
+        Ld[IX(i)] = dd[i] - lam;
+        Lu[IX(i)] = (i < n - 1) ? ee[i] : T(0);
+        Lu2[IX(i)] = T(0);
+    }
+    for (int i = 0; i < n - 1; ++i) {
+        const T di = Ld[IX(i)], sub = ee[i];
+        if (fabs(di) >= fabs(sub)) {
+            const T dn = (di == T(0)) ? pert : di;
+            Ld[IX(i)] = dn;
+            const T f = sub / dn;
+            Lf[IX(i)] = f;
+            Ld[IX(i + 1)] -= f * Lu[IX(i)];
+            piv[IX(i)] = 0;
+        } else {
+            const T f = di / sub;
+            Lf[IX(i)] = f;
+            Ld[IX(i)] = sub;
+            const T tmp = Lu[IX(i)];
+            Lu[IX(i)] = Ld[IX(i + 1)];
+            Ld[IX(i + 1)] = tmp - f * Ld[IX(i + 1)];
+            if (i < n - 2) {
+                Lu2[IX(i)] = Lu[IX(i + 1)];
+                Lu[IX(i + 1)] = -f * Lu[IX(i + 1)];
+            }
+            piv[IX(i)] = 1;
+        }
+    }
+    if (Ld[IX(n - 1)] == T(0)) Ld[IX(n - 1)] = pert;
+    // right-hand side
+    for (int i = 0; i < n; ++i) Lb[IX(i)] = fresh ? T(1) + T(0.125) * (T)((i * 7919 + slot * 104729) % 17) / T(17) : y[i];
+    for (int it = 0; it < (fresh ? 3 : 1); ++it) {
+        if (it > 0)
+            for (int i = 0; i < n; ++i) Lb[IX(i)] = y[i];
+        // forward with the interchanges
+        for (int i = 0; i < n - 1; ++i) {
+            if (piv[IX(i)]) {
+                const T t = Lb[IX(i)];
+                Lb[IX(i)] = Lb[IX(i + 1)];
+                Lb[IX(i + 1)] = t - Lf[IX(i)] * Lb[IX(i + 1)];
+            } else {
+                Lb[IX(i + 1)] -= Lf[IX(i)] * Lb[IX(i)];
+            }
+        }
+        // backward
+        T x1 = T(0), x2 = T(0), nrm = T(0);
+        for (int i = n - 1; i >= 0; --i) {
+            const T xi = (Lb[IX(i)] - Lu[IX(i)] * x1 - Lu2[IX(i)] * x2) / Ld[IX(i)];
+            y[i] = xi;
+            nrm += xi * xi;
+            x2 = x1;
+            x1 = xi;
+        }
+        const T inv = T(1) / Num<T>::sqrt_(nrm);
+        for (int i = 0; i < n; ++i) y[i] *= inv;
+    }
+#undef IX
+}
+
+// warp-level argmax |v| (lowest index on ties), sum of v * w
+template <typename T>
+__device__ void warp_sign_proj(const T* v, const T* w, int n, T& sgn, T& proj) {
+    const int lane = threadIdx.x & 31;
+    T best = T(-1), pr = T(0);
+    int bi = 0x7fffffff;
+    T bv = T(0);
+    for (int i = lane; i < n; i += 32) {
+        const T a = fabs(v[i]);
+        if (a > best) { best = a; bi = i; bv = v[i]; }
+        pr += v[i] * w[i];
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        const T ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; bv = ov; }
+        pr += __shfl_xor_sync(0xffffffffu, pr, o);
+    }
+    sgn = (bv >= T(0)) ? T(1) : T(-1);
+    proj = pr;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(FB_THREADS, 1) fullband_kernel(FullArgs a, Geo g, char* ws, size_t slab_bytes) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int sflag;
+    __shared__ int s_m;
+    __shared__ T s_bounds[4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    char* slab = ws + (size_t)blockIdx.x * slab_bytes;
+    // layout
+    Smem<T> m;
+    {
+        char* sp = reinterpret_cast<char*>(smem_raw);
+        size_t off = 0;
+        if (g.a_in_smem) { m.A = reinterpret_cast<T*>(sp); off += sizeof(T) * ntiles_of(g.nt) * 16; }
+        T* base = reinterpret_cast<T*>(sp + off);
+        m.xs = base;
+        base += (size_t)g.S * g.Dp;
+        m.mu_o = base; base += g.Dp;
+        m.mu_i = base; base += g.Dp;
+        m.r1 = base; base += g.Dp;
+        m.r2 = base; base += g.Dp;
+        m.v = base; base += g.Dp;
+        m.p = base; base += g.Dp;
+        m.dd = base; base += g.Dp;
+        m.ee = base; base += g.Dp;
+        m.lam = base; base += g.mcap;
+        m.res = base; base += 2 * g.mcap;
+        m.red = base;
+        m.flag = &sflag;
+    }
+    size_t soff = 0;
+    if (!g.a_in_smem) { m.A = reinterpret_cast<T*>(slab); soff += sizeof(T) * ntiles_of(g.nt) * 16; }
+    T* Y = reinterpret_cast<T*>(slab + soff);  // [mcap][Dp] eigenvectors (column-major by vector)
+    soff += sizeof(T) * (size_t)g.mcap * g.Dp;
+    T* Ld = reinterpret_cast<T*>(slab + soff); soff += sizeof(T) * (size_t)g.mcap * g.Dp;
+    T* Lu = reinterpret_cast<T*>(slab + soff); soff += sizeof(T) * (size_t)g.mcap * g.Dp;
+    T* Lu2 = reinterpret_cast<T*>(slab + soff); soff += sizeof(T) * (size_t)g.mcap * g.Dp;
+    T* Lf = reinterpret_cast<T*>(slab + soff); soff += sizeof(T) * (size_t)g.mcap * g.Dp;
+    T* Lb = reinterpret_cast<T*>(slab + soff); soff += sizeof(T) * (size_t)g.mcap * g.Dp;
+    int* piv = reinterpret_cast<int*>(slab + soff);
+
+    const int ro = a.outer / 2, ri = a.inner / 2;
+    const int N = a.outer * a.outer - a.inner * a.inner, ni = a.inner * a.inner;
+    const int D = g.D;
+    const int64_t P = (int64_t)a.H * a.W;
+    const bool want_rx = a.out[0] || a.out[1];
+    const float fnan = __int_as_float(0x7fc00000);
+
+    for (int64_t pix = blockIdx.x; pix < P; pix += gridDim.x) {
+        const int py = (int)(pix / a.W), px = (int)(pix % a.W);
+        if (a.border == 1 && (py - ro < 0 || py + ro >= a.H || px - ro < 0 || px + ro >= a.W)) {
+            if (threadIdx.x < 3 && a.out[threadIdx.x]) a.out[threadIdx.x][pix] = fnan;
+            if (threadIdx.x == 0 && a.flags) a.flags[pix] = 4;
+            continue;
+        }
+        uint8_t flag = 0;
+        __syncthreads();
+        sample_mean<T>(a.x, a.H, a.W, D, g.Dp, py, px, 0, N, ro, ri, m.mu_o);
+        sample_mean<T>(a.x, a.H, a.W, D, g.Dp, py, px, 1, ni, ro, ri, m.mu_i);
+        __syncthreads();
+        if (want_rx) {
+            for (int b = threadIdx.x; b < g.Dp; b += FB_THREADS) {
+                const T c = b < D ? (T)__ldg(a.x + pix * D + b) : T(0);
+                m.r1[b] = b < D ? c - m.mu_o[b] : T(0);
+                m.r2[b] = b < D ? m.mu_i[b] - m.mu_o[b] : T(0);
+            }
+            mat_zero(m.A, g);
+            gram_accumulate<T>(a.x, a.H, a.W, g, py, px, 0, N, ro, ri, m.mu_o, T(1), m.A, m.xs);
+            mat_scale(m.A, g, T(1) / (T)N);
+            T tr = T(0), dmax = T(0);
+            for (int b = threadIdx.x; b < D; b += FB_THREADS) { tr += el(m.A, b, b); dmax = max(dmax, el(m.A, b, b)); }
+            tr = block_sum(tr, m.red);
+            dmax = block_max(dmax, m.red);
+            const T delta = (T)a.loading * tr / (T)D;
+            for (int b = threadIdx.x; b < D; b += FB_THREADS) el(m.A, b, b) += delta;
+            __syncthreads();
+            const bool ok = cholesky_tiles(m.A, g, T(16) * Num<T>::eps * (dmax + delta), m.flag);
+            if (ok) {
+                forward_solve2(m.A, g, m.r1, m.r2);
+                T q1 = T(0), q2 = T(0);
+                for (int b = threadIdx.x; b < D; b += FB_THREADS) { q1 += m.r1[b] * m.r1[b]; q2 += m.r2[b] * m.r2[b]; }
+                q1 = block_sum(q1, m.red);
+                q2 = block_sum(q2, m.red);
+                if (threadIdx.x == 0) {
+                    if (a.out[0]) a.out[0][pix] = (float)q1;
+                    if (a.out[1]) a.out[1][pix] = (float)fabs(q2);
+                }
+            } else {
+                flag |= 2;
+                if (threadIdx.x == 0) {
+                    if (a.out[0]) a.out[0][pix] = fnan;
+                    if (a.out[1]) a.out[1][pix] = fnan;
+                }
+            }
+        }
+        if (a.out[2]) {
+            // C_diff = C_i - C_o (Eq. 2)
+            for (int b = threadIdx.x; b < g.Dp; b += FB_THREADS) m.r2[b] = b < D ? m.mu_i[b] - m.mu_o[b] : T(0);
+            mat_zero(m.A, g);
+            gram_accumulate<T>(a.x, a.H, a.W, g, py, px, 0, N, ro, ri, m.mu_o, T(1), m.A, m.xs);
+            mat_scale(m.A, g, T(-1) / (T)N);
+            gram_accumulate<T>(a.x, a.H, a.W, g, py, px, 1, ni, ro, ri, m.mu_i, T(1) / Num<T>::sqrt_((T)ni), m.A,
+                               m.xs);
+            tridiagonalise(m.A, g, m.v, m.p, m.dd, m.ee, m.red);
+            // spectrum bounds (Gershgorin), extreme eigenvalues, threshold, count above it
+            T glo, ghi;
+            {
+                T lo = T(3e38), hi = T(-3e38);
+                for (int i = threadIdx.x; i < D; i += FB_THREADS) {
+                    const T r = (i > 0 ? fabs(m.ee[i - 1]) : T(0)) + (i < D - 1 ? fabs(m.ee[i]) : T(0));
+                    lo = min(lo, m.dd[i] - r);
+                    hi = max(hi, m.dd[i] + r);
+                }
+                glo = -block_max(-lo, m.red);
+                ghi = block_max(hi, m.red);
+            }
+            const T tnorm = max(fabs(glo), fabs(ghi));
+            const T pivmin = max(tnorm * Num<T>::eps * Num<T>::eps, T(1e-30));
+            const T pad = tnorm * T(4) * Num<T>::eps + pivmin;
+            if (warp == 0) {
+                const T lmax = warp_bisect(m.dd, m.ee, D, D - 1, glo - pad, ghi + pad, pivmin);
+                if (lane == 0) s_bounds[0] = lmax;
+            } else if (warp == 1) {
+                const T lmin = warp_bisect(m.dd, m.ee, D, 0, glo - pad, ghi + pad, pivmin);
+                if (lane == 0) s_bounds[1] = lmin;
+            }
+            __syncthreads();
+            const T maxabs = max(fabs(s_bounds[0]), fabs(s_bounds[1]));
+            const T tau = (T)a.dwest_tau * maxabs;
+            if (threadIdx.x == 0) {
+                const int below = (maxabs > T(0)) ? sturm_below(m.dd, m.ee, D, tau, pivmin) : D;
+                s_m = D - below;
+            }
+            __syncthreads();
+            int msel = s_m;
+            if (msel > g.mcap) { msel = g.mcap; flag |= 8; }  // more than the slab holds: top mcap kept
+            // selected eigenvalues lambda_{D-msel} .. lambda_{D-1}
+            for (int s = warp; s < msel; s += FB_WARPS) {
+                const T l = warp_bisect(m.dd, m.ee, D, D - msel + s, glo - pad, ghi + pad, pivmin);
+                if (lane == 0) m.lam[s] = l;
+            }
+            __syncthreads();
+            // eigenvectors of the tridiagonal matrix
+            const T pert = max(tnorm * Num<T>::eps, pivmin);
+            if (threadIdx.x < msel)
+                inverse_iterate(m.dd, m.ee, D, m.lam[threadIdx.x], pert, threadIdx.x, g.mcap, Ld, Lu, Lu2, Lf, Lb,
+                                piv, Y + (size_t)threadIdx.x * g.Dp, true);
+            __syncthreads();
+            // re-orthogonalise inside clusters (gap below 1e-3 |T|), then one more iteration
+            for (int pass = 0; pass < 2; ++pass) {
+                for (int s = 1; s < msel; ++s) {
+                    for (int s2 = s - 1; s2 >= 0 && fabs(m.lam[s] - m.lam[s2]) <= T(1e-3) * tnorm; --s2) {
+                        T* ys = Y + (size_t)s * g.Dp;
+                        const T* yo = Y + (size_t)s2 * g.Dp;
+                        T dp = T(0);
+                        for (int i = threadIdx.x; i < D; i += FB_THREADS) dp += ys[i] * yo[i];
+                        dp = block_sum(dp, m.red);
+                        T nn = T(0);
+                        for (int i = threadIdx.x; i < D; i += FB_THREADS) { ys[i] -= dp * yo[i]; nn += ys[i] * ys[i]; }
+                        nn = block_sum(nn, m.red);
+                        const T inv = T(1) / Num<T>::sqrt_(nn);
+                        for (int i = threadIdx.x; i < D; i += FB_THREADS) ys[i] *= inv;
+                        __syncthreads();
+                    }
+                }
+                if (pass == 0) {
+                    if (threadIdx.x < msel)
+                        inverse_iterate(m.dd, m.ee, D, m.lam[threadIdx.x], pert, threadIdx.x, g.mcap, Ld, Lu, Lu2, Lf,
+                                        Lb, piv, Y + (size_t)threadIdx.x * g.Dp, false);
+                    __syncthreads();
+                }
+            }
+            // back-transformation v = H_0 ... H_{D-3} y, one warp per vector (no block barriers)
+            for (int s = warp; s < msel; s += FB_WARPS) {
+                T* y = Y + (size_t)s * g.Dp;
+                for (int k = D - 3; k >= 0; --k) {
+                    T dp = T(0);
+                    for (int i = k + 1 + lane; i < D; i += 32) dp += el(m.A, i, k) * y[i];
+#pragma unroll
+                    for (int o = 16; o >= 1; o >>= 1) dp += __shfl_xor_sync(0xffffffffu, dp, o);
+                    for (int i = k + 1 + lane; i < D; i += 32) y[i] -= T(2) * dp * el(m.A, i, k);
+                    __syncwarp();
+                }
+                T sg, pr;
+                warp_sign_proj(y, m.r2, D, sg, pr);
+                if (lane == 0) { m.res[2 * s] = sg * pr; m.res[2 * s + 1] = pr * pr; }
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                T acc = T(0), acc2 = T(0);
+                for (int s = 0; s < msel; ++s) { acc += m.res[2 * s]; acc2 += m.res[2 * s + 1]; }
+                a.out[2][pix] = (float)(a.dwest_mode == 0 ? fabs(acc) : Num<T>::sqrt_(acc2));
+            }
+        }
+        if (threadIdx.x == 0 && a.flags) a.flags[pix] = flag;
+    }
+}
+
+template <typename T>
+Geo make_geo(const FullArgs& a, bool* smem_ok, size_t* smem_bytes, size_t* slab) {
+    Geo g{};
+    g.D = a.D;
+    g.Dp = (a.D + 3) & ~3;
+    g.nt = g.Dp / 4;
+    g.S = fb_chunk(sizeof(T));
+    const int ni = a.inner * a.inner;
+    g.mcap = std::min(g.Dp, ni + 16);
+    const size_t amat = sizeof(T) * (size_t)ntiles_of(g.nt) * 16;
+    const size_t vecs = fb_smem_vectors_bytes<T>(g.Dp, g.S, g.mcap);
+    g.a_in_smem = (sizeof(T) == 4) && (amat + vecs <= 200 * 1024);
+    *smem_bytes = vecs + (g.a_in_smem ? amat : 0);
+    *smem_ok = *smem_bytes <= 227 * 1024;
+    *slab = (g.a_in_smem ? 0 : amat) + sizeof(T) * (size_t)g.mcap * g.Dp * 6 + sizeof(int) * (size_t)g.mcap * g.Dp;
+    *slab = (*slab + 255) & ~(size_t)255;
+    return g;
+}
+
+}  // namespace
+
+static int fb_grid(int num_sms, int64_t P) {
+    int64_t g = num_sms;
+    if (g > P) g = P;
+    return (int)(g < 1 ? 1 : g);
+}
+
+size_t fullband_workspace_bytes(const FullArgs& a, int num_sms) {
+    if (a.D < 9 || a.D > 1024) return 0;
+    bool ok;
+    size_t smem, slab;
+    if (a.precision == WDAD_PREC_FP64) make_geo<double>(a, &ok, &smem, &slab);
+    else make_geo<float>(a, &ok, &smem, &slab);
+    if (!ok) return 0;
+    return slab * (size_t)fb_grid(num_sms, (int64_t)a.H * a.W) + 256;
+}
+
+template <typename T>
+static cudaError_t launch_fb(const FullArgs& a, void* ws, int num_sms, cudaStream_t s) {
+    bool ok;
+    size_t smem, slab;
+    const Geo g = make_geo<T>(a, &ok, &smem, &slab);
+    if (!ok) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(fullband_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int grid = fb_grid(num_sms, (int64_t)a.H * a.W);
+    char* base = reinterpret_cast<char*>(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+    fullband_kernel<T><<<grid, FB_THREADS, smem, s>>>(a, g, base, slab);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_detect_full(const FullArgs& a, void* ws, size_t ws_bytes, int num_sms, cudaStream_t s) {
+    if ((int64_t)a.H * a.W == 0) return cudaSuccess;
+    if (ws_bytes < fullband_workspace_bytes(a, num_sms)) return cudaErrorInvalidValue;
+    if (a.precision == WDAD_PREC_FP64) return launch_fb<double>(a, ws, num_sms, s);
+    return launch_fb<float>(a, ws, num_sms, s);
+}
+
 }  // namespace wdad
