@@ -39,17 +39,24 @@ template <> struct Num<double> {
     static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
 };
 
-// ---- tile-packed symmetric storage: tile (I, K), I >= K, holds rows 4I.., cols 4K..
+// ---- tile-packed symmetric storage: tile (I, K), I >= K, holds rows 4I.., cols 4K..;
+// entry e = 4 (a % 4) + (b % 4) of tile u = I(I+1)/2 + K sits at A[e * ntl + u] (entries
+// of neighbouring tiles are adjacent, so threads walking tiles hit distinct banks).
 __host__ __device__ __forceinline__ int ntiles_of(int nt) { return nt * (nt + 1) / 2; }
-__device__ __forceinline__ int tile_off(int I, int K) { return ((I * (I + 1)) / 2 + K) * 16; }
+__device__ __forceinline__ int tile_idx(int I, int K) { return (I * (I + 1)) / 2 + K; }
 template <typename T>
-__device__ __forceinline__ T& el(T* A, int a, int b) {  // requires a >= b
-    return A[tile_off(a >> 2, b >> 2) + ((a & 3) << 2) + (b & 3)];
+__device__ __forceinline__ T& el(T* A, int ntl, int a, int b) {  // requires a >= b
+    return A[(((a & 3) << 2) + (b & 3)) * ntl + tile_idx(a >> 2, b >> 2)];
 }
 template <typename T>
-__device__ __forceinline__ T sym(const T* A, int a, int b) {
-    return a >= b ? A[tile_off(a >> 2, b >> 2) + ((a & 3) << 2) + (b & 3)]
-                  : A[tile_off(b >> 2, a >> 2) + ((b & 3) << 2) + (a & 3)];
+__device__ __forceinline__ void tile_load(const T* A, int ntl, int u, T (&t)[16]) {
+#pragma unroll
+    for (int e = 0; e < 16; ++e) t[e] = A[e * ntl + u];
+}
+template <typename T>
+__device__ __forceinline__ void tile_store(T* A, int ntl, int u, const T (&t)[16]) {
+#pragma unroll
+    for (int e = 0; e < 16; ++e) A[e * ntl + u] = t[e];
 }
 // linear index u of a lower-triangular tile grid -> (row, col), u = row(row+1)/2 + col
 __device__ __forceinline__ void tri_rc(int u, int& r, int& c) {
@@ -127,7 +134,7 @@ struct Smem {
 };
 
 struct Geo {
-    int D, Dp, nt, S, mcap;
+    int D, Dp, nt, ntl, S, mcap;
     bool a_in_smem;
 };
 
@@ -163,7 +170,7 @@ template <typename T>
 __device__ void gram_accumulate(const float* __restrict__ x, int H, int W, const Geo& g, int py, int px, int kind,
                                 int n, int ro, int ri, const T* mu, T sc, T* A, T* xs) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int ntl = ntiles_of(g.nt);
+    const int ntl = g.ntl;
     for (int s0 = 0; s0 < n; s0 += g.S) {
         __syncthreads();
         for (int ss = warp; ss < g.S; ss += FB_WARPS) {
@@ -184,9 +191,7 @@ __device__ void gram_accumulate(const float* __restrict__ x, int H, int W, const
             int I, K;
             tri_rc(u, I, K);
             T acc[16];
-            T* t = A + (size_t)u * 16;
-#pragma unroll
-            for (int e = 0; e < 16; ++e) acc[e] = t[e];
+            tile_load(A, ntl, u, acc);
             for (int s = 0; s < ns; ++s) {
                 const T* row = xs + (size_t)s * g.Dp;
                 T ai[4], bk[4];
@@ -197,8 +202,7 @@ __device__ void gram_accumulate(const float* __restrict__ x, int H, int W, const
 #pragma unroll
                     for (int cc = 0; cc < 4; ++cc) acc[rr * 4 + cc] += ai[rr] * bk[cc];
             }
-#pragma unroll
-            for (int e = 0; e < 16; ++e) t[e] = acc[e];
+            tile_store(A, ntl, u, acc);
         }
     }
     __syncthreads();
@@ -222,12 +226,15 @@ __device__ void mat_scale(T* A, const Geo& g, T s) {
 // pivot is not above `floor`.
 template <typename T>
 __device__ bool cholesky_tiles(T* A, const Geo& g, T floor, int* flag) {
+    const int ntl = g.ntl;
     if (threadIdx.x == 0) *flag = 0;
-    for (int b = g.D + threadIdx.x; b < g.Dp; b += FB_THREADS) el(A, b, b) = T(1);
+    for (int b = g.D + threadIdx.x; b < g.Dp; b += FB_THREADS) el(A, ntl, b, b) = T(1);
     __syncthreads();
     for (int J = 0; J < g.nt; ++J) {
         if (threadIdx.x == 0) {
-            T* t = A + tile_off(J, J);
+            T t[16];
+            const int u = tile_idx(J, J);
+            tile_load(A, ntl, u, t);
             bool ok = true;
             for (int j = 0; j < 4 && ok; ++j) {
                 T s = t[j * 4 + j];
@@ -241,14 +248,16 @@ __device__ bool cholesky_tiles(T* A, const Geo& g, T floor, int* flag) {
                     t[i * 4 + j] = v / l;
                 }
             }
+            tile_store(A, ntl, u, t);
             if (!ok) *flag = 1;
         }
         __syncthreads();
         if (*flag) return false;
         // panel: A_IJ <- A_IJ L_JJ^-T
         for (int I = J + 1 + threadIdx.x; I < g.nt; I += FB_THREADS) {
-            const T* l = A + tile_off(J, J);
-            T* b = A + tile_off(I, J);
+            T l[16], b[16];
+            tile_load(A, ntl, tile_idx(J, J), l);
+            tile_load(A, ntl, tile_idx(I, J), b);
 #pragma unroll
             for (int r = 0; r < 4; ++r)
 #pragma unroll
@@ -258,6 +267,7 @@ __device__ bool cholesky_tiles(T* A, const Geo& g, T floor, int* flag) {
                     for (int k = 0; k < c; ++k) v -= b[r * 4 + k] * l[c * 4 + k];
                     b[r * 4 + c] = v / l[c * 4 + c];
                 }
+            tile_store(A, ntl, tile_idx(I, J), b);
         }
         __syncthreads();
         // trailing: A_IK -= A_IJ A_KJ^T, I >= K > J
@@ -266,18 +276,21 @@ __device__ bool cholesky_tiles(T* A, const Geo& g, T floor, int* flag) {
             int i2, k2;
             tri_rc(u, i2, k2);
             const int I = J + 1 + i2, K = J + 1 + k2;
-            const T* a = A + tile_off(I, J);
-            const T* b = A + tile_off(K, J);
-            T* c = A + tile_off(I, K);
+            T av[16], bv[16], c[16];
+            tile_load(A, ntl, tile_idx(I, J), av);
+            tile_load(A, ntl, tile_idx(K, J), bv);
+            const int uc = tile_idx(I, K);
+            tile_load(A, ntl, uc, c);
 #pragma unroll
             for (int r = 0; r < 4; ++r)
 #pragma unroll
                 for (int cc = 0; cc < 4; ++cc) {
                     T v = c[r * 4 + cc];
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) v -= a[r * 4 + k] * b[cc * 4 + k];
+                    for (int k = 0; k < 4; ++k) v -= av[r * 4 + k] * bv[cc * 4 + k];
                     c[r * 4 + cc] = v;
                 }
+            tile_store(A, ntl, uc, c);
         }
         __syncthreads();
     }
@@ -287,10 +300,12 @@ __device__ bool cholesky_tiles(T* A, const Geo& g, T floor, int* flag) {
 // y <- L^-1 y for two right-hand sides (tile forward substitution)
 template <typename T>
 __device__ void forward_solve2(const T* A, const Geo& g, T* y1, T* y2) {
+    const int ntl = g.ntl;
     for (int J = 0; J < g.nt; ++J) {
         if (threadIdx.x < 2) {
             T* y = threadIdx.x == 0 ? y1 : y2;
-            const T* l = A + tile_off(J, J);
+            T l[16];
+            tile_load(A, ntl, tile_idx(J, J), l);
             for (int r = 0; r < 4; ++r) {
                 T v = y[4 * J + r];
                 for (int k = 0; k < r; ++k) v -= l[r * 4 + k] * y[4 * J + k];
@@ -300,7 +315,8 @@ __device__ void forward_solve2(const T* A, const Geo& g, T* y1, T* y2) {
         __syncthreads();
         for (int u = J + 1 + threadIdx.x / 2; u < g.nt; u += FB_THREADS / 2) {
             T* y = (threadIdx.x & 1) ? y2 : y1;
-            const T* l = A + tile_off(u, J);
+            T l[16];
+            tile_load(A, ntl, tile_idx(u, J), l);
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
                 T v = y[4 * u + r];
@@ -319,11 +335,11 @@ __device__ void forward_solve2(const T* A, const Geo& g, T* y1, T* y2) {
 // tile-level products need no masks.
 template <typename T>
 __device__ void tridiagonalise(T* A, const Geo& g, T* v, T* p, T* dd, T* ee, T* red) {
-    const int D = g.D, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int D = g.D, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, ntl = g.ntl;
     for (int k = 0; k < D - 2; ++k) {
         T part = T(0);
         for (int b = threadIdx.x; b < g.Dp; b += FB_THREADS) {
-            const T xb = (b > k && b < D) ? el(A, b, k) : T(0);
+            const T xb = (b > k && b < D) ? el(A, ntl, b, k) : T(0);
             v[b] = xb;
             if (b > k + 1) part += xb * xb;
         }
@@ -346,7 +362,8 @@ __device__ void tridiagonalise(T* A, const Geo& g, T* v, T* p, T* dd, T* ee, T* 
                 T s4[4] = {T(0), T(0), T(0), T(0)};
                 for (int K = T0 + lane; K < g.nt; K += 32) {
                     const bool low = K <= I;
-                    const T* t = low ? A + tile_off(I, K) : A + tile_off(K, I);
+                    T t[16];
+                    tile_load(A, ntl, low ? tile_idx(I, K) : tile_idx(K, I), t);
                     T vk[4];
 #pragma unroll
                     for (int c = 0; c < 4; ++c) vk[c] = v[4 * K + c];
@@ -377,7 +394,9 @@ __device__ void tridiagonalise(T* A, const Geo& g, T* v, T* p, T* dd, T* ee, T* 
                 int i2, k2;
                 tri_rc(u, i2, k2);
                 const int I = T0 + i2, Kt = T0 + k2;
-                T* t = A + tile_off(I, Kt);
+                const int ut = tile_idx(I, Kt);
+                T t[16];
+                tile_load(A, ntl, ut, t);
                 T va[4], qa[4], vb[4], qb[4];
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
@@ -388,18 +407,19 @@ __device__ void tridiagonalise(T* A, const Geo& g, T* v, T* p, T* dd, T* ee, T* 
                 for (int r = 0; r < 4; ++r)
 #pragma unroll
                     for (int c = 0; c < 4; ++c) t[r * 4 + c] -= va[r] * qb[c] + qa[r] * vb[c];
+                tile_store(A, ntl, ut, t);
             }
             __syncthreads();
         }
-        if (threadIdx.x == 0) { dd[k] = el(A, k, k); ee[k] = alpha; }
-        for (int b = k + 1 + threadIdx.x; b < D; b += FB_THREADS) el(A, b, k) = reflect ? v[b] : T(0);
+        if (threadIdx.x == 0) { dd[k] = el(A, ntl, k, k); ee[k] = alpha; }
+        for (int b = k + 1 + threadIdx.x; b < D; b += FB_THREADS) el(A, ntl, b, k) = reflect ? v[b] : T(0);
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        dd[D - 2] = el(A, D - 2, D - 2);
-        dd[D - 1] = el(A, D - 1, D - 1);
-        ee[D - 2] = el(A, D - 1, D - 2);
-        el(A, D - 1, D - 2) = T(0);  // no reflector for the last column
+        dd[D - 2] = el(A, ntl, D - 2, D - 2);
+        dd[D - 1] = el(A, ntl, D - 1, D - 1);
+        ee[D - 2] = el(A, ntl, D - 1, D - 2);
+        el(A, ntl, D - 1, D - 2) = T(0);  // no reflector for the last column
     }
     __syncthreads();
 }
@@ -440,70 +460,68 @@ __device__ T warp_bisect(const T* dd, const T* ee, int n, int j, T lo, T hi, T p
     return T(0.5) * (lo + hi);
 }
 
-// inverse iteration on (T - lambda I): one thread per eigenvalue, scratch in [i][slot] layout
-template <typename T>
-__device__ void inverse_iterate(const T* dd, const T* ee, int n, T lam, T pert, int slot, int nslot, T* Ld, T* Lu,
-                                T* Lu2, T* Lf, T* Lb, int* piv, T* y /* column of n */, bool fresh) {
-    // factor: diag d, super du, super2 du2, multipliers f, pivots
+// Inverse iteration on (T - lambda I), one thread per eigenvalue; scratch arrays in
+// [i][slot] layout so the threads of a warp touch adjacent words.  inv_factor builds
+// the LU factors with partial pivoting (zero pivots replaced by `pert`), inv_solve
+// overwrites y (a column of n) with (T - lambda I)^-1 y, normalised.
 #define IX(i) ((size_t)(i) * nslot + slot)
-    for (int i = 0; i < n; ++i) {
-        Ld[IX(i)] = dd[i] - lam;
-        Lu[IX(i)] = (i < n - 1) ? ee[i] : T(0);
-        Lu2[IX(i)] = T(0);
-    }
+template <typename T>
+__device__ void inv_factor(const T* dd, const T* ee, int n, T lam, T pert, int slot, int nslot, T* Ld, T* Lu,
+                           T* Lu2, T* Lf, int* piv) {
+    T d_cur = dd[0] - lam, u_cur = (n > 1) ? ee[0] : T(0);
+    T u2_prev_next = T(0);
     for (int i = 0; i < n - 1; ++i) {
-        const T di = Ld[IX(i)], sub = ee[i];
-        if (fabs(di) >= fabs(sub)) {
-            const T dn = (di == T(0)) ? pert : di;
-            Ld[IX(i)] = dn;
+        const T sub = ee[i];
+        const T dnext = dd[i + 1] - lam;
+        const T unext = (i + 1 < n - 1) ? ee[i + 1] : T(0);
+        if (fabs(d_cur) >= fabs(sub)) {
+            const T dn = (d_cur == T(0)) ? pert : d_cur;
             const T f = sub / dn;
-            Lf[IX(i)] = f;
-            Ld[IX(i + 1)] -= f * Lu[IX(i)];
-            piv[IX(i)] = 0;
+            Ld[IX(i)] = dn; Lu[IX(i)] = u_cur; Lu2[IX(i)] = T(0); Lf[IX(i)] = f; piv[IX(i)] = 0;
+            d_cur = dnext - f * u_cur;
+            u_cur = unext;
         } else {
-            const T f = di / sub;
-            Lf[IX(i)] = f;
-            Ld[IX(i)] = sub;
-            const T tmp = Lu[IX(i)];
-            Lu[IX(i)] = Ld[IX(i + 1)];
-            Ld[IX(i + 1)] = tmp - f * Ld[IX(i + 1)];
-            if (i < n - 2) {
-                Lu2[IX(i)] = Lu[IX(i + 1)];
-                Lu[IX(i + 1)] = -f * Lu[IX(i + 1)];
-            }
-            piv[IX(i)] = 1;
+            const T f = d_cur / sub;
+            Ld[IX(i)] = sub; Lu[IX(i)] = dnext; Lu2[IX(i)] = unext; Lf[IX(i)] = f; piv[IX(i)] = 1;
+            d_cur = u_cur - f * dnext;
+            u_cur = -f * unext;
         }
     }
-    if (Ld[IX(n - 1)] == T(0)) Ld[IX(n - 1)] = pert;
-    // right-hand side
-    for (int i = 0; i < n; ++i) Lb[IX(i)] = fresh ? T(1) + T(0.125) * (T)((i * 7919 + slot * 104729) % 17) / T(17) : y[i];
-    for (int it = 0; it < (fresh ? 3 : 1); ++it) {
-        if (it > 0)
-            for (int i = 0; i < n; ++i) Lb[IX(i)] = y[i];
-        // forward with the interchanges
-        for (int i = 0; i < n - 1; ++i) {
-            if (piv[IX(i)]) {
-                const T t = Lb[IX(i)];
-                Lb[IX(i)] = Lb[IX(i + 1)];
-                Lb[IX(i + 1)] = t - Lf[IX(i)] * Lb[IX(i + 1)];
-            } else {
-                Lb[IX(i + 1)] -= Lf[IX(i)] * Lb[IX(i)];
-            }
-        }
-        // backward
-        T x1 = T(0), x2 = T(0), nrm = T(0);
-        for (int i = n - 1; i >= 0; --i) {
-            const T xi = (Lb[IX(i)] - Lu[IX(i)] * x1 - Lu2[IX(i)] * x2) / Ld[IX(i)];
-            y[i] = xi;
-            nrm += xi * xi;
-            x2 = x1;
-            x1 = xi;
-        }
-        const T inv = T(1) / Num<T>::sqrt_(nrm);
-        for (int i = 0; i < n; ++i) y[i] *= inv;
-    }
-#undef IX
+    (void)u2_prev_next;
+    Ld[IX(n - 1)] = (d_cur == T(0)) ? pert : d_cur;
+    Lu[IX(n - 1)] = T(0);
+    Lu2[IX(n - 1)] = T(0);
 }
+
+template <typename T>
+__device__ void inv_solve(int n, int slot, int nslot, const T* Ld, const T* Lu, const T* Lu2, const T* Lf,
+                          const int* piv, T* y) {
+    // forward: apply the interchanges and multipliers
+    T b_cur = y[0];
+    for (int i = 0; i < n - 1; ++i) {
+        const T b_next = y[i + 1];
+        if (piv[IX(i)]) {
+            y[i] = b_next;
+            b_cur = b_cur - Lf[IX(i)] * b_next;
+        } else {
+            y[i] = b_cur;
+            b_cur = b_next - Lf[IX(i)] * b_cur;
+        }
+    }
+    y[n - 1] = b_cur;
+    // backward
+    T x1 = T(0), x2 = T(0), nrm = T(0);
+    for (int i = n - 1; i >= 0; --i) {
+        const T xi = (y[i] - Lu[IX(i)] * x1 - Lu2[IX(i)] * x2) / Ld[IX(i)];
+        y[i] = xi;
+        nrm += xi * xi;
+        x2 = x1;
+        x1 = xi;
+    }
+    const T inv = T(1) / Num<T>::sqrt_(nrm);
+    for (int i = 0; i < n; ++i) y[i] *= inv;
+}
+#undef IX
 
 // warp-level argmax |v| (lowest index on ties), sum of v * w
 template <typename T>
@@ -567,7 +585,7 @@ __global__ void __launch_bounds__(FB_THREADS, 1) fullband_kernel(FullArgs a, Geo
     T* Lu = reinterpret_cast<T*>(slab + soff); soff += sizeof(T) * (size_t)g.mcap * g.Dp;
     T* Lu2 = reinterpret_cast<T*>(slab + soff); soff += sizeof(T) * (size_t)g.mcap * g.Dp;
     T* Lf = reinterpret_cast<T*>(slab + soff); soff += sizeof(T) * (size_t)g.mcap * g.Dp;
-    T* Lb = reinterpret_cast<T*>(slab + soff); soff += sizeof(T) * (size_t)g.mcap * g.Dp;
+    soff += sizeof(T) * (size_t)g.mcap * g.Dp;  // reserved
     int* piv = reinterpret_cast<int*>(slab + soff);
 
     const int ro = a.outer / 2, ri = a.inner / 2;
@@ -599,11 +617,11 @@ __global__ void __launch_bounds__(FB_THREADS, 1) fullband_kernel(FullArgs a, Geo
             gram_accumulate<T>(a.x, a.H, a.W, g, py, px, 0, N, ro, ri, m.mu_o, T(1), m.A, m.xs);
             mat_scale(m.A, g, T(1) / (T)N);
             T tr = T(0), dmax = T(0);
-            for (int b = threadIdx.x; b < D; b += FB_THREADS) { tr += el(m.A, b, b); dmax = max(dmax, el(m.A, b, b)); }
+            for (int b = threadIdx.x; b < D; b += FB_THREADS) { tr += el(m.A, g.ntl, b, b); dmax = max(dmax, el(m.A, g.ntl, b, b)); }
             tr = block_sum(tr, m.red);
             dmax = block_max(dmax, m.red);
             const T delta = (T)a.loading * tr / (T)D;
-            for (int b = threadIdx.x; b < D; b += FB_THREADS) el(m.A, b, b) += delta;
+            for (int b = threadIdx.x; b < D; b += FB_THREADS) el(m.A, g.ntl, b, b) += delta;
             __syncthreads();
             const bool ok = cholesky_tiles(m.A, g, T(16) * Num<T>::eps * (dmax + delta), m.flag);
             if (ok) {
@@ -673,11 +691,16 @@ __global__ void __launch_bounds__(FB_THREADS, 1) fullband_kernel(FullArgs a, Geo
             __syncthreads();
             // eigenvectors of the tridiagonal matrix
             const T pert = max(tnorm * Num<T>::eps, pivmin);
-            if (threadIdx.x < msel)
-                inverse_iterate(m.dd, m.ee, D, m.lam[threadIdx.x], pert, threadIdx.x, g.mcap, Ld, Lu, Lu2, Lf, Lb,
-                                piv, Y + (size_t)threadIdx.x * g.Dp, true);
+            if (threadIdx.x < msel) {
+                const int sl = threadIdx.x;
+                T* y = Y + (size_t)sl * g.Dp;
+                inv_factor(m.dd, m.ee, D, m.lam[sl], pert, sl, g.mcap, Ld, Lu, Lu2, Lf, piv);
+                for (int i = 0; i < D; ++i) y[i] = T(1) + T(0.125) * (T)((i * 7919 + sl * 104729) % 17) / T(17);
+                inv_solve(D, sl, g.mcap, Ld, Lu, Lu2, Lf, piv, y);
+                inv_solve(D, sl, g.mcap, Ld, Lu, Lu2, Lf, piv, y);
+            }
             __syncthreads();
-            // re-orthogonalise inside clusters (gap below 1e-3 |T|), then one more iteration
+            // re-orthogonalise inside clusters (gap below 1e-3 |T|), one more solve, again
             for (int pass = 0; pass < 2; ++pass) {
                 for (int s = 1; s < msel; ++s) {
                     for (int s2 = s - 1; s2 >= 0 && fabs(m.lam[s] - m.lam[s2]) <= T(1e-3) * tnorm; --s2) {
@@ -696,8 +719,7 @@ __global__ void __launch_bounds__(FB_THREADS, 1) fullband_kernel(FullArgs a, Geo
                 }
                 if (pass == 0) {
                     if (threadIdx.x < msel)
-                        inverse_iterate(m.dd, m.ee, D, m.lam[threadIdx.x], pert, threadIdx.x, g.mcap, Ld, Lu, Lu2, Lf,
-                                        Lb, piv, Y + (size_t)threadIdx.x * g.Dp, false);
+                        inv_solve(D, (int)threadIdx.x, g.mcap, Ld, Lu, Lu2, Lf, piv, Y + (size_t)threadIdx.x * g.Dp);
                     __syncthreads();
                 }
             }
@@ -706,10 +728,10 @@ __global__ void __launch_bounds__(FB_THREADS, 1) fullband_kernel(FullArgs a, Geo
                 T* y = Y + (size_t)s * g.Dp;
                 for (int k = D - 3; k >= 0; --k) {
                     T dp = T(0);
-                    for (int i = k + 1 + lane; i < D; i += 32) dp += el(m.A, i, k) * y[i];
+                    for (int i = k + 1 + lane; i < D; i += 32) dp += el(m.A, g.ntl, i, k) * y[i];
 #pragma unroll
                     for (int o = 16; o >= 1; o >>= 1) dp += __shfl_xor_sync(0xffffffffu, dp, o);
-                    for (int i = k + 1 + lane; i < D; i += 32) y[i] -= T(2) * dp * el(m.A, i, k);
+                    for (int i = k + 1 + lane; i < D; i += 32) y[i] -= T(2) * dp * el(m.A, g.ntl, i, k);
                     __syncwarp();
                 }
                 T sg, pr;
@@ -733,6 +755,7 @@ Geo make_geo(const FullArgs& a, bool* smem_ok, size_t* smem_bytes, size_t* slab)
     g.D = a.D;
     g.Dp = (a.D + 3) & ~3;
     g.nt = g.Dp / 4;
+    g.ntl = ntiles_of(g.nt);
     g.S = fb_chunk(sizeof(T));
     const int ni = a.inner * a.inner;
     g.mcap = std::min(g.Dp, ni + 16);
