@@ -229,10 +229,44 @@ def run_ours(args):
     roofline = {"kernel": "dwt_apply_kernel", "bound": "hbm", "achieved": dwt_gbs, "peak": peak, "unit": "GB/s",
                 "frac": dwt_gbs / peak, "traffic": traffic, "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": H * W * BYTES_DWT_PER_PX}
+    # per-detector reduced timings and full-band throughput on a strip (outside the timed step)
+    def _time(fn, n=10):
+        for _ in range(2):
+            fn()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(n):
+            fn()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        return a0.elapsed_time(a1) / n
+
+    one = torch.empty((H, W), device=dev)
+    per_det = {}
+    for (wi, wo), p in zip(WINDOWS, params):
+        for det, name in enumerate(("lrx", "dwrx", "dwest")):
+            ms = _time(lambda: wdad.wdad_detect(approx, det, reduce=False, params=p, out=one))
+            dwt_plus = dwt_ms + ms
+            per_det[f"{name}@{wi}/{wo}"] = {"detector_ms": ms, "Mpixel_s_with_dwt": H * W / (dwt_plus * 1e-3) / 1e6}
+    full = {}
+    if not args.no_full:
+        rows = args.full_rows
+        strip = x[:rows].contiguous()
+        sout = torch.empty((3, rows, W), device=dev)
+        sone = torch.empty((rows, W), device=dev)
+        for (wi, wo), p in zip(WINDOWS, params):
+            ms_all = _time(lambda: wdad.wdad_detect_all(strip, reduce=False, params=p, out=sout), n=2)
+            ms_lrx = _time(lambda: wdad.wdad_detect(strip, 0, reduce=False, params=p, out=sone), n=2)
+            full[f"{wi}/{wo}"] = {"all3_Mpixel_s": rows * W / (ms_all * 1e-3) / 1e6,
+                                  "lrx_Mpixel_s": rows * W / (ms_lrx * 1e-3) / 1e6,
+                                  "reduced_speedup_all3": (ms_all / (rows * W)) / ((dwt_ms + det_ms[WINDOWS.index((wi, wo))]) / (H * W))}
+        full["sample"] = f"{rows} x {W} x {L} strip of the cube, FP32, all pixels of the strip"
     step_bytes = H * W * (BYTES_DWT_PER_PX + 3 * 3 * 4)
     breakdown = {"dwt_ms": dwt_ms, "detect_ms": dict(zip([f"{a}/{b}" for a, b in WINDOWS], det_ms)),
                  "step_algorithmic_GBps": step_bytes / (ms_step * 1e-3) / 1e9,
-                 "step_frac_of_hbm": step_bytes / (ms_step * 1e-3) / 1e9 / peak}
+                 "step_frac_of_hbm": step_bytes / (ms_step * 1e-3) / 1e9 / peak, "per_detector": per_det,
+                 "fullband_fp32": full}
 
     # end to end through the host-buffer entry point: H2D cube, DWT, 3 windows, D2H 9 maps
     hc = torch.from_numpy(sc.cube).pin_memory()
@@ -294,6 +328,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-rows", type=int, default=16)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-full", action="store_true")
+    ap.add_argument("--full-rows", type=int, default=16)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
