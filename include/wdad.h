@@ -128,6 +128,28 @@ wdad_status wdad_detect_all_host(wdad_handle h, const float* host_cube, int H, i
 wdad_status wdad_window_census(wdad_handle h, int H, int W, const wdad_params* p,
                                int64_t* out, void* stream);
 
+/* The reduced pass of wdad_detect_all (reduce = 1) without any device allocation.
+ * The paper has no counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc.  Examples are software that fixes its memory budget at start-up, hosts
+ * whose framework owns all device memory through its own pool, and latency-critical code
+ * where an allocation could block on or synchronise with queued work.
+ * There is no handle.  It works on the current CUDA device and on `stream`.  Its
+ * scratch (the DWT matrix and the H x W x K approximation matrix) is a fixed 16 MiB +
+ * 32 KiB array inside the library, held by every device that loads the library until
+ * the process exits.
+ *   - Limits: H * W * K <= 4,194,304 (e.g. 1024 x 1024 pixels at K = 4), L <= 1024,
+ *     K <= 8.  Larger sizes return WDAD_ERR_ARG; windows whose tile does not fit
+ *     shared memory return WDAD_ERR_UNSUPPORTED.  Other argument rules as wdad_detect_all.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress).  Make that first call before any stream capture.
+ *   - Every call on a device shares the one array.  Calls that overlap on the GPU (other
+ *     streams, other host threads) race on it and must be serialised by the caller.
+ *     Nothing in it needs clearing: each call overwrites what it reads.
+ *   - cube: [H][W][L] float32 device; scores: [3][H][W] float32 device (LRX, DWRX, DWEST);
+ *     flags: [H][W] uint8 device or NULL, as for wdad_detect. */
+wdad_status wdad_detect_all_noalloc(const float* cube, int H, int W, int L, const wdad_params* p,
+                                    float* scores, uint8_t* flags, void* stream);
+
 /* A10 — pixel-level ROC AUC of a score map against a truth mask (Sec. 5.3.1):
  * Mann-Whitney U with ties counted one half.  HOST pointers; NaN scores rank lowest.
  * Writes NaN when the mask has no positive or no negative pixel. */

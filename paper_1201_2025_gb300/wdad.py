@@ -61,9 +61,11 @@ def lib() -> ctypes.CDLL:
     L.wdad_detect_all.argtypes = [vp, f32p, i32, i32, i32, i32, pp, f32p, vp, vp]
     L.wdad_detect_all_host.argtypes = [vp, vp, i32, i32, i32, i32, i32, pp, vp, vp]
     L.wdad_window_census.argtypes = [vp, i32, i32, pp, vp, vp]
+    L.wdad_detect_all_noalloc.argtypes = [f32p, i32, i32, i32, pp, f32p, vp, vp]
     L.wdad_auc.argtypes = [vp, vp, i64, ctypes.POINTER(ctypes.c_double)]
     for name in ("wdad_create", "wdad_destroy", "wdad_last_error_detail", "wdad_dwt_approx", "wdad_detect",
-                 "wdad_detect_all", "wdad_detect_all_host", "wdad_window_census", "wdad_auc"):
+                 "wdad_detect_all", "wdad_detect_all_host", "wdad_window_census", "wdad_auc",
+                 "wdad_detect_all_noalloc"):
         getattr(L, name).restype = i32
     L.wdad_query_K.restype = i32
     _lib = L
@@ -193,6 +195,24 @@ def wdad_detect_all_host(cube, reduce: bool = True, params=None, out=None, devic
     h = handle(device)
     st = ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
     _check(lib().wdad_detect_all_host(h, cube.data_ptr(), H, W, L, int(bool(reduce)), n, arr, out.data_ptr(), st), h)
+    return out
+
+
+def wdad_detect_all_noalloc(cube, params: wdad_params | None = None, out=None, flags=None, **over):
+    """Reduced LRX, DWRX, DWEST pass [3, H, W] with no device allocation inside the
+    library (for callers that cannot call cudaMalloc; limits and sharing rules in
+    include/wdad.h).  `out` may be given to avoid the allocation of the result here."""
+    import torch
+    cube = _cube(cube)
+    p = _params(params, over)
+    H, W, L = cube.shape
+    if out is None:
+        out = torch.empty((3, H, W), device=cube.device, dtype=torch.float32)
+    with torch.cuda.device(cube.device):
+        st = lib().wdad_detect_all_noalloc(cube.data_ptr(), H, W, L, ctypes.byref(p), out.data_ptr(),
+                                           flags.data_ptr() if flags is not None else None, _stream(cube))
+    if st != WDAD_OK:
+        raise WdadError(st, "wdad_detect_all_noalloc")
     return out
 
 
