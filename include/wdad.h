@@ -119,6 +119,15 @@ wdad_status wdad_detect_all(wdad_handle h, const float* cube, int H, int W, int 
 wdad_status wdad_detect_all_host(wdad_handle h, const float* host_cube, int H, int W, int L, int reduce,
                                  int nwin, const wdad_params* params, float* host_scores, void* stream);
 
+/* A3 — background statistics of listed pixels (Sec. 2.1, Sec. 2.2): mean mu_o and covariance
+ * C_o = (1/N) sum (x - mu_o)(x - mu_o)^T over the annulus between p->inner and p->outer
+ * (reflect-101 borders), on the L-band cube as given.  pixels: device int64 [npix] linear
+ * indices y*W + x; mu_o: device [npix][L]; cov_o: device [npix][L][L] row-major (both
+ * triangles).  p->precision selects the Gram: FP32 SIMT, MIXED = BF16 tensor cores with
+ * FP32 accumulation (L <= 256; larger L uses FP32), FP64.  L <= 1024. */
+wdad_status wdad_window_moments(wdad_handle h, const float* cube, int H, int W, int L, const int64_t* pixels,
+                                int64_t npix, const wdad_params* p, float* mu_o, float* cov_o, void* stream);
+
 /* A2 — window census computed by the same tile loader and box-sum code as the
  * reduced detectors, with an integer payload: for every pixel, over the
  * background annulus and over the inner window (Sec. 2.2 dual window with

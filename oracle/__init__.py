@@ -57,6 +57,8 @@ def lib():
                                 ctypes.c_int64, dp, dp, ctypes.c_int, ctypes.c_int]
         L.or_window_census.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                        i64p, ctypes.c_int64, i64p]
+        L.or_window_moments.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        i64p, ctypes.c_int64, dp, dp, ctypes.c_int]
         L.or_auc.argtypes = [dp, u8p, ctypes.c_int64]
         L.or_auc.restype = ctypes.c_double
         _lib = L
@@ -153,6 +155,19 @@ def detect(cube: np.ndarray, detector: int, inner: int, outer: int, loading: flo
         if want_aux:
             aux = aux.reshape(H, W, NAUX)
     return (score, aux) if want_aux else score
+
+
+def window_moments(cube: np.ndarray, inner: int, outer: int, pixels, nthreads: int = 0):
+    """Background mean [n, D] and covariance [n, D, D] (1/N) of the listed pixels (Sec. 2.1)."""
+    c = np.ascontiguousarray(cube, dtype=np.float64)
+    H, W, D = c.shape
+    pix = np.ascontiguousarray(pixels, dtype=np.int64)
+    mu = np.zeros((len(pix), D))
+    cov = np.zeros((len(pix), D, D))
+    if lib().or_window_moments(_ptr(c, ctypes.c_double), H, W, D, inner, outer, _ptr(pix, ctypes.c_int64), len(pix),
+                               _ptr(mu, ctypes.c_double), _ptr(cov, ctypes.c_double), nthreads) != 0:
+        raise ValueError("bad window")
+    return mu, cov
 
 
 def window_census(H: int, W: int, inner: int, outer: int, border: int = 0, pixels=None) -> np.ndarray:

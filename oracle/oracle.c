@@ -492,6 +492,44 @@ int or_detect(const double* cube, int H, int W, int D, int det, int inner, int o
     return 0;
 }
 
+/* Background statistics of listed pixels (Sec. 2.1): mean and covariance (1/N, two
+ * passes) over the annulus; mu [npix][D], cov [npix][D][D]. */
+int or_window_moments(const double* cube, int H, int W, int D, int inner, int outer, const int64_t* pix,
+                      int64_t npix, double* mu, double* cov, int nthreads) {
+    if (inner < 1 || outer <= inner || !(inner & 1) || !(outer & 1) || D < 1) return -1;
+    int nmax = outer * outer;
+    int* in_dy = (int*)malloc(sizeof(int) * nmax);
+    int* in_dx = (int*)malloc(sizeof(int) * nmax);
+    int* bg_dy = (int*)malloc(sizeof(int) * nmax);
+    int* bg_dx = (int*)malloc(sizeof(int) * nmax);
+    int N;
+    window_lists(inner, outer, in_dy, in_dx, bg_dy, bg_dx, &N);
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+#pragma omp parallel for schedule(dynamic, 2)
+    for (int64_t t = 0; t < npix; ++t) {
+        int py = (int)(pix[t] / W), px = (int)(pix[t] % W);
+        double* m = mu + t * D;
+        double* c = cov + t * (int64_t)D * D;
+        for (int k = 0; k < D; ++k) m[k] = 0.0;
+        for (int s = 0; s < N; ++s) {
+            const double* x = cube + ((int64_t)or_reflect(py + bg_dy[s], H) * W + or_reflect(px + bg_dx[s], W)) * D;
+            for (int k = 0; k < D; ++k) m[k] += x[k];
+        }
+        for (int k = 0; k < D; ++k) m[k] /= N;
+        for (int64_t i = 0; i < (int64_t)D * D; ++i) c[i] = 0.0;
+        for (int s = 0; s < N; ++s) {
+            const double* x = cube + ((int64_t)or_reflect(py + bg_dy[s], H) * W + or_reflect(px + bg_dx[s], W)) * D;
+            for (int a = 0; a < D; ++a)
+                for (int b = 0; b < D; ++b) c[(int64_t)a * D + b] += (x[a] - m[a]) * (x[b] - m[b]);
+        }
+        for (int64_t i = 0; i < (int64_t)D * D; ++i) c[i] /= N;
+    }
+    free(in_dy); free(in_dx); free(bg_dy); free(bg_dx);
+    return 0;
+}
+
 /* Window census: for every listed pixel, the background and inner multisets as
  * (count, sum of linear indices, sum of squared linear indices).  Integer and
  * exact; used to pin the reflect-101 window indexing. */

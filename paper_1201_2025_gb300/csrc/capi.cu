@@ -376,6 +376,35 @@ wdad_status wdad_detect_all_host(wdad_handle h, const float* host_cube, int H, i
     }
 }
 
+wdad_status wdad_window_moments(wdad_handle h, const float* cube, int H, int W, int L, const int64_t* pixels,
+                                int64_t npix, const wdad_params* p, float* mu_o, float* cov_o, void* stream) {
+    if (!h) return WDAD_ERR_ARG;
+    try {
+        DeviceGuard g(h->device);
+        wdad_status st = check_params(h, p);
+        if (st != WDAD_OK) return st;
+        st = check_cube(h, cube, H, W, L);
+        if (st != WDAD_OK) return st;
+        if (npix < 0) return fail(h, WDAD_ERR_ARG, "npix must be >= 0");
+        if (npix == 0) return WDAD_OK;
+        if (!pixels || !mu_o || !cov_o) return fail(h, WDAD_ERR_ARG, "pixels, mu_o and cov_o must not be NULL");
+        if (L > 1024) return fail(h, WDAD_ERR_UNSUPPORTED, "window moments for more than 1024 bands");
+        wdad::FullArgs a{};
+        a.x = cube; a.H = H; a.W = W; a.D = L;
+        a.inner = p->inner; a.outer = p->outer; a.precision = p->precision;
+        const size_t need = wdad::moments_workspace_bytes(a, npix, h->num_sms);
+        if (need == 0) return fail(h, WDAD_ERR_UNSUPPORTED, "window moments for %d bands", L);
+        st = ensure_ws(h, need);
+        if (st != WDAD_OK) return st;
+        cudaError_t e = wdad::launch_window_moments(a, pixels, npix, mu_o, cov_o, h->ws, h->ws_bytes, h->num_sms,
+                                                    (cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "window moments launch");
+        return WDAD_OK;
+    } catch (...) {
+        return fail(h, WDAD_ERR_NOMEM, "host exception");
+    }
+}
+
 wdad_status wdad_window_census(wdad_handle h, int H, int W, const wdad_params* p, int64_t* out, void* stream) {
     if (!h) return WDAD_ERR_ARG;
     DeviceGuard g(h->device);

@@ -20,6 +20,7 @@
 #include <float.h>
 
 #include "internal.h"
+#include "tc.cuh"
 
 namespace wdad {
 namespace {
@@ -136,6 +137,7 @@ struct Smem {
 struct Geo {
     int D, Dp, nt, ntl, S, mcap;
     bool a_in_smem;
+    bool tc;  // window Gram on the tensor cores (mixed precision, D <= 256)
 };
 
 __host__ __device__ inline int fb_chunk(int elem_size) { return elem_size == 4 ? 32 : 8; }
@@ -144,6 +146,7 @@ template <typename T>
 __host__ __device__ inline size_t fb_smem_vectors_bytes(int Dp, int S, int mcap) {
     return sizeof(T) * ((size_t)S * Dp + 8 * (size_t)Dp + 3 * (size_t)mcap + FB_WARPS) + 16;
 }
+constexpr size_t kTcBufBytes = 2 * 256 * 64 * 2;  // two BF16 chunk buffers (TC_MB x TC_KC)
 
 // ---- statistics ---------------------------------------------------------------
 // mean over a sample list (kind 0 = background, 1 = inner) into out[0..Dp)
@@ -205,6 +208,117 @@ __device__ void gram_accumulate(const float* __restrict__ x, int H, int W, const
             tile_store(A, ntl, u, acc);
         }
     }
+    __syncthreads();
+}
+
+// ---- BF16 window Gram on the tensor cores (mixed precision).
+// The centred, scaled samples of one chunk are stored transposed, [band][sample], as
+// BF16 in the canonical K-major layout of 8 x 16-byte core matrices: element (b, s) at
+// byte (b/8)*KC*16 + (s/8)*128 + (b%8)*16 + (s%8)*2.  G = X^T X then reads the same
+// buffer as A (M = 128 bands per tile) and as B (N = all bands of the lower block
+// triangle), K = 16 samples per MMA; FP32 sums accumulate in tensor memory: tile 0
+// (bands 0..127 x 0..127) in columns [0, 128), tile 1 (bands 128..255 x 0..255) in
+// columns [128, 384).  Two chunk buffers alternate; each is reused only after the
+// tensor cores have signalled (commit -> mbarrier) that they finished reading it.
+constexpr int TC_KC = 64;          // samples per chunk
+constexpr int TC_MB = 256;         // band rows held per chunk buffer (D <= 256)
+constexpr uint32_t TC_COLS = 512;  // tensor-memory columns allocated per CTA
+constexpr uint32_t TC_WAIT = 1u << 26;
+
+struct TcState {
+    __nv_bfloat16* buf[2];  // 2 x TC_MB x TC_KC
+    uint64_t* bar;          // [2] mbarriers
+    uint32_t tmem;          // tensor-memory base address
+    uint32_t uses[2];       // completed-phase counters per buffer
+    int* err;               // shared error word
+};
+
+__device__ __forceinline__ uint32_t tc_off(int b, int s) {
+    return (uint32_t)((b >> 3) * (TC_KC * 16) + (s >> 3) * 128 + (b & 7) * 16 + (s & 7) * 2);
+}
+
+// A += scale * (X^T X) over the n samples of one list, X = sc (x - mu) (FP32 packed SoA A)
+__device__ void gram_tc(const float* __restrict__ x, int H, int W, const Geo& g, int py, int px, int kind, int n,
+                        int ro, int ri, const float* mu, float scale, float* A, TcState& st) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int MT = (g.Dp + 127) / 128;  // 1 or 2 band tiles
+    const int nchunk = (n + TC_KC - 1) / TC_KC;
+    const uint32_t id128 = tc::idesc_bf16_f32(128, 128), id256 = tc::idesc_bf16_f32(128, 256);
+    for (int c = 0; c < nchunk; ++c) {
+        const int b = c & 1;
+        // the tensor cores must be done with this buffer (chunk c - 2)
+        if (c >= 2) {
+            if (!tc::mbar_wait_bounded(&st.bar[b], st.uses[b] & 1, TC_WAIT)) *st.err = 1;
+            ++st.uses[b];
+        }
+        __syncthreads();
+        if (*st.err) return;
+        // fill: one task = 8 consecutive samples x 32 consecutive bands (lane = band)
+        __nv_bfloat16* buf = st.buf[b];
+        const int ntask = (TC_KC / 8) * (TC_MB / 32);
+        for (int t = warp; t < ntask; t += FB_WARPS) {
+            const int so = (t % (TC_KC / 8)) * 8, bg = (t / (TC_KC / 8)) * 32;
+            const int band = bg + lane;
+            const float m = band < g.D ? mu[band] : 0.f;
+            __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int s = c * TC_KC + so + e;
+                float val = 0.f;
+                if (s < n && band < g.D) {
+                    int dy, dx;
+                    if (kind == 0) bg_offset(s, ro, ri, dy, dx); else in_offset(s, ri, dy, dx);
+                    const size_t q = (size_t)reflect101(py + dy, H) * W + reflect101(px + dx, W);
+                    val = __ldg(x + q * g.D + band) - m;
+                }
+                v[e] = __float2bfloat16_rn(val);
+            }
+            *reinterpret_cast<uint4*>(reinterpret_cast<char*>(buf) + tc_off(band, so)) =
+                *reinterpret_cast<const uint4*>(v);
+        }
+        tc::fence_proxy_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tc::fence_after_sync();
+            const uint32_t base = tc::smem_u32(buf);
+#pragma unroll
+            for (int k = 0; k < TC_KC / 16; ++k) {
+                const uint32_t koff = (uint32_t)k * 256;  // two core matrices along K
+                for (int mt = 0; mt < MT; ++mt) {
+                    const uint64_t ad = tc::smem_desc(base + (uint32_t)mt * 16 * (TC_KC * 16) + koff, 128, TC_KC * 16);
+                    const uint64_t bd = tc::smem_desc(base + koff, 128, TC_KC * 16);
+                    tc::mma_bf16(st.tmem + (uint32_t)(mt * 128), ad, bd, mt == 0 ? id128 : id256, c > 0 || k > 0);
+                }
+            }
+            tc::commit(&st.bar[b]);
+        }
+    }
+    // drain the last one or two chunks
+    for (int c = (nchunk >= 2 ? nchunk - 2 : 0); c < nchunk; ++c) {
+        const int b = c & 1;
+        if (!tc::mbar_wait_bounded(&st.bar[b], st.uses[b] & 1, TC_WAIT)) *st.err = 1;
+        ++st.uses[b];
+    }
+    __syncthreads();
+    if (*st.err) return;
+    tc::fence_after_sync();
+    // read back: warps 0..3 own tensor-memory lanes 0..127 (one band row each)
+    if (warp < 4) {
+        for (int mt = 0; mt < MT; ++mt) {
+            const int r = mt * 128 + warp * 32 + lane;
+            const int ncol = (mt + 1) * 128;
+            for (int c0 = 0; c0 < ncol; c0 += 16) {
+                float v[16];
+                tc::tmem_ld16(st.tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(mt * 128 + c0), v);
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    const int col = c0 + e;
+                    if (r < g.D && col <= r) el(A, g.ntl, r, col) += scale * v[e];
+                }
+            }
+        }
+    }
+    tc::fence_before_sync();
     __syncthreads();
 }
 
@@ -555,12 +669,21 @@ __global__ void __launch_bounds__(FB_THREADS, 1) fullband_kernel(FullArgs a, Geo
     __shared__ T s_bounds[4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     char* slab = ws + (size_t)blockIdx.x * slab_bytes;
+    __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_err;
+    TcState st{};
     // layout
     Smem<T> m;
     {
-        char* sp = reinterpret_cast<char*>(smem_raw);
+        char* sp = reinterpret_cast<char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
         size_t off = 0;
-        if (g.a_in_smem) { m.A = reinterpret_cast<T*>(sp); off += sizeof(T) * ntiles_of(g.nt) * 16; }
+        if (g.tc) {
+            st.buf[0] = reinterpret_cast<__nv_bfloat16*>(sp);
+            st.buf[1] = reinterpret_cast<__nv_bfloat16*>(sp + kTcBufBytes / 2);
+            off += kTcBufBytes;
+        }
+        if (g.a_in_smem) { m.A = reinterpret_cast<T*>(sp + off); off += sizeof(T) * ntiles_of(g.nt) * 16; }
         T* base = reinterpret_cast<T*>(sp + off);
         m.xs = base;
         base += (size_t)g.S * g.Dp;
@@ -594,6 +717,24 @@ __global__ void __launch_bounds__(FB_THREADS, 1) fullband_kernel(FullArgs a, Geo
     const int64_t P = (int64_t)a.H * a.W;
     const bool want_rx = a.out[0] || a.out[1];
     const float fnan = __int_as_float(0x7fc00000);
+    if (g.tc) {
+        if (threadIdx.x == 0) {
+            s_err = 0;
+            tc::mbar_init(&s_bar[0], 1);
+            tc::mbar_init(&s_bar[1], 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        if (warp == 0) {
+            tc::tmem_alloc(&s_tmem, TC_COLS);
+            tc::tmem_relinquish();
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        st.bar = s_bar;
+        st.tmem = s_tmem;
+        st.err = &s_err;
+    }
 
     for (int64_t pix = blockIdx.x; pix < P; pix += gridDim.x) {
         const int py = (int)(pix / a.W), px = (int)(pix % a.W);
@@ -614,8 +755,13 @@ __global__ void __launch_bounds__(FB_THREADS, 1) fullband_kernel(FullArgs a, Geo
                 m.r2[b] = b < D ? m.mu_i[b] - m.mu_o[b] : T(0);
             }
             mat_zero(m.A, g);
-            gram_accumulate<T>(a.x, a.H, a.W, g, py, px, 0, N, ro, ri, m.mu_o, T(1), m.A, m.xs);
-            mat_scale(m.A, g, T(1) / (T)N);
+            if constexpr (sizeof(T) == 4) {
+                if (g.tc) gram_tc(a.x, a.H, a.W, g, py, px, 0, N, ro, ri, m.mu_o, 1.f / (float)N, m.A, st);
+            }
+            if (!g.tc) {
+                gram_accumulate<T>(a.x, a.H, a.W, g, py, px, 0, N, ro, ri, m.mu_o, T(1), m.A, m.xs);
+                mat_scale(m.A, g, T(1) / (T)N);
+            }
             T tr = T(0), dmax = T(0);
             for (int b = threadIdx.x; b < D; b += FB_THREADS) { tr += el(m.A, g.ntl, b, b); dmax = max(dmax, el(m.A, g.ntl, b, b)); }
             tr = block_sum(tr, m.red);
@@ -646,10 +792,18 @@ __global__ void __launch_bounds__(FB_THREADS, 1) fullband_kernel(FullArgs a, Geo
             // C_diff = C_i - C_o (Eq. 2)
             for (int b = threadIdx.x; b < g.Dp; b += FB_THREADS) m.r2[b] = b < D ? m.mu_i[b] - m.mu_o[b] : T(0);
             mat_zero(m.A, g);
-            gram_accumulate<T>(a.x, a.H, a.W, g, py, px, 0, N, ro, ri, m.mu_o, T(1), m.A, m.xs);
-            mat_scale(m.A, g, T(-1) / (T)N);
-            gram_accumulate<T>(a.x, a.H, a.W, g, py, px, 1, ni, ro, ri, m.mu_i, T(1) / Num<T>::sqrt_((T)ni), m.A,
-                               m.xs);
+            if constexpr (sizeof(T) == 4) {
+                if (g.tc) {
+                    gram_tc(a.x, a.H, a.W, g, py, px, 0, N, ro, ri, m.mu_o, -1.f / (float)N, m.A, st);
+                    gram_tc(a.x, a.H, a.W, g, py, px, 1, ni, ro, ri, m.mu_i, 1.f / (float)ni, m.A, st);
+                }
+            }
+            if (!g.tc) {
+                gram_accumulate<T>(a.x, a.H, a.W, g, py, px, 0, N, ro, ri, m.mu_o, T(1), m.A, m.xs);
+                mat_scale(m.A, g, T(-1) / (T)N);
+                gram_accumulate<T>(a.x, a.H, a.W, g, py, px, 1, ni, ro, ri, m.mu_i, T(1) / Num<T>::sqrt_((T)ni), m.A,
+                                   m.xs);
+            }
             tridiagonalise(m.A, g, m.v, m.p, m.dd, m.ee, m.red);
             // spectrum bounds (Gershgorin), extreme eigenvalues, threshold, count above it
             T glo, ghi;
@@ -747,6 +901,100 @@ __global__ void __launch_bounds__(FB_THREADS, 1) fullband_kernel(FullArgs a, Geo
         }
         if (threadIdx.x == 0 && a.flags) a.flags[pix] = flag;
     }
+    if (g.tc) {
+        __syncthreads();
+        if (s_err) {  // a wait gave up: give the tensor cores a last bounded chance to finish
+            tc::mbar_wait_bounded(&s_bar[0], st.uses[0] & 1, TC_WAIT);
+            tc::mbar_wait_bounded(&s_bar[1], st.uses[1] & 1, TC_WAIT);
+            if (threadIdx.x == 0 && a.status) atomicExch(a.status, (int)WDAD_ERR_TIMEOUT);
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (warp == 0) tc::tmem_dealloc(st.tmem, TC_COLS);
+    }
+}
+
+// A3 alone: background mean and covariance (1/N) of the listed pixels, written out
+// densely (cov [npix][D][D], row-major, both triangles).  Same statistics code as the
+// detectors: SIMT Gram (FP32 / FP64) or the BF16 tensor-core Gram (mixed precision).
+template <typename T>
+__global__ void __launch_bounds__(FB_THREADS, 1) moments_kernel(FullArgs a, Geo g, const int64_t* __restrict__ pix,
+                                                                 int64_t npix, float* __restrict__ mu_out,
+                                                                 float* __restrict__ cov_out, char* ws,
+                                                                 size_t slab_bytes) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_err;
+    const int warp = threadIdx.x >> 5;
+    char* slab = ws + (size_t)blockIdx.x * slab_bytes;
+    TcState st{};
+    char* sp = reinterpret_cast<char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    size_t off = 0;
+    if (g.tc) {
+        st.buf[0] = reinterpret_cast<__nv_bfloat16*>(sp);
+        st.buf[1] = reinterpret_cast<__nv_bfloat16*>(sp + kTcBufBytes / 2);
+        off += kTcBufBytes;
+    }
+    T* A;
+    if (g.a_in_smem) { A = reinterpret_cast<T*>(sp + off); off += sizeof(T) * ntiles_of(g.nt) * 16; }
+    else A = reinterpret_cast<T*>(slab);
+    T* xs = reinterpret_cast<T*>(sp + off);
+    T* mu = xs + (size_t)g.S * g.Dp;
+    if (g.tc) {
+        if (threadIdx.x == 0) {
+            s_err = 0;
+            tc::mbar_init(&s_bar[0], 1);
+            tc::mbar_init(&s_bar[1], 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        if (warp == 0) {
+            tc::tmem_alloc(&s_tmem, TC_COLS);
+            tc::tmem_relinquish();
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        st.bar = s_bar;
+        st.tmem = s_tmem;
+        st.err = &s_err;
+    }
+    const int ro = a.outer / 2, ri = a.inner / 2;
+    const int N = a.outer * a.outer - a.inner * a.inner;
+    const int D = g.D;
+    for (int64_t t = blockIdx.x; t < npix; t += gridDim.x) {
+        const int64_t p = pix[t];
+        const int py = (int)(p / a.W), px = (int)(p % a.W);
+        __syncthreads();
+        sample_mean<T>(a.x, a.H, a.W, D, g.Dp, py, px, 0, N, ro, ri, mu);
+        __syncthreads();
+        mat_zero(A, g);
+        if constexpr (sizeof(T) == 4) {
+            if (g.tc) gram_tc(a.x, a.H, a.W, g, py, px, 0, N, ro, ri, mu, 1.f / (float)N, A, st);
+        }
+        if (!g.tc) {
+            gram_accumulate<T>(a.x, a.H, a.W, g, py, px, 0, N, ro, ri, mu, T(1), A, xs);
+            mat_scale(A, g, T(1) / (T)N);
+        }
+        for (int b = threadIdx.x; b < D; b += FB_THREADS) mu_out[t * D + b] = (float)mu[b];
+        for (int e = threadIdx.x; e < D * D; e += FB_THREADS) {
+            const int r = e / D, c = e % D;
+            cov_out[t * D * D + e] = (float)(r >= c ? el(A, g.ntl, r, c) : el(A, g.ntl, c, r));
+        }
+    }
+    if (g.tc) {
+        __syncthreads();
+        if (s_err) {
+            tc::mbar_wait_bounded(&s_bar[0], st.uses[0] & 1, TC_WAIT);
+            tc::mbar_wait_bounded(&s_bar[1], st.uses[1] & 1, TC_WAIT);
+            if (threadIdx.x == 0 && a.status) atomicExch(a.status, (int)WDAD_ERR_TIMEOUT);
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (warp == 0) tc::tmem_dealloc(st.tmem, TC_COLS);
+    }
 }
 
 template <typename T>
@@ -761,8 +1009,10 @@ Geo make_geo(const FullArgs& a, bool* smem_ok, size_t* smem_bytes, size_t* slab)
     g.mcap = std::min(g.Dp, ni + 16);
     const size_t amat = sizeof(T) * (size_t)ntiles_of(g.nt) * 16;
     const size_t vecs = fb_smem_vectors_bytes<T>(g.Dp, g.S, g.mcap);
-    g.a_in_smem = (sizeof(T) == 4) && (amat + vecs <= 200 * 1024);
-    *smem_bytes = vecs + (g.a_in_smem ? amat : 0);
+    g.tc = (sizeof(T) == 4) && a.precision == WDAD_PREC_MIXED && a.D <= 256;
+    const size_t tcb = g.tc ? kTcBufBytes : 0;
+    g.a_in_smem = (sizeof(T) == 4) && (amat + vecs + tcb <= 210 * 1024);
+    *smem_bytes = vecs + tcb + (g.a_in_smem ? amat : 0) + 1024;  // + alignment slack
     *smem_ok = *smem_bytes <= 227 * 1024;
     *slab = (g.a_in_smem ? 0 : amat) + sizeof(T) * (size_t)g.mcap * g.Dp * 6 + sizeof(int) * (size_t)g.mcap * g.Dp;
     *slab = (*slab + 255) & ~(size_t)255;
@@ -799,6 +1049,39 @@ static cudaError_t launch_fb(const FullArgs& a, void* ws, int num_sms, cudaStrea
     char* base = reinterpret_cast<char*>(((uintptr_t)ws + 255) & ~(uintptr_t)255);
     fullband_kernel<T><<<grid, FB_THREADS, smem, s>>>(a, g, base, slab);
     return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t launch_mom(const FullArgs& a, const int64_t* pix, int64_t npix, float* mu, float* cov, void* ws,
+                              int num_sms, cudaStream_t s) {
+    bool ok;
+    size_t smem, slab;
+    const Geo g = make_geo<T>(a, &ok, &smem, &slab);
+    if (!ok) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(moments_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int grid = fb_grid(num_sms, npix);
+    char* base = reinterpret_cast<char*>(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+    moments_kernel<T><<<grid, FB_THREADS, smem, s>>>(a, g, pix, npix, mu, cov, base, slab);
+    return cudaGetLastError();
+}
+
+size_t moments_workspace_bytes(const FullArgs& a, int64_t npix, int num_sms) {
+    if (a.D < 1 || a.D > 1024) return 0;
+    bool ok;
+    size_t smem, slab;
+    if (a.precision == WDAD_PREC_FP64) make_geo<double>(a, &ok, &smem, &slab);
+    else make_geo<float>(a, &ok, &smem, &slab);
+    if (!ok) return 0;
+    return slab * (size_t)fb_grid(num_sms, npix) + 256;
+}
+
+cudaError_t launch_window_moments(const FullArgs& a, const int64_t* pix, int64_t npix, float* mu, float* cov, void* ws,
+                                  size_t ws_bytes, int num_sms, cudaStream_t s) {
+    if (npix == 0) return cudaSuccess;
+    if (ws_bytes < moments_workspace_bytes(a, npix, num_sms)) return cudaErrorInvalidValue;
+    if (a.precision == WDAD_PREC_FP64) return launch_mom<double>(a, pix, npix, mu, cov, ws, num_sms, s);
+    return launch_mom<float>(a, pix, npix, mu, cov, ws, num_sms, s);
 }
 
 cudaError_t launch_detect_full(const FullArgs& a, void* ws, size_t ws_bytes, int num_sms, cudaStream_t s) {

@@ -68,8 +68,12 @@ struct FullArgs {
     float dwest_tau;
     float* out[3];
     uint8_t* flags;
+    int* status;  // nullable device word: set to a wdad_status when a bounded wait gives up
 };
 size_t fullband_workspace_bytes(const FullArgs& a, int num_sms);
 cudaError_t launch_detect_full(const FullArgs& a, void* ws, size_t ws_bytes, int num_sms, cudaStream_t s);
+size_t moments_workspace_bytes(const FullArgs& a, int64_t npix, int num_sms);
+cudaError_t launch_window_moments(const FullArgs& a, const int64_t* pix, int64_t npix, float* mu, float* cov, void* ws,
+                                  size_t ws_bytes, int num_sms, cudaStream_t s);
 
 }  // namespace wdad

@@ -61,11 +61,12 @@ def lib() -> ctypes.CDLL:
     L.wdad_detect_all.argtypes = [vp, f32p, i32, i32, i32, i32, pp, f32p, vp, vp]
     L.wdad_detect_all_host.argtypes = [vp, vp, i32, i32, i32, i32, i32, pp, vp, vp]
     L.wdad_window_census.argtypes = [vp, i32, i32, pp, vp, vp]
+    L.wdad_window_moments.argtypes = [vp, f32p, i32, i32, i32, vp, i64, pp, f32p, f32p, vp]
     L.wdad_detect_all_noalloc.argtypes = [f32p, i32, i32, i32, pp, f32p, vp, vp]
     L.wdad_auc.argtypes = [vp, vp, i64, ctypes.POINTER(ctypes.c_double)]
     for name in ("wdad_create", "wdad_destroy", "wdad_last_error_detail", "wdad_dwt_approx", "wdad_detect",
                  "wdad_detect_all", "wdad_detect_all_host", "wdad_window_census", "wdad_auc",
-                 "wdad_detect_all_noalloc"):
+                 "wdad_detect_all_noalloc", "wdad_window_moments"):
         getattr(L, name).restype = i32
     L.wdad_query_K.restype = i32
     _lib = L
@@ -214,6 +215,22 @@ def wdad_detect_all_noalloc(cube, params: wdad_params | None = None, out=None, f
     if st != WDAD_OK:
         raise WdadError(st, "wdad_detect_all_noalloc")
     return out
+
+
+def wdad_window_moments(cube, pixels, params: wdad_params | None = None, **over):
+    """A3: background mean [npix, L] and covariance [npix, L, L] of the listed pixels."""
+    import torch
+    cube = _cube(cube)
+    p = _params(params, over)
+    H, W, L = cube.shape
+    pix = torch.as_tensor(pixels, dtype=torch.int64).to(cube.device).contiguous()
+    n = pix.numel()
+    mu = torch.empty((n, L), device=cube.device, dtype=torch.float32)
+    cov = torch.empty((n, L, L), device=cube.device, dtype=torch.float32)
+    h = handle(cube.device.index or 0)
+    _check(lib().wdad_window_moments(h, cube.data_ptr(), H, W, L, pix.data_ptr(), n, ctypes.byref(p), mu.data_ptr(),
+                                     cov.data_ptr(), _stream(cube)), h)
+    return mu, cov
 
 
 def wdad_window_census(H: int, W: int, params: wdad_params | None = None, device: int = 0, **over):

@@ -1,0 +1,78 @@
+"""Mixed precision (A7): the BF16 tensor-core window Gram, its FP32/FP64 siblings, and the
+condition-gated full-band detectors, against the FP64 oracle through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def wd():
+    from paper_1201_2025_gb300 import wdad
+    wdad.lib()
+    return wdad
+
+
+@pytest.fixture(scope="module")
+def scene48():
+    from paper_1201_2025_gb300 import synth
+    return synth.scene_48x48(0)
+
+
+def _gpu(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def bf16_round(x):
+    """Round float32 values to bfloat16 (nearest, ties to even), returned as float32."""
+    b = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    return r.view(np.float32)
+
+
+def _annulus(cube, y, x, wi, wo):
+    H, W, _ = cube.shape
+    ri, ro = wi // 2, wo // 2
+    return np.array([cube[oracle.reflect(y + dy, H), oracle.reflect(x + dx, W)]
+                     for dy in range(-ro, ro + 1) for dx in range(-ro, ro + 1) if max(abs(dy), abs(dx)) > ri])
+
+
+def _pixels(H, W, n=12, seed=0):
+    rng = np.random.default_rng(seed)
+    return np.unique(np.concatenate([rng.choice(H * W, n, replace=False), [0, H * W - 1, W - 1]]))
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-5), (2, 1e-6)])
+def test_window_moments_simt_vs_oracle(wd, scene48, prec, tol):
+    cube = scene48.cube
+    pix = _pixels(48, 48)
+    mu, cov = wd.wdad_window_moments(_gpu(cube), pix, inner=3, outer=11, precision=prec)
+    mu_r, cov_r = oracle.window_moments(cube.astype(np.float64), 3, 11, pix)
+    np.testing.assert_allclose(mu.cpu().numpy(), mu_r, rtol=1e-6, atol=0)
+    err = np.abs(cov.cpu().numpy() - cov_r).max(axis=(1, 2)) / np.abs(cov_r).max(axis=(1, 2))
+    assert err.max() <= tol, err.max()
+
+
+@pytest.mark.parametrize("D,win", [(224, (3, 11)), (100, (7, 21)), (256, (5, 15))])
+def test_tensor_core_gram_is_the_bf16_gram(wd, D, win):
+    """The MIXED Gram equals the FP64 Gram of the BF16-rounded centred samples (up to FP32
+    accumulation), and is within the BF16 rounding level of the exact covariance."""
+    rng = np.random.default_rng(D)
+    H, W = 23, 29
+    cube = (0.3 + 0.1 * rng.standard_normal((H, W, D)) @ (np.eye(D) + 0.05 * rng.standard_normal((D, D)))
+            ).astype(np.float32)
+    pix = _pixels(H, W, n=6, seed=D)
+    mu, cov = wd.wdad_window_moments(_gpu(cube), pix, inner=win[0], outer=win[1], precision=1)
+    mu, cov = mu.cpu().numpy(), cov.cpu().numpy()
+    _, cov_exact = oracle.window_moments(cube.astype(np.float64), win[0], win[1], pix)
+    for t, p in enumerate(pix):
+        y, x = divmod(int(p), W)
+        X = _annulus(cube, y, x, *win)  # [N][D] float32
+        Xc = bf16_round(X - mu[t][None, :].astype(np.float32)).astype(np.float64)
+        ref = Xc.T @ Xc / X.shape[0]
+        scale = np.abs(ref).max()
+        assert np.abs(cov[t] - ref).max() <= 2e-6 * scale, (t, np.abs(cov[t] - ref).max() / scale)
+        assert np.abs(cov[t] - cov_exact[t]).max() <= 2.0 ** -7 * np.abs(cov_exact[t]).max()

@@ -153,6 +153,21 @@ def test_window_census_interior_closed_form():
     assert got[0][0] == wo * wo - wi * wi
 
 
+def test_window_moments_match_numpy_cov_on_explicit_windows():
+    rng = np.random.default_rng(21)
+    H, W, D = 9, 12, 5
+    cube = rng.standard_normal((H, W, D))
+    pix = [0, 13, 57, H * W - 1]
+    mu, cov = oracle.window_moments(cube, 3, 7, pix)
+    for t, p in enumerate(pix):
+        y, x = divmod(p, W)
+        bg = [cube[oracle.reflect(y + dy, H), oracle.reflect(x + dx, W)]
+              for dy in range(-3, 4) for dx in range(-3, 4) if max(abs(dy), abs(dx)) > 1]
+        bg = np.array(bg)
+        np.testing.assert_allclose(mu[t], bg.mean(0), atol=1e-13)
+        np.testing.assert_allclose(cov[t], np.cov(bg.T, bias=True), atol=1e-12)
+
+
 def test_valid_border_mode_gives_nan():
     cube = np.random.default_rng(0).standard_normal((12, 12, 3))
     s = oracle.detect(cube, 0, 1, 5, border=1)
