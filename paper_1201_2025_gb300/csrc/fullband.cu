@@ -661,62 +661,291 @@ __device__ void warp_sign_proj(const T* v, const T* w, int n, T& sgn, T& proj) {
     proj = pr;
 }
 
+// Scratch of one pixel's pipeline: shared-memory vectors (or slab vectors for the FP64
+// re-solve) and slab arrays for the eigenvectors and the inverse-iteration factors.
 template <typename T>
-__global__ void __launch_bounds__(FB_THREADS, 1) fullband_kernel(FullArgs a, Geo g, char* ws, size_t slab_bytes) {
+struct Scratch {
+    T *Y, *Ld, *Lu, *Lu2, *Lf;
+    int* piv;
+};
+
+template <typename T>
+__device__ void carve(char* base, const Geo& g, Smem<T>& m, Scratch<T>& sc, bool a_here, char** end) {
+    size_t off = 0;
+    if (a_here) { m.A = reinterpret_cast<T*>(base); off += sizeof(T) * (size_t)g.ntl * 16; }
+    T* v = reinterpret_cast<T*>(base + off);
+    m.xs = v; v += (size_t)g.S * g.Dp;
+    m.mu_o = v; v += g.Dp;
+    m.mu_i = v; v += g.Dp;
+    m.r1 = v; v += g.Dp;
+    m.r2 = v; v += g.Dp;
+    m.v = v; v += g.Dp;
+    m.p = v; v += g.Dp;
+    m.dd = v; v += g.Dp;
+    m.ee = v; v += g.Dp;
+    m.lam = v; v += g.mcap;
+    m.res = v; v += 2 * g.mcap;
+    m.red = v; v += FB_WARPS;
+    char* e = reinterpret_cast<char*>(((uintptr_t)v + 255) & ~(uintptr_t)255);
+    (void)sc;
+    *end = e;
+}
+
+template <typename T>
+__device__ void carve_scratch(char* base, const Geo& g, Scratch<T>& sc, char** end) {
+    const size_t n = (size_t)g.mcap * g.Dp;
+    T* t = reinterpret_cast<T*>(base);
+    sc.Y = t; t += n;
+    sc.Ld = t; t += n;
+    sc.Lu = t; t += n;
+    sc.Lu2 = t; t += n;
+    sc.Lf = t; t += n;
+    sc.piv = reinterpret_cast<int*>(t);
+    *end = reinterpret_cast<char*>(((uintptr_t)(sc.piv + n) + 255) & ~(uintptr_t)255);
+}
+
+template <typename T>
+__host__ __device__ size_t vec_bytes(const Geo& g) {
+    return sizeof(T) * ((size_t)g.S * g.Dp + 8 * (size_t)g.Dp + 3 * (size_t)g.mcap + FB_WARPS) + 256;
+}
+template <typename T>
+__host__ __device__ size_t scratch_bytes(const Geo& g) {
+    return (sizeof(T) * 5 + sizeof(int)) * (size_t)g.mcap * g.Dp + 256;
+}
+
+// One pixel, the wanted detectors (bit d = detector d).  Returns, in mixed precision, the
+// detectors whose estimated condition exceeds cond_gate (to be re-solved in FP64).
+template <typename T>
+__device__ unsigned process_pixel(const FullArgs& a, const Geo& g, Smem<T>& m, Scratch<T>& sc, TcState* st, int64_t pix,
+                                  unsigned want, uint8_t& flag, int* sflag, int* s_m, T* s_bounds) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ro = a.outer / 2, ri = a.inner / 2;
+    const int N = a.outer * a.outer - a.inner * a.inner, ni = a.inner * a.inner;
+    const int D = g.D;
+    const int py = (int)(pix / a.W), px = (int)(pix % a.W);
+    const float fnan = __int_as_float(0x7fc00000);
+    const bool gate = g.tc;  // mixed precision: estimate the conditioning
+    unsigned redo = 0;
+    m.flag = sflag;
+    __syncthreads();
+    sample_mean<T>(a.x, a.H, a.W, D, g.Dp, py, px, 0, N, ro, ri, m.mu_o);
+    sample_mean<T>(a.x, a.H, a.W, D, g.Dp, py, px, 1, ni, ro, ri, m.mu_i);
+    __syncthreads();
+    if (want & 3u) {
+        for (int b = threadIdx.x; b < g.Dp; b += FB_THREADS) {
+            const T c = b < D ? (T)__ldg(a.x + pix * D + b) : T(0);
+            m.r1[b] = b < D ? c - m.mu_o[b] : T(0);
+            m.r2[b] = b < D ? m.mu_i[b] - m.mu_o[b] : T(0);
+        }
+        mat_zero(m.A, g);
+        if constexpr (sizeof(T) == 4) {
+            if (g.tc) gram_tc(a.x, a.H, a.W, g, py, px, 0, N, ro, ri, m.mu_o, 1.f / (float)N, m.A, *st);
+        }
+        if (!g.tc) {
+            gram_accumulate<T>(a.x, a.H, a.W, g, py, px, 0, N, ro, ri, m.mu_o, T(1), m.A, m.xs);
+            mat_scale(m.A, g, T(1) / (T)N);
+        }
+        T tr = T(0), dmax = T(0);
+        for (int b = threadIdx.x; b < D; b += FB_THREADS) {
+            tr += el(m.A, g.ntl, b, b);
+            dmax = max(dmax, el(m.A, g.ntl, b, b));
+        }
+        tr = block_sum(tr, m.red);
+        dmax = block_max(dmax, m.red);
+        const T delta = (T)a.loading * tr / (T)D;
+        for (int b = threadIdx.x; b < D; b += FB_THREADS) el(m.A, g.ntl, b, b) += delta;
+        __syncthreads();
+        bool ok = cholesky_tiles(m.A, g, T(16) * Num<T>::eps * (dmax + delta), m.flag);
+        if (ok && gate) {
+            // kappa estimate from the factor's diagonal: (max L_ii / min L_ii)^2
+            T lmax = T(0), lmin = T(3e38);
+            for (int b = threadIdx.x; b < D; b += FB_THREADS) {
+                const T l = el(m.A, g.ntl, b, b);
+                lmax = max(lmax, l);
+                lmin = min(lmin, l);
+            }
+            lmax = block_max(lmax, m.red);
+            lmin = -block_max(-lmin, m.red);
+            const T kap = (lmax / lmin) * (lmax / lmin);
+            if (!(kap <= (T)a.cond_gate)) redo |= want & 3u;
+        }
+        if (!ok && gate) redo |= want & 3u;
+        if (ok) {
+            forward_solve2(m.A, g, m.r1, m.r2);
+            T q1 = T(0), q2 = T(0);
+            for (int b = threadIdx.x; b < D; b += FB_THREADS) { q1 += m.r1[b] * m.r1[b]; q2 += m.r2[b] * m.r2[b]; }
+            q1 = block_sum(q1, m.red);
+            q2 = block_sum(q2, m.red);
+            if (threadIdx.x == 0) {
+                if ((want & 1u) && a.out[0]) a.out[0][pix] = (float)q1;
+                if ((want & 2u) && a.out[1]) a.out[1][pix] = (float)fabs(q2);
+            }
+        } else {
+            flag |= 2;
+            if (threadIdx.x == 0) {
+                if ((want & 1u) && a.out[0]) a.out[0][pix] = fnan;
+                if ((want & 2u) && a.out[1]) a.out[1][pix] = fnan;
+            }
+        }
+    }
+    if (want & 4u) {
+        // C_diff = C_i - C_o (Eq. 2)
+        for (int b = threadIdx.x; b < g.Dp; b += FB_THREADS) m.r2[b] = b < D ? m.mu_i[b] - m.mu_o[b] : T(0);
+        mat_zero(m.A, g);
+        if constexpr (sizeof(T) == 4) {
+            if (g.tc) {
+                gram_tc(a.x, a.H, a.W, g, py, px, 0, N, ro, ri, m.mu_o, -1.f / (float)N, m.A, *st);
+                gram_tc(a.x, a.H, a.W, g, py, px, 1, ni, ro, ri, m.mu_i, 1.f / (float)ni, m.A, *st);
+            }
+        }
+        if (!g.tc) {
+            gram_accumulate<T>(a.x, a.H, a.W, g, py, px, 0, N, ro, ri, m.mu_o, T(1), m.A, m.xs);
+            mat_scale(m.A, g, T(-1) / (T)N);
+            gram_accumulate<T>(a.x, a.H, a.W, g, py, px, 1, ni, ro, ri, m.mu_i, T(1) / Num<T>::sqrt_((T)ni), m.A,
+                               m.xs);
+        }
+        tridiagonalise(m.A, g, m.v, m.p, m.dd, m.ee, m.red);
+        // spectrum bounds (Gershgorin), extreme eigenvalues, threshold, count above it
+        T glo, ghi;
+        {
+            T lo = T(3e38), hi = T(-3e38);
+            for (int i = threadIdx.x; i < D; i += FB_THREADS) {
+                const T r = (i > 0 ? fabs(m.ee[i - 1]) : T(0)) + (i < D - 1 ? fabs(m.ee[i]) : T(0));
+                lo = min(lo, m.dd[i] - r);
+                hi = max(hi, m.dd[i] + r);
+            }
+            glo = -block_max(-lo, m.red);
+            ghi = block_max(hi, m.red);
+        }
+        const T tnorm = max(fabs(glo), fabs(ghi));
+        const T pivmin = max(tnorm * Num<T>::eps * Num<T>::eps, T(1e-30));
+        const T pad = tnorm * T(4) * Num<T>::eps + pivmin;
+        if (warp == 0) {
+            const T lmax = warp_bisect(m.dd, m.ee, D, D - 1, glo - pad, ghi + pad, pivmin);
+            if (lane == 0) s_bounds[0] = lmax;
+        } else if (warp == 1) {
+            const T lmin = warp_bisect(m.dd, m.ee, D, 0, glo - pad, ghi + pad, pivmin);
+            if (lane == 0) s_bounds[1] = lmin;
+        }
+        __syncthreads();
+        const T maxabs = max(fabs(s_bounds[0]), fabs(s_bounds[1]));
+        const T tau = (T)a.dwest_tau * maxabs;
+        if (threadIdx.x == 0) {
+            const int below = (maxabs > T(0)) ? sturm_below(m.dd, m.ee, D, tau, pivmin) : D;
+            *s_m = D - below;
+            if (gate && maxabs > T(0)) {
+                // selection conditioning: an eigenvalue within max|lambda| / cond_gate of tau
+                const T band = maxabs / (T)a.cond_gate;
+                const int nb = sturm_below(m.dd, m.ee, D, tau + band, pivmin) -
+                               sturm_below(m.dd, m.ee, D, tau - band, pivmin);
+                if (nb > 0) *s_m = -1 - *s_m;  // mark for the FP64 re-solve
+            }
+        }
+        __syncthreads();
+        int msel = *s_m;
+        if (msel < 0) { redo |= 4u; msel = -1 - msel; }
+        if (msel > g.mcap) { msel = g.mcap; flag |= 8; }  // more than the slab holds: top mcap kept
+        // selected eigenvalues lambda_{D-msel} .. lambda_{D-1}
+        for (int s = warp; s < msel; s += FB_WARPS) {
+            const T l = warp_bisect(m.dd, m.ee, D, D - msel + s, glo - pad, ghi + pad, pivmin);
+            if (lane == 0) m.lam[s] = l;
+        }
+        __syncthreads();
+        // eigenvectors of the tridiagonal matrix
+        const T pert = max(tnorm * Num<T>::eps, pivmin);
+        if (threadIdx.x < msel) {
+            const int sl = threadIdx.x;
+            T* y = sc.Y + (size_t)sl * g.Dp;
+            inv_factor(m.dd, m.ee, D, m.lam[sl], pert, sl, g.mcap, sc.Ld, sc.Lu, sc.Lu2, sc.Lf, sc.piv);
+            for (int i = 0; i < D; ++i) y[i] = T(1) + T(0.125) * (T)((i * 7919 + sl * 104729) % 17) / T(17);
+            inv_solve(D, sl, g.mcap, sc.Ld, sc.Lu, sc.Lu2, sc.Lf, sc.piv, y);
+            inv_solve(D, sl, g.mcap, sc.Ld, sc.Lu, sc.Lu2, sc.Lf, sc.piv, y);
+        }
+        __syncthreads();
+        // re-orthogonalise inside clusters (gap below 1e-3 |T|), one more solve, again
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int s = 1; s < msel; ++s) {
+                for (int s2 = s - 1; s2 >= 0 && fabs(m.lam[s] - m.lam[s2]) <= T(1e-3) * tnorm; --s2) {
+                    T* ys = sc.Y + (size_t)s * g.Dp;
+                    const T* yo = sc.Y + (size_t)s2 * g.Dp;
+                    T dp = T(0);
+                    for (int i = threadIdx.x; i < D; i += FB_THREADS) dp += ys[i] * yo[i];
+                    dp = block_sum(dp, m.red);
+                    T nn = T(0);
+                    for (int i = threadIdx.x; i < D; i += FB_THREADS) { ys[i] -= dp * yo[i]; nn += ys[i] * ys[i]; }
+                    nn = block_sum(nn, m.red);
+                    const T inv = T(1) / Num<T>::sqrt_(nn);
+                    for (int i = threadIdx.x; i < D; i += FB_THREADS) ys[i] *= inv;
+                    __syncthreads();
+                }
+            }
+            if (pass == 0) {
+                if (threadIdx.x < msel)
+                    inv_solve(D, (int)threadIdx.x, g.mcap, sc.Ld, sc.Lu, sc.Lu2, sc.Lf, sc.piv,
+                              sc.Y + (size_t)threadIdx.x * g.Dp);
+                __syncthreads();
+            }
+        }
+        // back-transformation v = H_0 ... H_{D-3} y, one warp per vector (no block barriers)
+        for (int s = warp; s < msel; s += FB_WARPS) {
+            T* y = sc.Y + (size_t)s * g.Dp;
+            for (int k = D - 3; k >= 0; --k) {
+                T dp = T(0);
+                for (int i = k + 1 + lane; i < D; i += 32) dp += el(m.A, g.ntl, i, k) * y[i];
+#pragma unroll
+                for (int o = 16; o >= 1; o >>= 1) dp += __shfl_xor_sync(0xffffffffu, dp, o);
+                for (int i = k + 1 + lane; i < D; i += 32) y[i] -= T(2) * dp * el(m.A, g.ntl, i, k);
+                __syncwarp();
+            }
+            T sg, pr;
+            warp_sign_proj(y, m.r2, D, sg, pr);
+            if (lane == 0) { m.res[2 * s] = sg * pr; m.res[2 * s + 1] = pr * pr; }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && a.out[2]) {
+            T acc = T(0), acc2 = T(0);
+            for (int s = 0; s < msel; ++s) { acc += m.res[2 * s]; acc2 += m.res[2 * s + 1]; }
+            a.out[2][pix] = (float)(a.dwest_mode == 0 ? fabs(acc) : Num<T>::sqrt_(acc2));
+        }
+        __syncthreads();
+    }
+    return redo;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(FB_THREADS, 1) fullband_kernel(FullArgs a, Geo g, Geo g64, char* ws, size_t slab_bytes) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int sflag;
     __shared__ int s_m;
     __shared__ T s_bounds[4];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    char* slab = ws + (size_t)blockIdx.x * slab_bytes;
+    __shared__ double s_bounds64[4];
     __shared__ __align__(8) uint64_t s_bar[2];
     __shared__ uint32_t s_tmem;
     __shared__ int s_err;
+    const int warp = threadIdx.x >> 5;
+    char* slab = ws + (size_t)blockIdx.x * slab_bytes;
     TcState st{};
-    // layout
-    Smem<T> m;
-    {
-        char* sp = reinterpret_cast<char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-        size_t off = 0;
-        if (g.tc) {
-            st.buf[0] = reinterpret_cast<__nv_bfloat16*>(sp);
-            st.buf[1] = reinterpret_cast<__nv_bfloat16*>(sp + kTcBufBytes / 2);
-            off += kTcBufBytes;
-        }
-        if (g.a_in_smem) { m.A = reinterpret_cast<T*>(sp + off); off += sizeof(T) * ntiles_of(g.nt) * 16; }
-        T* base = reinterpret_cast<T*>(sp + off);
-        m.xs = base;
-        base += (size_t)g.S * g.Dp;
-        m.mu_o = base; base += g.Dp;
-        m.mu_i = base; base += g.Dp;
-        m.r1 = base; base += g.Dp;
-        m.r2 = base; base += g.Dp;
-        m.v = base; base += g.Dp;
-        m.p = base; base += g.Dp;
-        m.dd = base; base += g.Dp;
-        m.ee = base; base += g.Dp;
-        m.lam = base; base += g.mcap;
-        m.res = base; base += 2 * g.mcap;
-        m.red = base;
-        m.flag = &sflag;
+    // shared memory: [tensor-core chunk buffers][matrix if it fits][vectors]
+    char* sp = reinterpret_cast<char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    if (g.tc) {
+        st.buf[0] = reinterpret_cast<__nv_bfloat16*>(sp);
+        st.buf[1] = reinterpret_cast<__nv_bfloat16*>(sp + kTcBufBytes / 2);
+        sp += kTcBufBytes;
     }
-    size_t soff = 0;
-    if (!g.a_in_smem) { m.A = reinterpret_cast<T*>(slab); soff += sizeof(T) * ntiles_of(g.nt) * 16; }
-    T* Y = reinterpret_cast<T*>(slab + soff);  // [mcap][Dp] eigenvectors (column-major by vector)
-    soff += sizeof(T) * (size_t)g.mcap * g.Dp;
-    T* Ld = reinterpret_cast<T*>(slab + soff); soff += sizeof(T) * (size_t)g.mcap * g.Dp;
-    T* Lu = reinterpret_cast<T*>(slab + soff); soff += sizeof(T) * (size_t)g.mcap * g.Dp;
-    T* Lu2 = reinterpret_cast<T*>(slab + soff); soff += sizeof(T) * (size_t)g.mcap * g.Dp;
-    T* Lf = reinterpret_cast<T*>(slab + soff); soff += sizeof(T) * (size_t)g.mcap * g.Dp;
-    soff += sizeof(T) * (size_t)g.mcap * g.Dp;  // reserved
-    int* piv = reinterpret_cast<int*>(slab + soff);
-
-    const int ro = a.outer / 2, ri = a.inner / 2;
-    const int N = a.outer * a.outer - a.inner * a.inner, ni = a.inner * a.inner;
-    const int D = g.D;
-    const int64_t P = (int64_t)a.H * a.W;
-    const bool want_rx = a.out[0] || a.out[1];
-    const float fnan = __int_as_float(0x7fc00000);
+    Smem<T> m;
+    Scratch<T> sc;
+    char* sp_end;
+    carve<T>(sp, g, m, sc, g.a_in_smem, &sp_end);
+    // slab: [matrix unless in shared memory][eigen scratch][FP64 re-solve area (mixed)]
+    char* q = slab;
+    if (!g.a_in_smem) { m.A = reinterpret_cast<T*>(q); q += ((sizeof(T) * (size_t)g.ntl * 16 + 255) & ~(size_t)255); }
+    carve_scratch<T>(q, g, sc, &q);
+    Smem<double> m64;
+    Scratch<double> sc64;
+    if (g.tc) {
+        carve<double>(q, g64, m64, sc64, true, &q);
+        carve_scratch<double>(q, g64, sc64, &q);
+    }
     if (g.tc) {
         if (threadIdx.x == 0) {
             s_err = 0;
@@ -735,7 +964,10 @@ __global__ void __launch_bounds__(FB_THREADS, 1) fullband_kernel(FullArgs a, Geo
         st.tmem = s_tmem;
         st.err = &s_err;
     }
-
+    const int ro = a.outer / 2;
+    const int64_t P = (int64_t)a.H * a.W;
+    const unsigned want = (a.out[0] ? 1u : 0u) | (a.out[1] ? 2u : 0u) | (a.out[2] ? 4u : 0u);
+    const float fnan = __int_as_float(0x7fc00000);
     for (int64_t pix = blockIdx.x; pix < P; pix += gridDim.x) {
         const int py = (int)(pix / a.W), px = (int)(pix % a.W);
         if (a.border == 1 && (py - ro < 0 || py + ro >= a.H || px - ro < 0 || px + ro >= a.W)) {
@@ -744,159 +976,12 @@ __global__ void __launch_bounds__(FB_THREADS, 1) fullband_kernel(FullArgs a, Geo
             continue;
         }
         uint8_t flag = 0;
-        __syncthreads();
-        sample_mean<T>(a.x, a.H, a.W, D, g.Dp, py, px, 0, N, ro, ri, m.mu_o);
-        sample_mean<T>(a.x, a.H, a.W, D, g.Dp, py, px, 1, ni, ro, ri, m.mu_i);
-        __syncthreads();
-        if (want_rx) {
-            for (int b = threadIdx.x; b < g.Dp; b += FB_THREADS) {
-                const T c = b < D ? (T)__ldg(a.x + pix * D + b) : T(0);
-                m.r1[b] = b < D ? c - m.mu_o[b] : T(0);
-                m.r2[b] = b < D ? m.mu_i[b] - m.mu_o[b] : T(0);
-            }
-            mat_zero(m.A, g);
-            if constexpr (sizeof(T) == 4) {
-                if (g.tc) gram_tc(a.x, a.H, a.W, g, py, px, 0, N, ro, ri, m.mu_o, 1.f / (float)N, m.A, st);
-            }
-            if (!g.tc) {
-                gram_accumulate<T>(a.x, a.H, a.W, g, py, px, 0, N, ro, ri, m.mu_o, T(1), m.A, m.xs);
-                mat_scale(m.A, g, T(1) / (T)N);
-            }
-            T tr = T(0), dmax = T(0);
-            for (int b = threadIdx.x; b < D; b += FB_THREADS) { tr += el(m.A, g.ntl, b, b); dmax = max(dmax, el(m.A, g.ntl, b, b)); }
-            tr = block_sum(tr, m.red);
-            dmax = block_max(dmax, m.red);
-            const T delta = (T)a.loading * tr / (T)D;
-            for (int b = threadIdx.x; b < D; b += FB_THREADS) el(m.A, g.ntl, b, b) += delta;
-            __syncthreads();
-            const bool ok = cholesky_tiles(m.A, g, T(16) * Num<T>::eps * (dmax + delta), m.flag);
-            if (ok) {
-                forward_solve2(m.A, g, m.r1, m.r2);
-                T q1 = T(0), q2 = T(0);
-                for (int b = threadIdx.x; b < D; b += FB_THREADS) { q1 += m.r1[b] * m.r1[b]; q2 += m.r2[b] * m.r2[b]; }
-                q1 = block_sum(q1, m.red);
-                q2 = block_sum(q2, m.red);
-                if (threadIdx.x == 0) {
-                    if (a.out[0]) a.out[0][pix] = (float)q1;
-                    if (a.out[1]) a.out[1][pix] = (float)fabs(q2);
-                }
-            } else {
-                flag |= 2;
-                if (threadIdx.x == 0) {
-                    if (a.out[0]) a.out[0][pix] = fnan;
-                    if (a.out[1]) a.out[1][pix] = fnan;
-                }
-            }
-        }
-        if (a.out[2]) {
-            // C_diff = C_i - C_o (Eq. 2)
-            for (int b = threadIdx.x; b < g.Dp; b += FB_THREADS) m.r2[b] = b < D ? m.mu_i[b] - m.mu_o[b] : T(0);
-            mat_zero(m.A, g);
-            if constexpr (sizeof(T) == 4) {
-                if (g.tc) {
-                    gram_tc(a.x, a.H, a.W, g, py, px, 0, N, ro, ri, m.mu_o, -1.f / (float)N, m.A, st);
-                    gram_tc(a.x, a.H, a.W, g, py, px, 1, ni, ro, ri, m.mu_i, 1.f / (float)ni, m.A, st);
-                }
-            }
-            if (!g.tc) {
-                gram_accumulate<T>(a.x, a.H, a.W, g, py, px, 0, N, ro, ri, m.mu_o, T(1), m.A, m.xs);
-                mat_scale(m.A, g, T(-1) / (T)N);
-                gram_accumulate<T>(a.x, a.H, a.W, g, py, px, 1, ni, ro, ri, m.mu_i, T(1) / Num<T>::sqrt_((T)ni), m.A,
-                                   m.xs);
-            }
-            tridiagonalise(m.A, g, m.v, m.p, m.dd, m.ee, m.red);
-            // spectrum bounds (Gershgorin), extreme eigenvalues, threshold, count above it
-            T glo, ghi;
-            {
-                T lo = T(3e38), hi = T(-3e38);
-                for (int i = threadIdx.x; i < D; i += FB_THREADS) {
-                    const T r = (i > 0 ? fabs(m.ee[i - 1]) : T(0)) + (i < D - 1 ? fabs(m.ee[i]) : T(0));
-                    lo = min(lo, m.dd[i] - r);
-                    hi = max(hi, m.dd[i] + r);
-                }
-                glo = -block_max(-lo, m.red);
-                ghi = block_max(hi, m.red);
-            }
-            const T tnorm = max(fabs(glo), fabs(ghi));
-            const T pivmin = max(tnorm * Num<T>::eps * Num<T>::eps, T(1e-30));
-            const T pad = tnorm * T(4) * Num<T>::eps + pivmin;
-            if (warp == 0) {
-                const T lmax = warp_bisect(m.dd, m.ee, D, D - 1, glo - pad, ghi + pad, pivmin);
-                if (lane == 0) s_bounds[0] = lmax;
-            } else if (warp == 1) {
-                const T lmin = warp_bisect(m.dd, m.ee, D, 0, glo - pad, ghi + pad, pivmin);
-                if (lane == 0) s_bounds[1] = lmin;
-            }
-            __syncthreads();
-            const T maxabs = max(fabs(s_bounds[0]), fabs(s_bounds[1]));
-            const T tau = (T)a.dwest_tau * maxabs;
-            if (threadIdx.x == 0) {
-                const int below = (maxabs > T(0)) ? sturm_below(m.dd, m.ee, D, tau, pivmin) : D;
-                s_m = D - below;
-            }
-            __syncthreads();
-            int msel = s_m;
-            if (msel > g.mcap) { msel = g.mcap; flag |= 8; }  // more than the slab holds: top mcap kept
-            // selected eigenvalues lambda_{D-msel} .. lambda_{D-1}
-            for (int s = warp; s < msel; s += FB_WARPS) {
-                const T l = warp_bisect(m.dd, m.ee, D, D - msel + s, glo - pad, ghi + pad, pivmin);
-                if (lane == 0) m.lam[s] = l;
-            }
-            __syncthreads();
-            // eigenvectors of the tridiagonal matrix
-            const T pert = max(tnorm * Num<T>::eps, pivmin);
-            if (threadIdx.x < msel) {
-                const int sl = threadIdx.x;
-                T* y = Y + (size_t)sl * g.Dp;
-                inv_factor(m.dd, m.ee, D, m.lam[sl], pert, sl, g.mcap, Ld, Lu, Lu2, Lf, piv);
-                for (int i = 0; i < D; ++i) y[i] = T(1) + T(0.125) * (T)((i * 7919 + sl * 104729) % 17) / T(17);
-                inv_solve(D, sl, g.mcap, Ld, Lu, Lu2, Lf, piv, y);
-                inv_solve(D, sl, g.mcap, Ld, Lu, Lu2, Lf, piv, y);
-            }
-            __syncthreads();
-            // re-orthogonalise inside clusters (gap below 1e-3 |T|), one more solve, again
-            for (int pass = 0; pass < 2; ++pass) {
-                for (int s = 1; s < msel; ++s) {
-                    for (int s2 = s - 1; s2 >= 0 && fabs(m.lam[s] - m.lam[s2]) <= T(1e-3) * tnorm; --s2) {
-                        T* ys = Y + (size_t)s * g.Dp;
-                        const T* yo = Y + (size_t)s2 * g.Dp;
-                        T dp = T(0);
-                        for (int i = threadIdx.x; i < D; i += FB_THREADS) dp += ys[i] * yo[i];
-                        dp = block_sum(dp, m.red);
-                        T nn = T(0);
-                        for (int i = threadIdx.x; i < D; i += FB_THREADS) { ys[i] -= dp * yo[i]; nn += ys[i] * ys[i]; }
-                        nn = block_sum(nn, m.red);
-                        const T inv = T(1) / Num<T>::sqrt_(nn);
-                        for (int i = threadIdx.x; i < D; i += FB_THREADS) ys[i] *= inv;
-                        __syncthreads();
-                    }
-                }
-                if (pass == 0) {
-                    if (threadIdx.x < msel)
-                        inv_solve(D, (int)threadIdx.x, g.mcap, Ld, Lu, Lu2, Lf, piv, Y + (size_t)threadIdx.x * g.Dp);
-                    __syncthreads();
-                }
-            }
-            // back-transformation v = H_0 ... H_{D-3} y, one warp per vector (no block barriers)
-            for (int s = warp; s < msel; s += FB_WARPS) {
-                T* y = Y + (size_t)s * g.Dp;
-                for (int k = D - 3; k >= 0; --k) {
-                    T dp = T(0);
-                    for (int i = k + 1 + lane; i < D; i += 32) dp += el(m.A, g.ntl, i, k) * y[i];
-#pragma unroll
-                    for (int o = 16; o >= 1; o >>= 1) dp += __shfl_xor_sync(0xffffffffu, dp, o);
-                    for (int i = k + 1 + lane; i < D; i += 32) y[i] -= T(2) * dp * el(m.A, g.ntl, i, k);
-                    __syncwarp();
-                }
-                T sg, pr;
-                warp_sign_proj(y, m.r2, D, sg, pr);
-                if (lane == 0) { m.res[2 * s] = sg * pr; m.res[2 * s + 1] = pr * pr; }
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                T acc = T(0), acc2 = T(0);
-                for (int s = 0; s < msel; ++s) { acc += m.res[2 * s]; acc2 += m.res[2 * s + 1]; }
-                a.out[2][pix] = (float)(a.dwest_mode == 0 ? fabs(acc) : Num<T>::sqrt_(acc2));
+        const unsigned redo = process_pixel<T>(a, g, m, sc, &st, pix, want, flag, &sflag, &s_m, s_bounds);
+        if constexpr (sizeof(T) == 4) {
+            if (g.tc && redo) {  // estimated condition above the gate: FP64 from the data
+                uint8_t f64 = 0;
+                process_pixel<double>(a, g64, m64, sc64, nullptr, pix, redo, f64, &sflag, &s_m, s_bounds64);
+                flag = (uint8_t)((flag & ~2u) | f64 | 1u);
             }
         }
         if (threadIdx.x == 0 && a.flags) a.flags[pix] = flag;
@@ -998,24 +1083,35 @@ __global__ void __launch_bounds__(FB_THREADS, 1) moments_kernel(FullArgs a, Geo 
 }
 
 template <typename T>
-Geo make_geo(const FullArgs& a, bool* smem_ok, size_t* smem_bytes, size_t* slab) {
+Geo make_geo_only(const FullArgs& a) {
     Geo g{};
     g.D = a.D;
     g.Dp = (a.D + 3) & ~3;
     g.nt = g.Dp / 4;
     g.ntl = ntiles_of(g.nt);
     g.S = fb_chunk(sizeof(T));
-    const int ni = a.inner * a.inner;
-    g.mcap = std::min(g.Dp, ni + 16);
-    const size_t amat = sizeof(T) * (size_t)ntiles_of(g.nt) * 16;
-    const size_t vecs = fb_smem_vectors_bytes<T>(g.Dp, g.S, g.mcap);
+    g.mcap = std::min(g.Dp, a.inner * a.inner + 16);
+    g.tc = false;
+    g.a_in_smem = false;
+    return g;
+}
+
+template <typename T>
+Geo make_geo(const FullArgs& a, bool* smem_ok, size_t* smem_bytes, size_t* slab, Geo* g64_out = nullptr) {
+    Geo g = make_geo_only<T>(a);
+    const size_t amat = sizeof(T) * (size_t)g.ntl * 16;
+    const size_t vecs = vec_bytes<T>(g);
     g.tc = (sizeof(T) == 4) && a.precision == WDAD_PREC_MIXED && a.D <= 256;
     const size_t tcb = g.tc ? kTcBufBytes : 0;
     g.a_in_smem = (sizeof(T) == 4) && (amat + vecs + tcb <= 210 * 1024);
     *smem_bytes = vecs + tcb + (g.a_in_smem ? amat : 0) + 1024;  // + alignment slack
     *smem_ok = *smem_bytes <= 227 * 1024;
-    *slab = (g.a_in_smem ? 0 : amat) + sizeof(T) * (size_t)g.mcap * g.Dp * 6 + sizeof(int) * (size_t)g.mcap * g.Dp;
-    *slab = (*slab + 255) & ~(size_t)255;
+    size_t sl = (g.a_in_smem ? 0 : ((amat + 255) & ~(size_t)255)) + scratch_bytes<T>(g);
+    Geo g64 = make_geo_only<double>(a);
+    if (g.tc) sl += ((sizeof(double) * (size_t)g64.ntl * 16 + 255) & ~(size_t)255) + vec_bytes<double>(g64) +
+                    scratch_bytes<double>(g64);
+    *slab = (sl + 255) & ~(size_t)255;
+    if (g64_out) *g64_out = g64;
     return g;
 }
 
@@ -1041,13 +1137,14 @@ template <typename T>
 static cudaError_t launch_fb(const FullArgs& a, void* ws, int num_sms, cudaStream_t s) {
     bool ok;
     size_t smem, slab;
-    const Geo g = make_geo<T>(a, &ok, &smem, &slab);
+    Geo g64{};
+    const Geo g = make_geo<T>(a, &ok, &smem, &slab, &g64);
     if (!ok) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(fullband_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = fb_grid(num_sms, (int64_t)a.H * a.W);
     char* base = reinterpret_cast<char*>(((uintptr_t)ws + 255) & ~(uintptr_t)255);
-    fullband_kernel<T><<<grid, FB_THREADS, smem, s>>>(a, g, base, slab);
+    fullband_kernel<T><<<grid, FB_THREADS, smem, s>>>(a, g, g64, base, slab);
     return cudaGetLastError();
 }
 

@@ -76,3 +76,22 @@ def test_tensor_core_gram_is_the_bf16_gram(wd, D, win):
         scale = np.abs(ref).max()
         assert np.abs(cov[t] - ref).max() <= 2e-6 * scale, (t, np.abs(cov[t] - ref).max() / scale)
         assert np.abs(cov[t] - cov_exact[t]).max() <= 2.0 ** -7 * np.abs(cov_exact[t]).max()
+
+
+def test_mixed_gate_everything_reproduces_fp64(wd, scene48):
+    # cond_gate = 1: every pixel's estimate exceeds it -> FP64 re-solve from the data for all
+    cube = scene48.cube[:20, :24]
+    x = _gpu(cube)
+    flags = torch.zeros(cube.shape[:2], dtype=torch.uint8, device="cuda")
+    mixed = wd.wdad_detect_all(x, reduce=False, inner=3, outer=9, precision=1, cond_gate=1.0, flags=flags)
+    fp64 = wd.wdad_detect_all(x, reduce=False, inner=3, outer=9, precision=2)
+    assert torch.equal(mixed, fp64)
+    assert bool(torch.all(flags & 1))
+
+
+def test_mixed_without_gate_is_finite_and_unflagged(wd, scene48):
+    cube = scene48.cube[:20, :24]
+    flags = torch.zeros(cube.shape[:2], dtype=torch.uint8, device="cuda")
+    mixed = wd.wdad_detect_all(_gpu(cube), reduce=False, inner=3, outer=9, precision=1, cond_gate=1e30, flags=flags)
+    assert bool(torch.isfinite(mixed).all())
+    assert not bool(torch.any(flags & 1))
