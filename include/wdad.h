@@ -159,6 +159,42 @@ wdad_status wdad_window_census(wdad_handle h, int H, int W, const wdad_params* p
 wdad_status wdad_detect_all_noalloc(const float* cube, int H, int W, int L, const wdad_params* p,
                                     float* scores, uint8_t* flags, void* stream);
 
+/* A8 — batching.  One job = one cube through the DWT-reduced path (A1 + detectors).
+ * Limits of the batched path: L % 4 == 0, L <= 256, K <= 4 (e.g. L in {128, 188, 224}). */
+typedef struct {
+    const float* cube;    /* [H][W][L] device, read-only */
+    int H, W, L;
+    int detector;         /* 0 LRX, 1 DWRX, 2 DWEST, 3 = all three */
+    wdad_params params;   /* windows, loading, border, DWEST mode, wavelet, level */
+    float* scores;        /* device: [H][W], or [3][H][W] (LRX, DWRX, DWEST) when detector == 3 */
+    uint8_t* flags;       /* device [H][W] or NULL */
+} wdad_job;
+
+typedef struct wdad_batch_ctx* wdad_batch;
+
+/* Tile height the library's autotuner picks for D bands and a window: candidate heights
+ * are timed with CUDA events on a synthetic 256 x 256 cube; the winner is cached in the
+ * handle.  Synchronises `stream`; do not call while `stream` is being captured. */
+wdad_status wdad_autotune(wdad_handle h, int D, int inner, int outer, int* tile_h, void* stream);
+
+/* Prepare a batch of n jobs: DWT plans, tile plans (autotune != 0: the autotuner's, else
+ * the defaults that wdad_detect uses), a device work list and per-job scratch owned by the
+ * batch, and, when use_graph != 0, a CUDA graph of the whole launch (counter reset plus one
+ * persistent kernel) captured on a private stream.  The jobs' pointers are baked in: later
+ * launches read and write the same buffers.  With default plans every job's scores are
+ * bit-identical to wdad_detect / wdad_detect_all on the same job. */
+wdad_status wdad_batch_create(wdad_handle h, int n, const wdad_job* jobs, int autotune, int use_graph,
+                              wdad_batch* out, void* stream);
+/* Enqueue the batch on `stream` (graph replay when captured). */
+wdad_status wdad_batch_launch(wdad_batch b, void* stream);
+/* Synchronise the batch's last launch and report its device status: WDAD_OK, or
+ * WDAD_ERR_TIMEOUT when a tile gave up waiting for its cube's DWT (that job's scores are
+ * then not written).  *tile_h_out (nullable, n entries) receives each job's tile height. */
+wdad_status wdad_batch_status(wdad_batch b, int* tile_h_out);
+wdad_status wdad_batch_destroy(wdad_batch b);
+/* One-shot: create (default plans, no graph), launch on `stream`, synchronise, destroy. */
+wdad_status wdad_batch_run(wdad_handle h, int n, const wdad_job* jobs, void* stream);
+
 /* A10 — pixel-level ROC AUC of a score map against a truth mask (Sec. 5.3.1):
  * Mann-Whitney U with ties counted one half.  HOST pointers; NaN scores rank lowest.
  * Writes NaN when the mask has no positive or no negative pixel. */

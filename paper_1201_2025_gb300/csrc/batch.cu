@@ -1,0 +1,130 @@
+// A8 — many cubes of uneven size, band count, window and detector in one persistent
+// launch (captured once into a CUDA graph and replayed).
+//
+// The host builds a work list: first every cube's DWT items (ranges of 8-pixel groups),
+// then every cube's detector tiles.  Persistent CTAs pop items with one atomic counter.
+// A tile of cube j may only start once all DWT items of cube j have finished: the DWT
+// items bump done[j] after a fence, and the tile's first thread waits for
+// done[j] == dwt_items[j] with a bounded spin.  Items are popped in list order, so every
+// DWT item a tile waits on is already held by a running CTA that will finish it; if the
+// spin still runs out (about a second), the tile is skipped and the launch status becomes
+// WDAD_ERR_TIMEOUT instead of hanging.  The per-item arithmetic is the same device code
+// as the standalone kernels, with the same tile plan, so a batched job's scores are
+// bit-identical to the same job run alone.
+#include <cstdlib>
+
+#include "batch.h"
+#include "dwt_dev.cuh"
+#include "reduced_dev.cuh"
+
+namespace wdad {
+
+constexpr int BATCH_THREADS = 512;
+constexpr int kGroupsPerDwtItem = 512;  // 4096 pixels per DWT item
+
+__global__ void __launch_bounds__(BATCH_THREADS, 1)
+    batch_kernel(const BatchJob* __restrict__ jobs, const BatchItem* __restrict__ items, int nitems, int* counter,
+                 int* done, int* status, uint32_t spin_limit) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_item;
+    __shared__ int s_ready;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= nitems) break;
+        const BatchItem bi = items[it];
+        const BatchJob& j = jobs[bi.job];
+        if (bi.kind == 0) {
+            const int64_t P = (int64_t)j.H * j.W;
+            const int64_t warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+            if (j.variant == 0)
+                dwt_groups<4, 1, 4>(j.cube, P, j.L, j.A, j.K, j.approx, bi.a, bi.b, warp, nw);
+            else
+                dwt_groups<4, 2, 4>(j.cube, P, j.L, j.A, j.K, j.approx, bi.a, bi.b, warp, nw);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                atomicAdd(&done[bi.job], 1);
+            }
+        } else {
+            if (threadIdx.x == 0) {
+                uint32_t n = 0;
+                int ok = 1;
+                while (atomicAdd(&done[bi.job], 0) < j.dwt_items) {
+                    if (atomicAdd(&status[1 + bi.job], 0) != 0 || ++n > spin_limit) {
+                        ok = 0;
+                        atomicExch(&status[1 + bi.job], 1);
+                        atomicExch(&status[0], (int)WDAD_ERR_TIMEOUT);
+                        break;
+                    }
+                    __nanosleep(256);
+                }
+                __threadfence();
+                s_ready = ok;
+            }
+            __syncthreads();
+            if (s_ready) {
+                DetectArgs a{};
+                a.x = j.approx; a.H = j.H; a.W = j.W; a.D = j.K;
+                a.inner = j.inner; a.outer = j.outer; a.loading = j.loading; a.border = j.border;
+                a.dwest_mode = j.dwest_mode; a.dwest_tau = j.tau;
+                for (int t = 0; t < 3; ++t) a.out[t] = j.out[t];
+                a.flags = j.flags;
+                switch (j.K) {
+                    case 1: detect_tile<1>(a, j.th, bi.a, bi.b, smem_raw); break;
+                    case 2: detect_tile<2>(a, j.th, bi.a, bi.b, smem_raw); break;
+                    case 3: detect_tile<3>(a, j.th, bi.a, bi.b, smem_raw); break;
+                    default: detect_tile<4>(a, j.th, bi.a, bi.b, smem_raw); break;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+bool batch_job_supported(int L, int K) { return L % 4 == 0 && L <= 256 && K >= 1 && K <= 4; }
+
+int batch_variant(int L) { return L <= 128 ? 0 : 1; }
+
+void batch_build_items(const std::vector<BatchJob>& jobs, std::vector<BatchItem>& items, std::vector<int>& dwt_items,
+                       int drop_job) {
+    items.clear();
+    dwt_items.assign(jobs.size(), 0);
+    for (size_t j = 0; j < jobs.size(); ++j) {
+        const int64_t P = (int64_t)jobs[j].H * jobs[j].W;
+        const int64_t ngroups = (P + 7) / 8;
+        bool dropped = false;
+        for (int64_t g0 = 0; g0 < ngroups; g0 += kGroupsPerDwtItem) {
+            dwt_items[j]++;
+            if ((int)j == drop_job && !dropped) { dropped = true; continue; }  // fault injection (host only)
+            items.push_back({(int)j, 0, (int)g0, (int)std::min<int64_t>(ngroups, g0 + kGroupsPerDwtItem)});
+        }
+    }
+    for (size_t j = 0; j < jobs.size(); ++j) {
+        const int tx = (jobs[j].W + 31) / 32, ty = (jobs[j].H + jobs[j].th - 1) / jobs[j].th;
+        for (int y = 0; y < ty; ++y)
+            for (int x = 0; x < tx; ++x) items.push_back({(int)j, 1, x, y});
+    }
+}
+
+cudaError_t batch_launch(const BatchJob* d_jobs, const BatchItem* d_items, int nitems, int* d_counters, int njobs,
+                         size_t smem, int num_sms, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, BATCH_THREADS, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    // counters: [0] work counter, [1, 1 + njobs) done, then status[0] and one word per job
+    e = cudaMemsetAsync(d_counters, 0, sizeof(int) * (size_t)(2 + 2 * njobs), s);
+    if (e != cudaSuccess) return e;
+    int grid = num_sms * per_sm;
+    if (grid > nitems) grid = nitems > 0 ? nitems : 1;
+    batch_kernel<<<grid, BATCH_THREADS, smem, s>>>(d_jobs, d_items, nitems, d_counters, d_counters + 1,
+                                                   d_counters + 1 + njobs, 4u << 20);
+    return cudaGetLastError();
+}
+
+}  // namespace wdad

@@ -10,6 +10,10 @@
 #include <string>
 #include <vector>
 
+#include <cstdlib>
+#include <map>
+
+#include "batch.h"
 #include "internal.h"
 
 struct wdad_ctx {
@@ -19,7 +23,24 @@ struct wdad_ctx {
     size_t ws_bytes = 0;
     struct DwtPlan { int L, taps, J, K; float* A; };
     std::vector<DwtPlan> dwt_plans;
+    std::map<long long, int> tuned;  // (D, inner, outer) -> autotuned tile height
     std::string err;
+};
+
+struct wdad_batch_ctx {
+    wdad_ctx* h = nullptr;
+    int n = 0;
+    int nitems = 0;
+    size_t smem = 0;
+    wdad::BatchJob* d_jobs = nullptr;
+    wdad::BatchItem* d_items = nullptr;
+    int* d_counters = nullptr;
+    float* d_approx = nullptr;
+    std::vector<int> th;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t last = nullptr;
 };
 
 namespace {
@@ -133,7 +154,7 @@ wdad_status detect_bands(wdad_ctx* h, const float* x, int H, int W, int D, const
         a.flags = flags;
         if (wdad::detect_small_smem(D, p->inner, p->outer, 1) > 227 * 1024)
             return fail(h, WDAD_ERR_UNSUPPORTED, "window %d/%d too large for %d bands", p->inner, p->outer, D);
-        cudaError_t e = wdad::launch_detect_small(a, 16, s);
+        cudaError_t e = wdad::launch_detect_small_th(a, wdad::detect_small_default_th(D, p->inner, p->outer), s);
         if (e != cudaSuccess) return cuda_fail(h, e, "detect_small launch");
         return WDAD_OK;
     }
@@ -197,6 +218,71 @@ wdad_status run_detect(wdad_ctx* h, const float* cube, int H, int W, int L, int 
     cudaError_t e = wdad::launch_dwt_approx(cube, P, L, A, K, xr, h->num_sms, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "dwt_approx launch");
     return detect_bands(h, xr, H, W, K, p, out3, flags, (char*)h->ws + off, h->ws_bytes - off, s);
+}
+
+long long tune_key(int D, int inner, int outer) { return ((long long)D << 32) | ((long long)inner << 16) | outer; }
+
+__global__ void fill_pattern_kernel(float* x, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t v = (uint32_t)(i * 2654435761u) ^ (uint32_t)(i >> 7) * 40503u;
+        v ^= v >> 13;
+        v *= 0x5bd1e995u;
+        v ^= v >> 15;
+        x[i] = 1.0f + 0.25f * (float)(v & 0xFFFFFF) / 16777216.0f;
+    }
+}
+
+// Time every feasible tile height on a synthetic 256 x 256 x D cube and keep the fastest.
+wdad_status autotune(wdad_ctx* h, int D, int inner, int outer, int* out, cudaStream_t s) {
+    const long long key = tune_key(D, inner, outer);
+    auto it = h->tuned.find(key);
+    if (it != h->tuned.end()) { *out = it->second; return WDAD_OK; }
+    const int S = 256;
+    const size_t nx = (size_t)S * S * D, ns = (size_t)3 * S * S;
+    wdad_status st = ensure_ws(h, sizeof(float) * (nx + ns) + 256);
+    if (st != WDAD_OK) return st;
+    float* x = (float*)h->ws;
+    float* sc = x + nx;
+    fill_pattern_kernel<<<256, 256, 0, s>>>(x, (int64_t)nx);
+    wdad::DetectArgs a{};
+    a.x = x; a.H = S; a.W = S; a.D = D; a.inner = inner; a.outer = outer; a.loading = 1e-3f;
+    a.dwest_tau = 1e-6f;
+    for (int t = 0; t < 3; ++t) a.out[t] = sc + (size_t)t * S * S;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return fail(h, WDAD_ERR_CUDA, "autotune events");
+    int best = 0;
+    float best_ms = 1e30f;
+    for (int th : {32, 16, 8, 4, 2}) {
+        if (wdad::detect_small_smem(D, inner, outer, th) > 227 * 1024) continue;
+        if (wdad::launch_detect_small_th(a, th, s) != cudaSuccess) { cudaGetLastError(); continue; }
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < 3; ++r) wdad::launch_detect_small_th(a, th, s);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) { best_ms = ms; best = th; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best == 0) return fail(h, WDAD_ERR_UNSUPPORTED, "no tile height fits window %d/%d for %d bands", inner, outer, D);
+    h->tuned[key] = best;
+    *out = best;
+    return WDAD_OK;
+}
+
+void batch_free(wdad_batch_ctx* b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->last) cudaEventDestroy(b->last);
+    cudaFree(b->d_jobs);
+    cudaFree(b->d_items);
+    cudaFree(b->d_counters);
+    cudaFree(b->d_approx);
+    delete b;
 }
 
 }  // namespace
@@ -416,6 +502,156 @@ wdad_status wdad_window_census(wdad_handle h, int H, int W, const wdad_params* p
     cudaError_t e = wdad::launch_window_census(H, W, p->inner, p->outer, p->border, out, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "census launch");
     return WDAD_OK;
+}
+
+wdad_status wdad_autotune(wdad_handle h, int D, int inner, int outer, int* tile_h, void* stream) {
+    if (!h) return WDAD_ERR_ARG;
+    if (!tile_h || D < 1 || D > 8 || inner < 1 || !(inner & 1) || outer <= inner || !(outer & 1) || outer > 63)
+        return fail(h, WDAD_ERR_ARG, "autotune: D in 1..8, odd windows 1 <= inner < outer <= 63");
+    try {
+        DeviceGuard g(h->device);
+        return autotune(h, D, inner, outer, tile_h, (cudaStream_t)stream);
+    } catch (...) {
+        return fail(h, WDAD_ERR_NOMEM, "host exception");
+    }
+}
+
+wdad_status wdad_batch_create(wdad_handle h, int n, const wdad_job* jobs, int autotune_plans, int use_graph,
+                              wdad_batch* out, void* stream) {
+    if (!h) return WDAD_ERR_ARG;
+    if (!out || n < 1 || !jobs) return fail(h, WDAD_ERR_ARG, "batch: n >= 1 jobs and an output handle");
+    *out = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    wdad_batch_ctx* b = nullptr;
+    try {
+        DeviceGuard g(h->device);
+        std::vector<wdad::BatchJob> hj((size_t)n);
+        size_t approx_floats = 0;
+        std::vector<size_t> aoff((size_t)n);
+        size_t smem = 0;
+        for (int i = 0; i < n; ++i) {
+            const wdad_job& j = jobs[i];
+            wdad_status st = check_params(h, &j.params);
+            if (st != WDAD_OK) return st;
+            st = check_cube(h, j.cube, j.H, j.W, j.L);
+            if (st != WDAD_OK) return st;
+            if ((int64_t)j.H * j.W == 0) return fail(h, WDAD_ERR_ARG, "batch job %d is empty", i);
+            if (j.detector < 0 || j.detector > 3 || !j.scores) return fail(h, WDAD_ERR_ARG, "batch job %d: detector/scores", i);
+            const int K = wdad_query_K(j.L, j.params.wavelet_taps, j.params.level);
+            if (!wdad::batch_job_supported(j.L, K))
+                return fail(h, WDAD_ERR_UNSUPPORTED, "batch job %d: L %% 4 == 0, L <= 256, K <= 4 (L=%d, K=%d)", i, j.L, K);
+            const float* A = nullptr;
+            int k2 = 0;
+            st = get_dwt_plan(h, j.L, j.params.wavelet_taps, j.params.level, &A, &k2, s);
+            if (st != WDAD_OK) return st;
+            int th = wdad::detect_small_default_th(K, j.params.inner, j.params.outer);
+            if (autotune_plans) {
+                st = autotune(h, K, j.params.inner, j.params.outer, &th, s);
+                if (st != WDAD_OK) return st;
+            }
+            if (th < 1) return fail(h, WDAD_ERR_UNSUPPORTED, "batch job %d: window too large", i);
+            smem = std::max(smem, wdad::detect_small_smem(K, j.params.inner, j.params.outer, th));
+            wdad::BatchJob& bj = hj[(size_t)i];
+            bj = wdad::BatchJob{};
+            bj.cube = j.cube; bj.A = A; bj.flags = j.flags;
+            bj.H = j.H; bj.W = j.W; bj.L = j.L; bj.K = K;
+            bj.inner = j.params.inner; bj.outer = j.params.outer; bj.border = j.params.border;
+            bj.dwest_mode = j.params.dwest_mode; bj.loading = j.params.loading; bj.tau = j.params.dwest_tau;
+            bj.th = th;
+            bj.variant = wdad::batch_variant(j.L);
+            const size_t P = (size_t)j.H * j.W;
+            if (j.detector == 3) { bj.out[0] = j.scores; bj.out[1] = j.scores + P; bj.out[2] = j.scores + 2 * P; }
+            else bj.out[j.detector] = j.scores;
+            aoff[(size_t)i] = approx_floats;
+            approx_floats += ((P * K + 63) / 64) * 64;
+        }
+        int drop = -1;
+        if (const char* e = std::getenv("WDAD_FAULT_DROP_DWT_ITEM")) drop = std::atoi(e);
+        std::vector<wdad::BatchItem> items;
+        std::vector<int> dwt_items;
+        wdad::batch_build_items(hj, items, dwt_items, drop);
+        b = new wdad_batch_ctx();
+        b->h = h;
+        b->n = n;
+        b->nitems = (int)items.size();
+        b->smem = smem;
+        cudaError_t e = cudaMalloc(&b->d_approx, sizeof(float) * std::max<size_t>(approx_floats, 64));
+        if (e == cudaSuccess) e = cudaMalloc(&b->d_jobs, sizeof(wdad::BatchJob) * (size_t)n);
+        if (e == cudaSuccess) e = cudaMalloc(&b->d_items, sizeof(wdad::BatchItem) * std::max<size_t>(items.size(), 1));
+        if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, sizeof(int) * (size_t)(2 + 2 * n));
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->last, cudaEventDisableTiming);
+        if (e != cudaSuccess) { batch_free(b); return cuda_fail(h, e, "batch allocation"); }
+        for (int i = 0; i < n; ++i) {
+            hj[(size_t)i].approx = b->d_approx + aoff[(size_t)i];
+            hj[(size_t)i].dwt_items = dwt_items[(size_t)i];
+            b->th.push_back(hj[(size_t)i].th);
+        }
+        e = cudaMemcpyAsync(b->d_jobs, hj.data(), sizeof(wdad::BatchJob) * (size_t)n, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && !items.empty())
+            e = cudaMemcpyAsync(b->d_items, items.data(), sizeof(wdad::BatchItem) * items.size(), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { batch_free(b); return cuda_fail(h, e, "batch upload"); }
+        if (use_graph) {
+            e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                cudaError_t el = wdad::batch_launch(b->d_jobs, b->d_items, b->nitems, b->d_counters, n, smem,
+                                                    h->num_sms, b->cap_stream);
+                e = cudaStreamEndCapture(b->cap_stream, &b->graph);
+                if (el != cudaSuccess) e = el;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+            if (e != cudaSuccess) { batch_free(b); return cuda_fail(h, e, "batch graph capture"); }
+        }
+        *out = b;
+        return WDAD_OK;
+    } catch (...) {
+        batch_free(b);
+        return fail(h, WDAD_ERR_NOMEM, "host exception");
+    }
+}
+
+wdad_status wdad_batch_launch(wdad_batch b, void* stream) {
+    if (!b) return WDAD_ERR_ARG;
+    DeviceGuard g(b->h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = b->exec ? cudaGraphLaunch(b->exec, s)
+                            : wdad::batch_launch(b->d_jobs, b->d_items, b->nitems, b->d_counters, b->n, b->smem,
+                                                 b->h->num_sms, s);
+    if (e == cudaSuccess) e = cudaEventRecord(b->last, s);
+    if (e != cudaSuccess) return cuda_fail(b->h, e, "batch launch");
+    return WDAD_OK;
+}
+
+wdad_status wdad_batch_status(wdad_batch b, int* tile_h_out) {
+    if (!b) return WDAD_ERR_ARG;
+    DeviceGuard g(b->h->device);
+    if (tile_h_out)
+        for (int i = 0; i < b->n; ++i) tile_h_out[i] = b->th[(size_t)i];
+    cudaError_t e = cudaEventSynchronize(b->last);
+    int dev_status = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&dev_status, b->d_counters + 1 + b->n, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(b->h, e, "batch status");
+    if (dev_status != 0) return fail(b->h, (wdad_status)dev_status, "a batched tile gave up waiting for its DWT");
+    return WDAD_OK;
+}
+
+wdad_status wdad_batch_destroy(wdad_batch b) {
+    if (!b) return WDAD_ERR_ARG;
+    DeviceGuard g(b->h->device);
+    cudaEventSynchronize(b->last);
+    batch_free(b);
+    return WDAD_OK;
+}
+
+wdad_status wdad_batch_run(wdad_handle h, int n, const wdad_job* jobs, void* stream) {
+    wdad_batch b = nullptr;
+    wdad_status st = wdad_batch_create(h, n, jobs, 0, 0, &b, stream);
+    if (st != WDAD_OK) return st;
+    st = wdad_batch_launch(b, stream);
+    if (st == WDAD_OK) st = wdad_batch_status(b, nullptr);
+    wdad_batch_destroy(b);
+    return st;
 }
 
 wdad_status wdad_auc(const float* score, const uint8_t* mask, int64_t n, double* auc) {

@@ -10,7 +10,7 @@
 // butterfly leaves lane l with coefficient (pixel l / KP, k = l % KP), so the
 // PX*K results leave as one coalesced store.  The lane partial sums plus the tree
 // of shuffles keep the FP32 rounding error near sqrt(L) ulp instead of L ulp.
-#include "internal.h"
+#include "dwt_dev.cuh"
 
 namespace wdad {
 
@@ -68,90 +68,6 @@ cudaError_t build_dwt_matrix(int L, int taps, int J, int K, float* A, double* /*
     const size_t smem = sizeof(double) * 2 * (L + 2);
     dwt_matrix_kernel<<<L, 128, smem, s>>>(L, J, K, f, A);
     return cudaGetLastError();
-}
-
-// Reduce-scatter of 32 per-lane values: afterwards lane l holds sum over lanes of v[l].
-__device__ __forceinline__ float butterfly32(float (&v)[32], int lane) {
-#pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) {
-        const bool upper = (lane & off) != 0;
-#pragma unroll
-        for (int j = 0; j < off; ++j) {
-            const float send = upper ? v[j] : v[j + off];
-            const float keep = upper ? v[j + off] : v[j];
-            v[j] = keep + __shfl_xor_sync(0xffffffffu, send, off);
-        }
-    }
-    return v[0];
-}
-
-// Pixels per warp step: at most 8, at most 32/KP (one butterfly), and fewer for long
-// spectra so that the staged chunks stay in registers.
-__host__ __device__ constexpr int px_per_step(int nch, int kp) {
-    int px = 32 / kp < 8 ? 32 / kp : 8;
-    const int cap = 16 / nch < 1 ? 1 : 16 / nch;
-    return px < cap ? px : cap;
-}
-
-// VEC = 4: 16-byte chunks (L % 4 == 0); VEC = 1: 4-byte elements.
-// NCH = chunks per lane (NCH * 32 * VEC >= L); KP = K padded to a power of two <= 8.
-template <int VEC, int NCH, int KP>
-__global__ void __launch_bounds__(256) dwt_apply_kernel(const float* __restrict__ cube, int64_t P, int L,
-                                                        const float* __restrict__ A, int K,
-                                                        float* __restrict__ out) {
-    constexpr int PX = px_per_step(NCH, KP);
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int LV = L / VEC;
-
-    float a[NCH][KP][VEC];
-#pragma unroll
-    for (int i = 0; i < NCH; ++i) {
-        const int c = lane + 32 * i;
-#pragma unroll
-        for (int k = 0; k < KP; ++k)
-#pragma unroll
-            for (int e = 0; e < VEC; ++e)
-                a[i][k][e] = (c < LV && k < K) ? __ldg(A + (size_t)k * L + c * VEC + e) : 0.0f;
-    }
-
-    const int64_t ngroups = (P + PX - 1) / PX;
-    for (int64_t g = warp; g < ngroups; g += nwarps) {
-        const int64_t p0 = g * PX;
-        float x[PX][NCH][VEC];
-#pragma unroll
-        for (int p = 0; p < PX; ++p)
-#pragma unroll
-            for (int i = 0; i < NCH; ++i) {
-                const int c = lane + 32 * i;
-                const bool ok = (p0 + p < P) && (c < LV);
-                if constexpr (VEC == 4) {
-                    float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (ok) t = __ldcs(reinterpret_cast<const float4*>(cube + (p0 + p) * L) + c);
-                    x[p][i][0] = t.x; x[p][i][1] = t.y; x[p][i][2] = t.z; x[p][i][3] = t.w;
-                } else {
-                    x[p][i][0] = ok ? __ldcs(cube + (p0 + p) * L + c) : 0.0f;
-                }
-            }
-        float v[32];
-#pragma unroll
-        for (int t = PX * KP; t < 32; ++t) v[t] = 0.0f;
-#pragma unroll
-        for (int p = 0; p < PX; ++p)
-#pragma unroll
-            for (int k = 0; k < KP; ++k) {
-                float s = 0.0f;
-#pragma unroll
-                for (int i = 0; i < NCH; ++i)
-#pragma unroll
-                    for (int e = 0; e < VEC; ++e) s = fmaf(x[p][i][e], a[i][k][e], s);
-                v[p * KP + k] = s;
-            }
-        const float r = butterfly32(v, lane);
-        const int p = lane / KP, k = lane % KP;
-        if (k < K && p < PX && p0 + p < P) out[(p0 + p) * K + k] = r;
-    }
 }
 
 static int kpad(int K) { return K <= 1 ? 1 : K <= 2 ? 2 : K <= 4 ? 4 : 8; }

@@ -834,8 +834,9 @@ __device__ unsigned process_pixel(const FullArgs& a, const Geo& g, Smem<T>& m, S
             const int below = (maxabs > T(0)) ? sturm_below(m.dd, m.ee, D, tau, pivmin) : D;
             *s_m = D - below;
             if (gate && maxabs > T(0)) {
-                // selection conditioning: an eigenvalue within max|lambda| / cond_gate of tau
-                const T band = maxabs / (T)a.cond_gate;
+                // selection conditioning: an eigenvalue within max|lambda| / cond_gate of tau, the
+                // band never narrower than the BF16 perturbation of the Gram (2^-8 max|lambda|)
+                const T band = max(maxabs / (T)a.cond_gate, maxabs * T(0.00390625));
                 const int nb = sturm_below(m.dd, m.ee, D, tau + band, pivmin) -
                                sturm_below(m.dd, m.ee, D, tau - band, pivmin);
                 if (nb > 0) *s_m = -1 - *s_m;  // mark for the FP64 re-solve

@@ -36,6 +36,12 @@ class wdad_params(ctypes.Structure):
                 ("dwest_tau", ctypes.c_float)]
 
 
+class wdad_job(ctypes.Structure):
+    _fields_ = [("cube", ctypes.c_void_p), ("H", ctypes.c_int), ("W", ctypes.c_int), ("L", ctypes.c_int),
+                ("detector", ctypes.c_int), ("params", wdad_params), ("scores", ctypes.c_void_p),
+                ("flags", ctypes.c_void_p)]
+
+
 _lib = None
 _lock = threading.Lock()
 _handles: dict = {}
@@ -62,11 +68,19 @@ def lib() -> ctypes.CDLL:
     L.wdad_detect_all_host.argtypes = [vp, vp, i32, i32, i32, i32, i32, pp, vp, vp]
     L.wdad_window_census.argtypes = [vp, i32, i32, pp, vp, vp]
     L.wdad_window_moments.argtypes = [vp, f32p, i32, i32, i32, vp, i64, pp, f32p, f32p, vp]
+    jp = ctypes.POINTER(wdad_job)
+    L.wdad_autotune.argtypes = [vp, i32, i32, i32, ctypes.POINTER(i32), vp]
+    L.wdad_batch_create.argtypes = [vp, i32, jp, i32, i32, ctypes.POINTER(vp), vp]
+    L.wdad_batch_launch.argtypes = [vp, vp]
+    L.wdad_batch_status.argtypes = [vp, ctypes.POINTER(i32)]
+    L.wdad_batch_destroy.argtypes = [vp]
+    L.wdad_batch_run.argtypes = [vp, i32, jp, vp]
     L.wdad_detect_all_noalloc.argtypes = [f32p, i32, i32, i32, pp, f32p, vp, vp]
     L.wdad_auc.argtypes = [vp, vp, i64, ctypes.POINTER(ctypes.c_double)]
     for name in ("wdad_create", "wdad_destroy", "wdad_last_error_detail", "wdad_dwt_approx", "wdad_detect",
                  "wdad_detect_all", "wdad_detect_all_host", "wdad_window_census", "wdad_auc",
-                 "wdad_detect_all_noalloc", "wdad_window_moments"):
+                 "wdad_detect_all_noalloc", "wdad_window_moments", "wdad_autotune", "wdad_batch_create",
+                 "wdad_batch_launch", "wdad_batch_status", "wdad_batch_destroy", "wdad_batch_run"):
         getattr(L, name).restype = i32
     L.wdad_query_K.restype = i32
     _lib = L
@@ -231,6 +245,75 @@ def wdad_window_moments(cube, pixels, params: wdad_params | None = None, **over)
     _check(lib().wdad_window_moments(h, cube.data_ptr(), H, W, L, pix.data_ptr(), n, ctypes.byref(p), mu.data_ptr(),
                                      cov.data_ptr(), _stream(cube)), h)
     return mu, cov
+
+
+def wdad_autotune(D: int, inner: int, outer: int, device: int = 0) -> int:
+    """Tile height the autotuner picks for D bands and an (inner, outer) window."""
+    import torch
+    h = handle(device)
+    th = ctypes.c_int(0)
+    _check(lib().wdad_autotune(h, D, inner, outer, ctypes.byref(th),
+                               ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)), h)
+    return th.value
+
+
+def _jobs(jobs):
+    arr = (wdad_job * len(jobs))()
+    for i, j in enumerate(jobs):
+        cube = _cube(j["cube"])
+        H, W, L = cube.shape
+        p = j.get("params") or wdad_default_params(**j.get("over", {}))
+        arr[i] = wdad_job(cube.data_ptr(), H, W, L, int(j["detector"]), p, j["scores"].data_ptr(),
+                          j["flags"].data_ptr() if j.get("flags") is not None else None)
+    return arr
+
+
+class wdad_batch:
+    """A8: many reduced-path jobs in one persistent launch (optionally one CUDA graph).
+    jobs: list of dicts {cube: CUDA [H,W,L], detector: 0..3, scores: CUDA [H,W] or [3,H,W],
+    params or over: wdad_params fields, flags: optional CUDA uint8 [H,W]}."""
+
+    def __init__(self, jobs, autotune: bool = True, use_graph: bool = True, device: int = 0):
+        import torch
+        self.device = device
+        self._keep = list(jobs)
+        self._arr = _jobs(jobs)
+        self._h = handle(device)
+        b = ctypes.c_void_p()
+        st = ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+        _check(lib().wdad_batch_create(self._h, len(jobs), self._arr, int(autotune), int(use_graph), ctypes.byref(b),
+                                       st), self._h)
+        self._b = b.value
+        self.n = len(jobs)
+
+    def launch(self):
+        import torch
+        _check(lib().wdad_batch_launch(self._b, ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)),
+               self._h)
+
+    def status(self):
+        """Synchronise; returns (wdad status code, per-job tile heights)."""
+        ths = (ctypes.c_int * self.n)()
+        st = lib().wdad_batch_status(self._b, ths)
+        return st, list(ths)
+
+    def close(self):
+        if self._b:
+            lib().wdad_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def wdad_batch_run(jobs, device: int = 0):
+    import torch
+    arr = _jobs(jobs)
+    h = handle(device)
+    _check(lib().wdad_batch_run(h, len(jobs), arr, ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)), h)
 
 
 def wdad_window_census(H: int, W: int, params: wdad_params | None = None, device: int = 0, **over):
