@@ -253,7 +253,9 @@ wdad_status autotune(wdad_ctx* h, int D, int inner, int outer, int* out, cudaStr
         return fail(h, WDAD_ERR_CUDA, "autotune events");
     int best = 0;
     float best_ms = 1e30f;
-    for (int th : {32, 16, 8, 4, 2}) {
+    // sliding box sums restart every th rows; th <= 16 keeps the FP32 error at the level the
+    // parity tests pin
+    for (int th : {16, 8, 4, 2}) {
         if (wdad::detect_small_smem(D, inner, outer, th) > 227 * 1024) continue;
         if (wdad::launch_detect_small_th(a, th, s) != cudaSuccess) { cudaGetLastError(); continue; }
         cudaEventRecord(e0, s);

@@ -411,29 +411,37 @@ __device__ void detect_tile(const DetectArgs& a, int th, int tile_x, int tile_y,
     float* hso = xs + (size_t)g.HR * g.XP * P::DP;
     float* hsi = hso + (size_t)NC * g.HR * HP;
     __shared__ float cref[8];
+    __shared__ float red[16][8];
 
-    // stage 0 + tile reference: the mean of the halo region, summed by warp 0 in a fixed order
+    // stage 0 + tile reference: the mean of the halo region, as 16 fixed partial sums (halo
+    // rows r = v mod 16) combined in a fixed order, whatever the block size
     float part[D];
     load_halo_spec<D>(g, a.x, xs, part);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     __syncthreads();
-    if (warp == 0) {
+    for (int v = warp; v < 16; v += nw) {
         float acc[D];
 #pragma unroll
         for (int k = 0; k < D; ++k) acc[k] = 0.f;
-        for (int r = 0; r < g.HR; ++r)
+        for (int r = v; r < g.HR; r += 16)
             for (int c = lane; c < g.WR; c += 32) {
-                const float* v = xs + ((size_t)r * g.XP + c) * P::DP;
+                const float* px = xs + ((size_t)r * g.XP + c) * P::DP;
 #pragma unroll
-                for (int k = 0; k < D; ++k) acc[k] += v[k];
+                for (int k = 0; k < D; ++k) acc[k] += px[k];
             }
 #pragma unroll
         for (int k = 0; k < D; ++k) {
-            float v = acc[k];
+            float t = acc[k];
 #pragma unroll
-            for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) cref[k] = v / (float)(g.HR * g.WR);
+            for (int o = 16; o >= 1; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == 0) red[v][k] = t;
         }
+    }
+    __syncthreads();
+    if (threadIdx.x < D) {
+        float t = 0.f;
+        for (int v = 0; v < 16; ++v) t += red[v][threadIdx.x];
+        cref[threadIdx.x] = t / (float)(g.HR * g.WR);
     }
     __syncthreads();
     // stage 1: shift in place
