@@ -195,6 +195,49 @@ wdad_status wdad_batch_destroy(wdad_batch b);
 /* One-shot: create (default plans, no graph), launch on `stream`, synchronise, destroy. */
 wdad_status wdad_batch_run(wdad_handle h, int n, const wdad_job* jobs, void* stream);
 
+/* A9 — learned screening.  A 4-layer CNN on the DWT approximation matrix:
+ * K -> 32 (5x5, ReLU) -> 32 (5x5, ReLU) -> 32 (5x5, ReLU) -> 1 (3x3), "same" zero padding,
+ * receptive field 15 x 15, predicting log(1 + DWT-LRX score).  Activations NHWC float32;
+ * FP32 master weights trained with Adam, forward with BF16-rounded weights (bf16_weights = 1)
+ * or the masters (0); the paper has no such network (it is an addition on top of Sec. 4). */
+typedef struct wdad_cnn_ctx* wdad_cnn;
+
+/* New network with He-uniform weights drawn from splitmix64(seed); max_batch_pixels bounds
+ * B * H * W of training batches (device buffers are sized for it). */
+wdad_status wdad_cnn_create(wdad_handle h, int K, int bf16_weights, uint64_t seed, int64_t max_batch_pixels,
+                            wdad_cnn* out);
+wdad_status wdad_cnn_destroy(wdad_cnn c);
+/* Input normalisation (host [2K]: per-channel mean then std) applied to raw approximation input. */
+wdad_status wdad_cnn_set_norm(wdad_cnn c, const float* host_mean_std);
+/* Parameter count (and, when host != NULL, a host copy of the FP32 masters, per layer
+ * weights [ci][ky*k+kx][co] then biases). */
+wdad_status wdad_cnn_params(wdad_cnn c, float* host, int64_t* count);
+/* Replace the masters (resets the Adam state). */
+wdad_status wdad_cnn_set_params(wdad_cnn c, const float* host, int64_t count);
+/* pred [B][H][W] from raw x [B][H][W][K] (device); normalisation applied inside. */
+wdad_status wdad_cnn_forward(wdad_cnn c, const float* x, int B, int H, int W, float* pred, void* stream);
+/* Gradients of the interior MSE (7-pixel border excluded) for normalised x [B][H][W][K] and
+ * targets [B][H][W] (device); host_grad [count] and host_loss (both nullable); synchronises. */
+wdad_status wdad_cnn_grad(wdad_cnn c, const float* x, const float* target, int B, int H, int W, float* host_grad,
+                          float* host_loss, void* stream);
+/* `steps` Adam steps on random crop x crop patches (batch per step, positions from
+ * splitmix64(seed, step)) of one reduced cube approx [H][W][K] with targets
+ * log(1 + score[H][W]); host_loss (nullable) receives the last batch loss. */
+wdad_status wdad_cnn_train(wdad_cnn c, const float* approx, const float* score, int H, int W, int steps, int batch,
+                           int crop, float lr, uint64_t seed, float* host_loss, void* stream);
+/* Versioned checkpoint: masters, Adam moments, step, normalisation. */
+wdad_status wdad_cnn_save(wdad_cnn c, const char* path);
+wdad_status wdad_cnn_load(wdad_handle h, const char* path, int64_t max_batch_pixels, wdad_cnn* out);
+/* Screened LRX: A1 on the cube, the CNN on row tiles (tile_rows + 7-row halo), the top
+ * top_frac of its predictions plus a random audit of audit_frac (splitmix64(seed, pixel)),
+ * then the exact LRX (exact_reduce = 0: full band; 1: on the reduced cube) on the selected
+ * pixels only.  score [H][W]: exact LRX where selected, -inf elsewhere.  pred [H][W] and
+ * selected [H][W] (1 = top, 2 = audit, 0 = skipped) are nullable; *n_selected (host,
+ * nullable) receives the number of exact evaluations.  Synchronises `stream`. */
+wdad_status wdad_screen_run(wdad_handle h, wdad_cnn c, const float* cube, int H, int W, int L, const wdad_params* p,
+                            float top_frac, float audit_frac, uint64_t seed, int tile_rows, int exact_reduce,
+                            float* score, float* pred, uint8_t* selected, int64_t* n_selected, void* stream);
+
 /* A10 — pixel-level ROC AUC of a score map against a truth mask (Sec. 5.3.1):
  * Mann-Whitney U with ties counted one half.  HOST pointers; NaN scores rank lowest.
  * Writes NaN when the mask has no positive or no negative pixel. */

@@ -60,6 +60,11 @@ def lib():
         L.or_window_moments.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         i64p, ctypes.c_int64, dp, dp, ctypes.c_int]
         L.or_auc.argtypes = [dp, u8p, ctypes.c_int64]
+        L.or_cnn_nparam.argtypes = [ctypes.c_int]
+        L.or_cnn_nparam.restype = ctypes.c_long
+        L.or_cnn_forward.argtypes = [ctypes.c_int, dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp]
+        L.or_cnn_grad.argtypes = [ctypes.c_int, dp, dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                  dp, dp]
         L.or_auc.restype = ctypes.c_double
         _lib = L
     return _lib
@@ -177,6 +182,33 @@ def window_census(H: int, W: int, inner: int, outer: int, border: int = 0, pixel
                               _ptr(out, ctypes.c_int64)) != 0:
         raise ValueError("bad window")
     return out
+
+
+def cnn_nparam(K: int = 4) -> int:
+    return int(lib().or_cnn_nparam(K))
+
+
+def cnn_forward(params: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """Screening CNN forward (FP64): x [B][H][W][K] (normalised) -> [B][H][W]."""
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    xx = np.ascontiguousarray(x, dtype=np.float64)
+    B, H, W, K = xx.shape
+    out = np.zeros((B, H, W))
+    lib().or_cnn_forward(K, _ptr(p, ctypes.c_double), _ptr(xx, ctypes.c_double), B, H, W, _ptr(out, ctypes.c_double))
+    return out
+
+
+def cnn_grad(params: np.ndarray, x: np.ndarray, t: np.ndarray, edge: int = 7):
+    """Loss (interior MSE) and its gradient with respect to every parameter (FP64)."""
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    xx = np.ascontiguousarray(x, dtype=np.float64)
+    tt = np.ascontiguousarray(t, dtype=np.float64)
+    B, H, W, K = xx.shape
+    g = np.zeros_like(p)
+    loss = ctypes.c_double(0.0)
+    lib().or_cnn_grad(K, _ptr(p, ctypes.c_double), _ptr(xx, ctypes.c_double), _ptr(tt, ctypes.c_double), B, H, W, edge,
+                      _ptr(g, ctypes.c_double), ctypes.byref(loss))
+    return loss.value, g
 
 
 def auc(score: np.ndarray, mask: np.ndarray) -> float:

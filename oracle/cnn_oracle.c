@@ -1,0 +1,160 @@
+/*
+ * FP64 CPU oracle of the screening CNN: forward and backward of
+ *   K -> 32 (5x5, ReLU) -> 32 (5x5, ReLU) -> 32 (5x5, ReLU) -> 1 (3x3), "same" zero padding,
+ * with the mean squared error over the interior of each image (a border of `edge` pixels
+ * excluded).  Parameters per layer: weights [ci][ky*k+kx][co], then biases [co].
+ * Activations [B][H][W][C].  TEST INFRASTRUCTURE ONLY; plain loops, no shared code with the
+ * CUDA path.  The network is an addition to the paper's method (no counterpart in it).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+static const int KS[4] = {5, 5, 5, 3};
+
+static void dims(int K, int l, int* cin, int* cout, int* k) {
+    *cin = l == 0 ? K : 32;
+    *cout = l == 3 ? 1 : 32;
+    *k = KS[l];
+}
+
+long or_cnn_nparam(int K) {
+    long n = 0;
+    for (int l = 0; l < 4; ++l) {
+        int ci, co, k;
+        dims(K, l, &ci, &co, &k);
+        n += (long)ci * k * k * co + co;
+    }
+    return n;
+}
+
+/* out[b,y,x,co] = bias[co] + sum_{ci,ky,kx} in[b, y+ky-p, x+kx-p, ci] w[ci, ky*k+kx, co] */
+static void conv(const double* in, int B, int H, int W, int cin, const double* w, const double* bias, int cout, int k,
+                 double* out) {
+    int p = k / 2;
+    for (int b = 0; b < B; ++b)
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) {
+                double* o = out + (((long)b * H + y) * W + x) * cout;
+                for (int co = 0; co < cout; ++co) o[co] = bias[co];
+                for (int ky = 0; ky < k; ++ky) {
+                    int yy = y + ky - p;
+                    if (yy < 0 || yy >= H) continue;
+                    for (int kx = 0; kx < k; ++kx) {
+                        int xx = x + kx - p;
+                        if (xx < 0 || xx >= W) continue;
+                        const double* a = in + (((long)b * H + yy) * W + xx) * cin;
+                        for (int ci = 0; ci < cin; ++ci) {
+                            const double* wr = w + ((long)ci * k * k + ky * k + kx) * cout;
+                            for (int co = 0; co < cout; ++co) o[co] += a[ci] * wr[co];
+                        }
+                    }
+                }
+            }
+}
+
+/* given dz (gradient w.r.t. conv output): accumulate dw, db and (nullable) din */
+static void conv_back(const double* in, const double* dz, int B, int H, int W, int cin, const double* w, int cout,
+                      int k, double* dw, double* db, double* din) {
+    int p = k / 2;
+    if (din) memset(din, 0, sizeof(double) * (size_t)B * H * W * cin);
+    for (int b = 0; b < B; ++b)
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) {
+                const double* d = dz + (((long)b * H + y) * W + x) * cout;
+                for (int co = 0; co < cout; ++co) db[co] += d[co];
+                for (int ky = 0; ky < k; ++ky) {
+                    int yy = y + ky - p;
+                    if (yy < 0 || yy >= H) continue;
+                    for (int kx = 0; kx < k; ++kx) {
+                        int xx = x + kx - p;
+                        if (xx < 0 || xx >= W) continue;
+                        const double* a = in + (((long)b * H + yy) * W + xx) * cin;
+                        double* da = din ? din + (((long)b * H + yy) * W + xx) * cin : NULL;
+                        for (int ci = 0; ci < cin; ++ci) {
+                            const long wb = ((long)ci * k * k + ky * k + kx) * cout;
+                            double g = 0.0;
+                            for (int co = 0; co < cout; ++co) {
+                                dw[wb + co] += a[ci] * d[co];
+                                g += w[wb + co] * d[co];
+                            }
+                            if (da) da[ci] += g;
+                        }
+                    }
+                }
+            }
+}
+
+int or_cnn_forward(int K, const double* params, const double* x, int B, int H, int W, double* pred) {
+    long px = (long)B * H * W;
+    double* a = (double*)malloc(sizeof(double) * px * 32);
+    double* c = (double*)malloc(sizeof(double) * px * 32);
+    const double* in = x;
+    long off = 0;
+    for (int l = 0; l < 4; ++l) {
+        int ci, co, k;
+        dims(K, l, &ci, &co, &k);
+        const double* w = params + off;
+        const double* bias = w + (long)ci * k * k * co;
+        off += (long)ci * k * k * co + co;
+        double* out = (l == 3) ? pred : (l % 2 == 0 ? a : c);
+        conv(in, B, H, W, ci, w, bias, co, k, out);
+        if (l < 3)
+            for (long i = 0; i < px * co; ++i) out[i] = out[i] > 0.0 ? out[i] : 0.0;
+        in = out;
+    }
+    free(a); free(c);
+    return 0;
+}
+
+/* loss = mean over interior pixels of (pred - t)^2; grad (nparam) */
+int or_cnn_grad(int K, const double* params, const double* x, const double* t, int B, int H, int W, int edge,
+                double* grad, double* loss) {
+    long px = (long)B * H * W;
+    double* act[4];
+    for (int l = 0; l < 4; ++l) act[l] = (double*)malloc(sizeof(double) * px * 32);
+    const double* in = x;
+    long woff[4];
+    long off = 0;
+    for (int l = 0; l < 4; ++l) {
+        int ci, co, k;
+        dims(K, l, &ci, &co, &k);
+        woff[l] = off;
+        const double* w = params + off;
+        conv(in, B, H, W, ci, w, w + (long)ci * k * k * co, co, k, act[l]);
+        if (l < 3)
+            for (long i = 0; i < px * co; ++i) act[l][i] = act[l][i] > 0.0 ? act[l][i] : 0.0;
+        off += (long)ci * k * k * co + co;
+        in = act[l];
+    }
+    long n = (long)B * (H - 2 * edge) * (W - 2 * edge);
+    double* dz = (double*)malloc(sizeof(double) * px * 32);
+    double* dnext = (double*)malloc(sizeof(double) * px * 32);
+    double s = 0.0;
+    for (int b = 0; b < B; ++b)
+        for (int y = 0; y < H; ++y)
+            for (int xx = 0; xx < W; ++xx) {
+                long i = ((long)b * H + y) * W + xx;
+                int interior = y >= edge && y < H - edge && xx >= edge && xx < W - edge;
+                double r = act[3][i] - t[i];
+                dz[i] = interior ? 2.0 * r / n : 0.0;
+                if (interior) s += r * r;
+            }
+    *loss = s / n;
+    memset(grad, 0, sizeof(double) * or_cnn_nparam(K));
+    for (int l = 3; l >= 0; --l) {
+        int ci, co, k;
+        dims(K, l, &ci, &co, &k);
+        const double* lin = l == 0 ? x : act[l - 1];
+        double* dw = grad + woff[l];
+        double* db = dw + (long)ci * k * k * co;
+        conv_back(lin, dz, B, H, W, ci, params + woff[l], co, k, dw, db, l > 0 ? dnext : NULL);
+        if (l > 0) {
+            for (long i = 0; i < px * ci; ++i) dnext[i] = lin[i] > 0.0 ? dnext[i] : 0.0;  /* ReLU of layer l-1 */
+            double* tmp = dz; dz = dnext; dnext = tmp;
+        }
+    }
+    for (int l = 0; l < 4; ++l) free(act[l]);
+    free(dz); free(dnext);
+    return 0;
+}

@@ -14,6 +14,7 @@
 #include <map>
 
 #include "batch.h"
+#include "cnn.h"
 #include "internal.h"
 
 struct wdad_ctx {
@@ -25,6 +26,11 @@ struct wdad_ctx {
     std::vector<DwtPlan> dwt_plans;
     std::map<long long, int> tuned;  // (D, inner, outer) -> autotuned tile height
     std::string err;
+};
+
+struct wdad_cnn_ctx {
+    wdad_ctx* h = nullptr;
+    wdad::cnn::Net net;
 };
 
 struct wdad_batch_ctx {
@@ -273,6 +279,18 @@ wdad_status autotune(wdad_ctx* h, int D, int inner, int outer, int* out, cudaStr
     *out = best;
     return WDAD_OK;
 }
+
+void cnn_free(wdad_cnn_ctx* c) {
+    if (!c) return;
+    auto& n = c->net;
+    cudaFree(n.w); cudaFree(n.wf); cudaFree(n.m); cudaFree(n.v); cudaFree(n.grad); cudaFree(n.wt);
+    cudaFree(n.norm); cudaFree(n.act); cudaFree(n.loss); cudaFree(n.cx); cudaFree(n.ct);
+    delete c;
+}
+
+// magic, version, K, bf16, step, nparam, then w, m, v (float32), norm (2K float32)
+constexpr uint32_t kCnnMagic = 0x4E4E4357u;  // "WCNN"
+constexpr uint32_t kCnnVersion = 1;
 
 void batch_free(wdad_batch_ctx* b) {
     if (!b) return;
@@ -654,6 +672,302 @@ wdad_status wdad_batch_run(wdad_handle h, int n, const wdad_job* jobs, void* str
     if (st == WDAD_OK) st = wdad_batch_status(b, nullptr);
     wdad_batch_destroy(b);
     return st;
+}
+
+
+wdad_status wdad_cnn_create(wdad_handle h, int K, int bf16_weights, uint64_t seed, int64_t max_batch_pixels,
+                            wdad_cnn* out) {
+    if (!h) return WDAD_ERR_ARG;
+    if (!out || K < 1 || K > 8 || max_batch_pixels < 1) return fail(h, WDAD_ERR_ARG, "cnn: K in 1..8, max pixels >= 1");
+    *out = nullptr;
+    wdad_cnn_ctx* c = nullptr;
+    try {
+        DeviceGuard g(h->device);
+        c = new wdad_cnn_ctx();
+        c->h = h;
+        auto& n = c->net;
+        n.K = K;
+        n.bf16 = bf16_weights ? 1 : 0;
+        n.max_px = max_batch_pixels;
+        wdad::cnn::param_layout(K, n.woff, n.boff, &n.nparam);
+        cudaError_t e = cudaSuccess;
+        for (float** pp : {&n.w, &n.wf, &n.m, &n.v, &n.grad})
+            if (e == cudaSuccess) e = cudaMalloc(pp, sizeof(float) * n.nparam);
+        if (e == cudaSuccess) e = cudaMalloc(&n.wt, sizeof(float) * 32 * 32 * 25);
+        if (e == cudaSuccess) e = cudaMalloc(&n.norm, sizeof(float) * 2 * K);
+        if (e == cudaSuccess) e = cudaMalloc(&n.act, sizeof(float) * wdad::cnn::act_floats(max_batch_pixels));
+        if (e == cudaSuccess) e = cudaMalloc(&n.loss, sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc(&n.cx, sizeof(float) * (size_t)max_batch_pixels * K);
+        if (e == cudaSuccess) e = cudaMalloc(&n.ct, sizeof(float) * (size_t)max_batch_pixels);
+        if (e != cudaSuccess) { cnn_free(c); return cuda_fail(h, e, "cnn allocation"); }
+        std::vector<float> norm(2 * K);
+        for (int k = 0; k < K; ++k) { norm[k] = 0.f; norm[K + k] = 1.f; }
+        e = cudaMemcpy(n.norm, norm.data(), sizeof(float) * 2 * K, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = wdad::cnn::net_init(n, seed, 0);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) { cnn_free(c); return cuda_fail(h, e, "cnn init"); }
+        *out = c;
+        return WDAD_OK;
+    } catch (...) {
+        cnn_free(c);
+        return fail(h, WDAD_ERR_NOMEM, "host exception");
+    }
+}
+
+wdad_status wdad_cnn_destroy(wdad_cnn c) {
+    if (!c) return WDAD_ERR_ARG;
+    DeviceGuard g(c->h->device);
+    cudaDeviceSynchronize();
+    cnn_free(c);
+    return WDAD_OK;
+}
+
+wdad_status wdad_cnn_set_norm(wdad_cnn c, const float* host_mean_std) {
+    if (!c || !host_mean_std) return WDAD_ERR_ARG;
+    DeviceGuard g(c->h->device);
+    for (int k = 0; k < c->net.K; ++k)
+        if (!(host_mean_std[c->net.K + k] > 0.f)) return fail(c->h, WDAD_ERR_ARG, "cnn: std must be > 0");
+    cudaError_t e = cudaMemcpy(c->net.norm, host_mean_std, sizeof(float) * 2 * c->net.K, cudaMemcpyHostToDevice);
+    return e == cudaSuccess ? WDAD_OK : cuda_fail(c->h, e, "cnn norm");
+}
+
+wdad_status wdad_cnn_params(wdad_cnn c, float* host, int64_t* count) {
+    if (!c || !count) return WDAD_ERR_ARG;
+    DeviceGuard g(c->h->device);
+    *count = (int64_t)c->net.nparam;
+    if (!host) return WDAD_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(host, c->net.w, sizeof(float) * c->net.nparam, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? WDAD_OK : cuda_fail(c->h, e, "cnn params");
+}
+
+wdad_status wdad_cnn_set_params(wdad_cnn c, const float* host, int64_t count) {
+    if (!c || !host || count != (int64_t)c->net.nparam) return WDAD_ERR_ARG;
+    DeviceGuard g(c->h->device);
+    auto& n = c->net;
+    cudaError_t e = cudaMemcpy(n.w, host, sizeof(float) * n.nparam, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(n.m, 0, sizeof(float) * n.nparam);
+    if (e == cudaSuccess) e = cudaMemset(n.v, 0, sizeof(float) * n.nparam);
+    n.step = 0;
+    if (e == cudaSuccess) e = wdad::cnn::net_refresh_forward_copy(n, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    return e == cudaSuccess ? WDAD_OK : cuda_fail(c->h, e, "cnn set params");
+}
+
+wdad_status wdad_cnn_forward(wdad_cnn c, const float* x, int B, int H, int W, float* pred, void* stream) {
+    if (!c || !x || !pred || B < 1 || H < 1 || W < 1) return WDAD_ERR_ARG;
+    DeviceGuard g(c->h->device);
+    wdad_ctx* h = c->h;
+    const int64_t px = (int64_t)B * H * W;
+    wdad_status st = ensure_ws(h, sizeof(float) * (size_t)px * 96 + 256);
+    if (st != WDAD_OK) return st;
+    float* a0 = (float*)h->ws;
+    cudaError_t e = wdad::cnn::net_forward(c->net, x, B, H, W, c->net.norm, a0, a0 + px * 32, a0 + px * 64, pred,
+                                           (cudaStream_t)stream);
+    return e == cudaSuccess ? WDAD_OK : cuda_fail(h, e, "cnn forward");
+}
+
+wdad_status wdad_cnn_grad(wdad_cnn c, const float* x, const float* target, int B, int H, int W, float* host_grad,
+                          float* host_loss, void* stream) {
+    if (!c || !x || !target || B < 1 || H < 15 || W < 15) return WDAD_ERR_ARG;
+    if ((int64_t)B * H * W > c->net.max_px) return fail(c->h, WDAD_ERR_ARG, "cnn: batch larger than max pixels");
+    DeviceGuard g(c->h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = wdad::cnn::net_grad(c->net, x, target, B, H, W, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && host_grad)
+        e = cudaMemcpy(host_grad, c->net.grad, sizeof(float) * c->net.nparam, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && host_loss) e = cudaMemcpy(host_loss, c->net.loss, sizeof(float), cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? WDAD_OK : cuda_fail(c->h, e, "cnn grad");
+}
+
+wdad_status wdad_cnn_train(wdad_cnn c, const float* approx, const float* score, int H, int W, int steps, int batch,
+                           int crop, float lr, uint64_t seed, float* host_loss, void* stream) {
+    if (!c || !approx || !score || steps < 0 || batch < 1 || crop < 15 || crop > H || crop > W || !(lr > 0.f))
+        return WDAD_ERR_ARG;
+    auto& n = c->net;
+    if ((int64_t)batch * crop * crop > n.max_px) return fail(c->h, WDAD_ERR_ARG, "cnn: batch larger than max pixels");
+    DeviceGuard g(c->h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    for (int it = 0; it < steps && e == cudaSuccess; ++it) {
+        e = wdad::cnn::sample_crops(n, approx, score, H, W, batch, crop, crop, seed, (uint64_t)n.step, n.cx, n.ct, s);
+        if (e == cudaSuccess) e = wdad::cnn::net_grad(n, n.cx, n.ct, batch, crop, crop, s);
+        if (e == cudaSuccess) e = wdad::cnn::net_adam(n, lr, s);
+    }
+    if (e == cudaSuccess && host_loss) {
+        e = cudaMemcpyAsync(host_loss, n.loss, sizeof(float), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    return e == cudaSuccess ? WDAD_OK : cuda_fail(c->h, e, "cnn train");
+}
+
+wdad_status wdad_cnn_save(wdad_cnn c, const char* path) {
+    if (!c || !path) return WDAD_ERR_ARG;
+    DeviceGuard g(c->h->device);
+    auto& n = c->net;
+    std::vector<float> w(n.nparam), m(n.nparam), v(n.nparam), norm(2 * n.K);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(w.data(), n.w, sizeof(float) * n.nparam, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(m.data(), n.m, sizeof(float) * n.nparam, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(v.data(), n.v, sizeof(float) * n.nparam, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(norm.data(), n.norm, sizeof(float) * 2 * n.K, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c->h, e, "cnn save");
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(c->h, WDAD_ERR_ARG, "cannot open %s", path);
+    const uint32_t hdr[5] = {kCnnMagic, kCnnVersion, (uint32_t)n.K, (uint32_t)n.bf16, (uint32_t)n.step};
+    const uint64_t np = n.nparam;
+    bool ok = std::fwrite(hdr, sizeof hdr, 1, f) == 1 && std::fwrite(&np, sizeof np, 1, f) == 1 &&
+              std::fwrite(w.data(), sizeof(float), np, f) == np && std::fwrite(m.data(), sizeof(float), np, f) == np &&
+              std::fwrite(v.data(), sizeof(float), np, f) == np &&
+              std::fwrite(norm.data(), sizeof(float), norm.size(), f) == norm.size();
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? WDAD_OK : fail(c->h, WDAD_ERR_ARG, "write failed: %s", path);
+}
+
+wdad_status wdad_cnn_load(wdad_handle h, const char* path, int64_t max_batch_pixels, wdad_cnn* out) {
+    if (!h || !path || !out) return WDAD_ERR_ARG;
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(h, WDAD_ERR_ARG, "cannot open %s", path);
+    uint32_t hdr[5];
+    uint64_t np = 0;
+    if (std::fread(hdr, sizeof hdr, 1, f) != 1 || std::fread(&np, sizeof np, 1, f) != 1 || hdr[0] != kCnnMagic ||
+        hdr[1] != kCnnVersion || hdr[2] < 1 || hdr[2] > 8) {
+        std::fclose(f);
+        return fail(h, WDAD_ERR_ARG, "%s is not a version-%u CNN checkpoint", path, kCnnVersion);
+    }
+    wdad_cnn c = nullptr;
+    wdad_status st = wdad_cnn_create(h, (int)hdr[2], (int)hdr[3], 0, max_batch_pixels, &c);
+    if (st != WDAD_OK) { std::fclose(f); return st; }
+    auto& n = c->net;
+    if (np != n.nparam) { std::fclose(f); wdad_cnn_destroy(c); return fail(h, WDAD_ERR_ARG, "checkpoint size mismatch"); }
+    std::vector<float> w(np), m(np), v(np), norm(2 * n.K);
+    const bool ok = std::fread(w.data(), sizeof(float), np, f) == np && std::fread(m.data(), sizeof(float), np, f) == np &&
+                    std::fread(v.data(), sizeof(float), np, f) == np &&
+                    std::fread(norm.data(), sizeof(float), norm.size(), f) == norm.size();
+    std::fclose(f);
+    if (!ok) { wdad_cnn_destroy(c); return fail(h, WDAD_ERR_ARG, "truncated checkpoint %s", path); }
+    DeviceGuard g(h->device);
+    cudaError_t e = cudaMemcpy(n.w, w.data(), sizeof(float) * np, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(n.m, m.data(), sizeof(float) * np, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(n.v, v.data(), sizeof(float) * np, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(n.norm, norm.data(), sizeof(float) * norm.size(), cudaMemcpyHostToDevice);
+    n.step = (int)hdr[4];
+    if (e == cudaSuccess) e = wdad::cnn::net_refresh_forward_copy(n, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) { wdad_cnn_destroy(c); return cuda_fail(h, e, "cnn load"); }
+    *out = c;
+    return WDAD_OK;
+}
+
+wdad_status wdad_screen_run(wdad_handle h, wdad_cnn c, const float* cube, int H, int W, int L, const wdad_params* p,
+                            float top_frac, float audit_frac, uint64_t seed, int tile_rows, int exact_reduce,
+                            float* score, float* pred_out, uint8_t* selected, int64_t* n_selected, void* stream) {
+    if (!h) return WDAD_ERR_ARG;
+    if (!c || !score || !(top_frac > 0.f && top_frac <= 1.f) || !(audit_frac >= 0.f && audit_frac < 1.f) ||
+        tile_rows < 1 || (exact_reduce != 0 && exact_reduce != 1))
+        return fail(h, WDAD_ERR_ARG, "screen: fractions in (0,1], tile_rows >= 1, exact_reduce 0/1");
+    try {
+        DeviceGuard g(h->device);
+        wdad_status st = check_params(h, p);
+        if (st != WDAD_OK) return st;
+        st = check_cube(h, cube, H, W, L);
+        if (st != WDAD_OK) return st;
+        const int64_t P = (int64_t)H * W;
+        if (P == 0) { if (n_selected) *n_selected = 0; return WDAD_OK; }
+        cudaStream_t s = (cudaStream_t)stream;
+        auto& n = c->net;
+        const int K = wdad_query_K(L, p->wavelet_taps, p->level);
+        if (K != n.K) return fail(h, WDAD_ERR_ARG, "screen: the network expects K=%d, the cube gives K=%d", n.K, K);
+        if (!wdad::dwt_shape_supported(L, K)) return fail(h, WDAD_ERR_UNSUPPORTED, "screen: DWT shape L=%d", L);
+        const int halo = 7, rows_max = std::min(H, tile_rows + 2 * halo);
+        const int64_t tpx = (int64_t)rows_max * W;
+        const size_t b_ap = align256(sizeof(float) * (size_t)P * K);
+        const size_t b_pred = align256(sizeof(float) * (size_t)P);
+        const size_t b_act = align256(sizeof(float) * (size_t)tpx * (3 * 32 + 1));
+        const size_t b_list = align256(sizeof(int64_t) * (size_t)P);
+        const size_t b_hist = align256(sizeof(unsigned int) * 65536 + 64);
+        const size_t fixed = b_ap + b_pred + b_act + b_list + b_hist;
+        st = ensure_ws(h, fixed);
+        if (st != WDAD_OK) return st;
+        char* base = (char*)h->ws;
+        float* approx = (float*)base;
+        float* pred = (float*)(base + b_ap);
+        float* act = (float*)(base + b_ap + b_pred);
+        int64_t* list = (int64_t*)(base + b_ap + b_pred + b_act);
+        unsigned int* hist = (unsigned int*)(base + b_ap + b_pred + b_act + b_list);
+        unsigned long long* cnt = (unsigned long long*)(hist + 65536);
+        // A1 on the whole cube
+        const float* A = nullptr;
+        int k2 = 0;
+        st = get_dwt_plan(h, L, p->wavelet_taps, p->level, &A, &k2, s);
+        if (st != WDAD_OK) return st;
+        cudaError_t e = wdad::launch_dwt_approx(cube, P, L, A, K, approx, h->num_sms, s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "screen dwt");
+        // CNN over row tiles with a 7-row halo (receptive field 15)
+        for (int r0 = 0; r0 < H && e == cudaSuccess; r0 += tile_rows) {
+            const int r1 = std::min(H, r0 + tile_rows);
+            const int h0 = std::max(0, r0 - halo), h1 = std::min(H, r1 + halo);
+            const int hr = h1 - h0;
+            const int64_t npx = (int64_t)hr * W;
+            float* a0 = act;
+            float* a1 = a0 + npx * 32;
+            float* a2 = a1 + npx * 32;
+            float* o = a2 + npx * 32;
+            e = wdad::cnn::net_forward(n, approx + (size_t)h0 * W * K, 1, hr, W, n.norm, a0, a1, a2, o, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(pred + (size_t)r0 * W, o + (size_t)(r0 - h0) * W, sizeof(float) * (size_t)(r1 - r0) * W,
+                                    cudaMemcpyDeviceToDevice, s);
+        }
+        if (e != cudaSuccess) return cuda_fail(h, e, "screen cnn");
+        if (pred_out) {
+            e = cudaMemcpyAsync(pred_out, pred, sizeof(float) * (size_t)P, cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) return cuda_fail(h, e, "screen pred copy");
+        }
+        // top fraction threshold, audit draw, compaction
+        const int64_t kth = std::max<int64_t>(1, (int64_t)std::ceil((double)top_frac * (double)P));
+        uint32_t thr = 0;
+        e = wdad::cnn::top_threshold(pred, P, kth, hist, &thr, s);
+        if (e == cudaSuccess) e = wdad::cnn::select_pixels(pred, P, thr, audit_frac, seed, selected, list, cnt, s);
+        unsigned long long nsel = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&nsel, cnt, sizeof nsel, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "screen selection");
+        if (n_selected) *n_selected = (int64_t)nsel;
+        // unevaluated pixels score -inf; the exact detector fills the selected ones
+        e = wdad::cnn::fill(score, P, -INFINITY, s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "screen fill");
+        if (nsel == 0) return WDAD_OK;
+        wdad::FullArgs a{};
+        a.x = exact_reduce ? approx : cube;
+        a.H = H; a.W = W; a.D = exact_reduce ? K : L;
+        a.inner = p->inner; a.outer = p->outer; a.loading = p->loading; a.cond_gate = p->cond_gate;
+        a.border = p->border; a.dwest_mode = p->dwest_mode; a.precision = p->precision; a.dwest_tau = p->dwest_tau;
+        a.out[0] = score;
+        a.pix = list;
+        a.npix = (int64_t)nsel;
+        if (a.D <= 8) {
+            // reduced exact LRX: the whole reduced map is cheap; the selection keeps its values
+            wdad::DetectArgs d{};
+            d.x = approx; d.H = H; d.W = W; d.D = K;
+            d.inner = p->inner; d.outer = p->outer; d.loading = p->loading; d.border = p->border;
+            d.dwest_mode = p->dwest_mode; d.dwest_tau = p->dwest_tau;
+            d.out[0] = pred;  // the predictions are no longer needed
+            e = wdad::launch_detect_small_th(d, wdad::detect_small_default_th(K, p->inner, p->outer), s);
+            if (e == cudaSuccess) e = wdad::cnn::scatter_list(pred, list, (int64_t)nsel, score, s);
+            return e == cudaSuccess ? WDAD_OK : cuda_fail(h, e, "screen exact reduced detector");
+        }
+        const size_t need = wdad::fullband_workspace_bytes(a, h->num_sms);
+        if (need == 0) return fail(h, WDAD_ERR_UNSUPPORTED, "screen: full-band LRX for %d bands", L);
+        st = ensure_ws(h, fixed + need);  // may move the workspace: recompute pointers
+        if (st != WDAD_OK) return st;
+        base = (char*)h->ws;
+        a.pix = (const int64_t*)(base + b_ap + b_pred + b_act);
+        e = wdad::launch_detect_full(a, base + fixed, h->ws_bytes - fixed, h->num_sms, s);
+        return e == cudaSuccess ? WDAD_OK : cuda_fail(h, e, "screen exact detector");
+    } catch (...) {
+        return fail(h, WDAD_ERR_NOMEM, "host exception");
+    }
 }
 
 wdad_status wdad_auc(const float* score, const uint8_t* mask, int64_t n, double* auc) {

@@ -969,7 +969,9 @@ __global__ void __launch_bounds__(FB_THREADS, 1) fullband_kernel(FullArgs a, Geo
     const int64_t P = (int64_t)a.H * a.W;
     const unsigned want = (a.out[0] ? 1u : 0u) | (a.out[1] ? 2u : 0u) | (a.out[2] ? 4u : 0u);
     const float fnan = __int_as_float(0x7fc00000);
-    for (int64_t pix = blockIdx.x; pix < P; pix += gridDim.x) {
+    const int64_t count = a.pix ? a.npix : P;
+    for (int64_t it = blockIdx.x; it < count; it += gridDim.x) {
+        const int64_t pix = a.pix ? a.pix[it] : it;
         const int py = (int)(pix / a.W), px = (int)(pix % a.W);
         if (a.border == 1 && (py - ro < 0 || py + ro >= a.H || px - ro < 0 || px + ro >= a.W)) {
             if (threadIdx.x < 3 && a.out[threadIdx.x]) a.out[threadIdx.x][pix] = fnan;
@@ -1131,7 +1133,7 @@ size_t fullband_workspace_bytes(const FullArgs& a, int num_sms) {
     if (a.precision == WDAD_PREC_FP64) make_geo<double>(a, &ok, &smem, &slab);
     else make_geo<float>(a, &ok, &smem, &slab);
     if (!ok) return 0;
-    return slab * (size_t)fb_grid(num_sms, (int64_t)a.H * a.W) + 256;
+    return slab * (size_t)fb_grid(num_sms, a.pix ? a.npix : (int64_t)a.H * a.W) + 256;
 }
 
 template <typename T>
@@ -1143,7 +1145,7 @@ static cudaError_t launch_fb(const FullArgs& a, void* ws, int num_sms, cudaStrea
     if (!ok) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(fullband_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int grid = fb_grid(num_sms, (int64_t)a.H * a.W);
+    const int grid = fb_grid(num_sms, a.pix ? a.npix : (int64_t)a.H * a.W);
     char* base = reinterpret_cast<char*>(((uintptr_t)ws + 255) & ~(uintptr_t)255);
     fullband_kernel<T><<<grid, FB_THREADS, smem, s>>>(a, g, g64, base, slab);
     return cudaGetLastError();
@@ -1183,7 +1185,7 @@ cudaError_t launch_window_moments(const FullArgs& a, const int64_t* pix, int64_t
 }
 
 cudaError_t launch_detect_full(const FullArgs& a, void* ws, size_t ws_bytes, int num_sms, cudaStream_t s) {
-    if ((int64_t)a.H * a.W == 0) return cudaSuccess;
+    if ((int64_t)a.H * a.W == 0 || (a.pix && a.npix == 0)) return cudaSuccess;
     if (ws_bytes < fullband_workspace_bytes(a, num_sms)) return cudaErrorInvalidValue;
     if (a.precision == WDAD_PREC_FP64) return launch_fb<double>(a, ws, num_sms, s);
     return launch_fb<float>(a, ws, num_sms, s);

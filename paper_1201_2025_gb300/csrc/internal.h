@@ -72,6 +72,8 @@ struct FullArgs {
     float* out[3];
     uint8_t* flags;
     int* status;  // nullable device word: set to a wdad_status when a bounded wait gives up
+    const int64_t* pix;  // nullable: only these pixels (linear indices), npix of them
+    int64_t npix;
 };
 size_t fullband_workspace_bytes(const FullArgs& a, int num_sms);
 cudaError_t launch_detect_full(const FullArgs& a, void* ws, size_t ws_bytes, int num_sms, cudaStream_t s);

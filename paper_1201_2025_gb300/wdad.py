@@ -75,12 +75,27 @@ def lib() -> ctypes.CDLL:
     L.wdad_batch_status.argtypes = [vp, ctypes.POINTER(i32)]
     L.wdad_batch_destroy.argtypes = [vp]
     L.wdad_batch_run.argtypes = [vp, i32, jp, vp]
+    L.wdad_cnn_create.argtypes = [vp, i32, i32, ctypes.c_uint64, i64, ctypes.POINTER(vp)]
+    L.wdad_cnn_destroy.argtypes = [vp]
+    L.wdad_cnn_set_norm.argtypes = [vp, vp]
+    L.wdad_cnn_params.argtypes = [vp, vp, ctypes.POINTER(i64)]
+    L.wdad_cnn_set_params.argtypes = [vp, vp, i64]
+    L.wdad_cnn_forward.argtypes = [vp, f32p, i32, i32, i32, f32p, vp]
+    L.wdad_cnn_grad.argtypes = [vp, f32p, f32p, i32, i32, i32, vp, vp, vp]
+    L.wdad_cnn_train.argtypes = [vp, f32p, f32p, i32, i32, i32, i32, i32, ctypes.c_float, ctypes.c_uint64, vp, vp]
+    L.wdad_cnn_save.argtypes = [vp, ctypes.c_char_p]
+    L.wdad_cnn_load.argtypes = [vp, ctypes.c_char_p, i64, ctypes.POINTER(vp)]
+    L.wdad_screen_run.argtypes = [vp, vp, f32p, i32, i32, i32, pp, ctypes.c_float, ctypes.c_float, ctypes.c_uint64,
+                                  i32, i32, f32p, vp, vp, ctypes.POINTER(i64), vp]
     L.wdad_detect_all_noalloc.argtypes = [f32p, i32, i32, i32, pp, f32p, vp, vp]
     L.wdad_auc.argtypes = [vp, vp, i64, ctypes.POINTER(ctypes.c_double)]
     for name in ("wdad_create", "wdad_destroy", "wdad_last_error_detail", "wdad_dwt_approx", "wdad_detect",
                  "wdad_detect_all", "wdad_detect_all_host", "wdad_window_census", "wdad_auc",
                  "wdad_detect_all_noalloc", "wdad_window_moments", "wdad_autotune", "wdad_batch_create",
-                 "wdad_batch_launch", "wdad_batch_status", "wdad_batch_destroy", "wdad_batch_run"):
+                 "wdad_batch_launch", "wdad_batch_status", "wdad_batch_destroy", "wdad_batch_run",
+                 "wdad_cnn_create", "wdad_cnn_destroy", "wdad_cnn_set_norm", "wdad_cnn_params",
+                 "wdad_cnn_set_params", "wdad_cnn_forward", "wdad_cnn_grad", "wdad_cnn_train", "wdad_cnn_save",
+                 "wdad_cnn_load", "wdad_screen_run"):
         getattr(L, name).restype = i32
     L.wdad_query_K.restype = i32
     _lib = L
@@ -314,6 +329,119 @@ def wdad_batch_run(jobs, device: int = 0):
     arr = _jobs(jobs)
     h = handle(device)
     _check(lib().wdad_batch_run(h, len(jobs), arr, ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)), h)
+
+
+class wdad_cnn:
+    """A9 screening network (K -> 32 -> 32 -> 32 -> 1, receptive field 15)."""
+
+    def __init__(self, K: int = 4, bf16_weights: bool = True, seed: int = 0, max_batch_pixels: int = 1 << 16,
+                 device: int = 0, _ptr=None):
+        self.device = device
+        self._h = handle(device)
+        if _ptr is None:
+            c = ctypes.c_void_p()
+            _check(lib().wdad_cnn_create(self._h, K, int(bool(bf16_weights)), seed, max_batch_pixels, ctypes.byref(c)),
+                   self._h)
+            self._c = c.value
+        else:
+            self._c = _ptr
+        self.K = K
+
+    @classmethod
+    def load(cls, path: str, max_batch_pixels: int = 1 << 16, device: int = 0):
+        h = handle(device)
+        c = ctypes.c_void_p()
+        _check(lib().wdad_cnn_load(h, path.encode(), max_batch_pixels, ctypes.byref(c)), h)
+        obj = cls.__new__(cls)
+        obj.device, obj._h, obj._c = device, h, c.value
+        obj.K = 0
+        return obj
+
+    def _stream(self):
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
+
+    def set_norm(self, mean_std):
+        a = np.ascontiguousarray(mean_std, dtype=np.float32)
+        _check(lib().wdad_cnn_set_norm(self._c, a.ctypes.data), self._h)
+
+    def params(self) -> np.ndarray:
+        n = ctypes.c_int64(0)
+        _check(lib().wdad_cnn_params(self._c, None, ctypes.byref(n)), self._h)
+        out = np.zeros(n.value, dtype=np.float32)
+        _check(lib().wdad_cnn_params(self._c, out.ctypes.data, ctypes.byref(n)), self._h)
+        return out
+
+    def set_params(self, p):
+        a = np.ascontiguousarray(p, dtype=np.float32)
+        _check(lib().wdad_cnn_set_params(self._c, a.ctypes.data, a.size), self._h)
+
+    def forward(self, x, out=None):
+        """x: CUDA [B, H, W, K] raw approximation values -> [B, H, W]."""
+        import torch
+        x = x.contiguous()
+        B, H, W, _ = x.shape
+        if out is None:
+            out = torch.empty((B, H, W), device=x.device, dtype=torch.float32)
+        _check(lib().wdad_cnn_forward(self._c, x.data_ptr(), B, H, W, out.data_ptr(), self._stream()), self._h)
+        return out
+
+    def grad(self, x, t):
+        """Interior-MSE loss and gradient (host) for normalised x [B, H, W, K], targets [B, H, W]."""
+        x = x.contiguous()
+        t = t.contiguous()
+        B, H, W, _ = x.shape
+        n = ctypes.c_int64(0)
+        lib().wdad_cnn_params(self._c, None, ctypes.byref(n))
+        g = np.zeros(n.value, dtype=np.float32)
+        loss = ctypes.c_float(0.0)
+        _check(lib().wdad_cnn_grad(self._c, x.data_ptr(), t.data_ptr(), B, H, W, g.ctypes.data, ctypes.byref(loss),
+                                   self._stream()), self._h)
+        return loss.value, g
+
+    def train(self, approx, score, steps: int, batch: int = 8, crop: int = 32, lr: float = 1e-3, seed: int = 0):
+        """`steps` Adam steps on random crops of one reduced cube approx [H, W, K] and its score map [H, W]."""
+        approx = approx.contiguous()
+        score = score.contiguous()
+        H, W, _ = approx.shape
+        loss = ctypes.c_float(0.0)
+        _check(lib().wdad_cnn_train(self._c, approx.data_ptr(), score.data_ptr(), H, W, steps, batch, crop, lr, seed,
+                                    ctypes.byref(loss), self._stream()), self._h)
+        return loss.value
+
+    def save(self, path: str):
+        _check(lib().wdad_cnn_save(self._c, path.encode()), self._h)
+
+    def close(self):
+        if getattr(self, "_c", None):
+            lib().wdad_cnn_destroy(self._c)
+            self._c = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def wdad_screen_run(net: "wdad_cnn", cube, top_frac: float = 0.02, audit_frac: float = 0.005, seed: int = 0,
+                    tile_rows: int = 256, exact_reduce: bool = False, params: wdad_params | None = None,
+                    want_pred: bool = True, **over):
+    """A9 screened LRX: (score [H, W] with -inf where not evaluated, pred, selected, n_selected)."""
+    import torch
+    cube = _cube(cube)
+    p = _params(params, over)
+    H, W, L = cube.shape
+    score = torch.empty((H, W), device=cube.device, dtype=torch.float32)
+    pred = torch.empty((H, W), device=cube.device, dtype=torch.float32) if want_pred else None
+    sel = torch.empty((H, W), device=cube.device, dtype=torch.uint8)
+    n = ctypes.c_int64(0)
+    h = handle(cube.device.index or 0)
+    _check(lib().wdad_screen_run(h, net._c, cube.data_ptr(), H, W, L, ctypes.byref(p), top_frac, audit_frac, seed,
+                                 tile_rows, int(bool(exact_reduce)), score.data_ptr(),
+                                 pred.data_ptr() if pred is not None else None, sel.data_ptr(), ctypes.byref(n),
+                                 _stream(cube)), h)
+    return score, pred, sel, n.value
 
 
 def wdad_window_census(H: int, W: int, params: wdad_params | None = None, device: int = 0, **over):

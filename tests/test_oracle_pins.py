@@ -333,3 +333,35 @@ def test_auc_against_sklearn_and_special_cases():
     assert abs(oracle.auc(s, m) - skm.roc_auc_score(m, s)) < 1e-12
     assert oracle.auc(np.array([0.1, 0.2, 0.9, 1.0]), np.array([0, 0, 1, 1])) == 1.0
     assert oracle.auc(np.ones(10), np.array([0, 1] * 5)) == 0.5
+
+
+# ---------------------------------------------------------------- screening CNN (addition, no paper counterpart)
+def test_cnn_gradient_matches_central_differences():
+    rng = np.random.default_rng(31)
+    K = 4
+    n = oracle.cnn_nparam(K)
+    assert n == 4 * 25 * 32 + 32 + 2 * (32 * 25 * 32 + 32) + 32 * 9 + 1
+    params = rng.standard_normal(n) * 0.05
+    x = rng.standard_normal((1, 16, 17, K))
+    t = rng.standard_normal((1, 16, 17))
+    loss, g = oracle.cnn_grad(params, x, t)
+    idx = rng.choice(n, 40, replace=False)
+    idx = np.concatenate([idx, [n - 1, 0, 3232 - 1]])  # last bias, first weight, first layer's last bias
+    h = 1e-5
+    for i in idx:
+        pp = params.copy(); pp[i] += h
+        lp, _ = oracle.cnn_grad(pp, x, t)
+        pp[i] -= 2 * h
+        lm, _ = oracle.cnn_grad(pp, x, t)
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(abs(fd), 1e-3 * np.abs(g).max()), (i, fd, g[i])
+
+
+def test_cnn_forward_is_linear_in_the_last_layer_and_zero_padding():
+    # with every hidden weight zero, the output equals the last bias everywhere
+    K = 4
+    n = oracle.cnn_nparam(K)
+    params = np.zeros(n)
+    params[-1] = 0.75
+    x = np.random.default_rng(32).standard_normal((2, 15, 15, K))
+    np.testing.assert_allclose(oracle.cnn_forward(params, x), 0.75, atol=0)
