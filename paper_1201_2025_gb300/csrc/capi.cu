@@ -888,7 +888,17 @@ wdad_status wdad_screen_run(wdad_handle h, wdad_cnn c, const float* cube, int H,
         const size_t b_list = align256(sizeof(int64_t) * (size_t)P);
         const size_t b_hist = align256(sizeof(unsigned int) * 65536 + 64);
         const size_t fixed = b_ap + b_pred + b_act + b_list + b_hist;
-        st = ensure_ws(h, fixed);
+        // the exact detector's slabs are sized now (at most one per SM) so that the workspace
+        // never moves while it holds the selection
+        size_t need_full = 0;
+        if (!exact_reduce) {
+            wdad::FullArgs probe{};
+            probe.H = H; probe.W = W; probe.D = L; probe.inner = p->inner; probe.outer = p->outer;
+            probe.precision = p->precision;
+            need_full = wdad::fullband_workspace_bytes(probe, h->num_sms);
+            if (need_full == 0) return fail(h, WDAD_ERR_UNSUPPORTED, "screen: full-band LRX for %d bands", L);
+        }
+        st = ensure_ws(h, fixed + need_full);
         if (st != WDAD_OK) return st;
         char* base = (char*)h->ws;
         float* approx = (float*)base;
@@ -957,12 +967,6 @@ wdad_status wdad_screen_run(wdad_handle h, wdad_cnn c, const float* cube, int H,
             if (e == cudaSuccess) e = wdad::cnn::scatter_list(pred, list, (int64_t)nsel, score, s);
             return e == cudaSuccess ? WDAD_OK : cuda_fail(h, e, "screen exact reduced detector");
         }
-        const size_t need = wdad::fullband_workspace_bytes(a, h->num_sms);
-        if (need == 0) return fail(h, WDAD_ERR_UNSUPPORTED, "screen: full-band LRX for %d bands", L);
-        st = ensure_ws(h, fixed + need);  // may move the workspace: recompute pointers
-        if (st != WDAD_OK) return st;
-        base = (char*)h->ws;
-        a.pix = (const int64_t*)(base + b_ap + b_pred + b_act);
         e = wdad::launch_detect_full(a, base + fixed, h->ws_bytes - fixed, h->num_sms, s);
         return e == cudaSuccess ? WDAD_OK : cuda_fail(h, e, "screen exact detector");
     } catch (...) {
