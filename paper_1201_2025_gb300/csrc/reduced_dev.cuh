@@ -183,8 +183,7 @@ __device__ __forceinline__ void horizontal_sums_part(const TileGeom& g, ChanFn c
         chan(r, j - 1, c2);       // leaving column
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
-            so[q] += ch[Q0 + q];
-            so[q] -= c2[Q0 + q];
+            so[q] += ch[Q0 + q] - c2[Q0 + q];  // one rounding at the running-sum magnitude
             po[q * plane_o + jj] = so[q];
         }
         if (inner_row) {
@@ -192,8 +191,7 @@ __device__ __forceinline__ void horizontal_sums_part(const TileGeom& g, ChanFn c
             chan(r, j - 1 + i0, c2);
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
-                si[q] += ch[Q0 + q];
-                si[q] -= c2[Q0 + q];
+                si[q] += ch[Q0 + q] - c2[Q0 + q];
                 pi[q * plane_i + jj] = si[q];
             }
         }
@@ -242,10 +240,8 @@ __device__ __forceinline__ void vertical_sums_inplace(const TileGeom& g, typenam
             const T li = hi[(i - 1) * HP], ei = hi[(i + wi - 1) * HP];
             ho[(i - 1) * HP] = so;
             hi[(i - 1) * HP] = si;
-            so += eo;
-            so -= lo;
-            si += ei;
-            si -= li;
+            so += eo - lo;  // one rounding at the running-sum magnitude
+            si += ei - li;
         }
         ho[(g.th - 1) * HP] = so;
         hi[(g.th - 1) * HP] = si;
