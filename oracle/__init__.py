@@ -60,6 +60,7 @@ def lib():
         L.or_window_moments.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         i64p, ctypes.c_int64, dp, dp, ctypes.c_int]
         L.or_auc.argtypes = [dp, u8p, ctypes.c_int64]
+        L.or_scene_whiten.argtypes = [ctypes.c_int, dp, ctypes.c_long, dp, dp]
         L.or_cnn_nparam.argtypes = [ctypes.c_int]
         L.or_cnn_nparam.restype = ctypes.c_long
         L.or_cnn_forward.argtypes = [ctypes.c_int, dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp]
@@ -182,6 +183,18 @@ def window_census(H: int, W: int, inner: int, outer: int, border: int = 0, pixel
                               _ptr(out, ctypes.c_int64)) != 0:
         raise ValueError("bad window")
     return out
+
+
+def scene_whiten(x: np.ndarray):
+    """Whitening of the network input: x [..., K] -> (mu [K], M [K][K]) with z = M (x - mu)."""
+    xx = np.ascontiguousarray(x, dtype=np.float64)
+    K = xx.shape[-1]
+    P = xx.size // K
+    mu = np.zeros(K)
+    M = np.zeros((K, K))
+    if lib().or_scene_whiten(K, _ptr(xx, ctypes.c_double), P, _ptr(mu, ctypes.c_double), _ptr(M, ctypes.c_double)):
+        raise ValueError("scene_whiten: K in 1..8 and at least one pixel")
+    return mu, M
 
 
 def cnn_nparam(K: int = 4) -> int:

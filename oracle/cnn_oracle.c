@@ -3,8 +3,10 @@
  *   K -> 32 (5x5, ReLU) -> 32 (5x5, ReLU) -> 32 (5x5, ReLU) -> 1 (3x3), "same" zero padding,
  * with the mean squared error over the interior of each image (a border of `edge` pixels
  * excluded).  Parameters per layer: weights [ci][ky*k+kx][co], then biases [co].
- * Activations [B][H][W][C].  TEST INFRASTRUCTURE ONLY; plain loops, no shared code with the
- * CUDA path.  The network is an addition to the paper's method (no counterpart in it).
+ * Activations [B][H][W][C].  The network's input is the approximation matrix whitened with
+ * the scene's own statistics (or_scene_whiten).  TEST INFRASTRUCTURE ONLY; plain loops, no
+ * shared code with the CUDA path.  The network is an addition to the paper's method (no
+ * counterpart in it).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -156,5 +158,52 @@ int or_cnn_grad(int K, const double* params, const double* x, const double* t, i
     }
     for (int l = 0; l < 4; ++l) free(act[l]);
     free(dz); free(dnext);
+    return 0;
+}
+
+/*
+ * Scene whitening of the network's input: mean mu and population covariance
+ * C = (1/P) sum_p (x_p - mu)(x_p - mu)^T of P pixels with K values each, the Cholesky factor
+ * C = L L^T, and M = L^{-1} (lower triangular, positive diagonal), so that z = M (x - mu) has
+ * zero mean and identity covariance.  A pivot that is not above 1e-12 * trace(C) / K is
+ * replaced by that floor (by 1 when trace(C) == 0), so constant bands give a finite M.
+ * Two passes (mean, then centred products); M by forward substitution on the unit vectors.
+ */
+int or_scene_whiten(int K, const double* x, long P, double* mu, double* M) {
+    if (K < 1 || K > 8 || P < 1) return -1;
+    double C[64], Lf[64];
+    for (int i = 0; i < K; ++i) {
+        double s = 0.0;
+        for (long p = 0; p < P; ++p) s += x[p * K + i];
+        mu[i] = s / (double)P;
+    }
+    double tr = 0.0;
+    for (int i = 0; i < K; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double s = 0.0;
+            for (long p = 0; p < P; ++p) s += (x[p * K + i] - mu[i]) * (x[p * K + j] - mu[j]);
+            C[i * K + j] = C[j * K + i] = s / (double)P;
+            if (i == j) tr += C[i * K + i];
+        }
+    const double floor = tr > 0.0 ? 1e-12 * tr / (double)K : 1.0;
+    memset(Lf, 0, sizeof Lf);
+    for (int j = 0; j < K; ++j) {
+        double d = C[j * K + j];
+        for (int k = 0; k < j; ++k) d -= Lf[j * K + k] * Lf[j * K + k];
+        if (!(d > floor)) d = floor;
+        Lf[j * K + j] = sqrt(d);
+        for (int i = j + 1; i < K; ++i) {
+            double v = C[i * K + j];
+            for (int k = 0; k < j; ++k) v -= Lf[i * K + k] * Lf[j * K + k];
+            Lf[i * K + j] = v / Lf[j * K + j];
+        }
+    }
+    /* column c of M solves L m = e_c */
+    for (int c = 0; c < K; ++c)
+        for (int i = 0; i < K; ++i) {
+            double v = (i == c) ? 1.0 : 0.0;
+            for (int k = 0; k < i; ++k) v -= Lf[i * K + k] * M[k * K + c];
+            M[i * K + c] = v / Lf[i * K + i];
+        }
     return 0;
 }

@@ -365,3 +365,36 @@ def test_cnn_forward_is_linear_in_the_last_layer_and_zero_padding():
     params[-1] = 0.75
     x = np.random.default_rng(32).standard_normal((2, 15, 15, K))
     np.testing.assert_allclose(oracle.cnn_forward(params, x), 0.75, atol=0)
+
+
+def test_scene_whitening_is_the_unique_lower_triangular_whitener():
+    # M C M^T = I with M lower triangular and a positive diagonal fixes M uniquely; the
+    # whitened data has zero mean and identity (population) covariance
+    rng = np.random.default_rng(33)
+    for K in (1, 3, 4, 8):
+        A = np.eye(K) + 0.5 * rng.standard_normal((K, K))
+        x = 0.3 + rng.standard_normal((500, K)) @ A.T * 0.02
+        mu, M = oracle.scene_whiten(x)
+        C = np.cov(x.T, bias=True).reshape(K, K)
+        np.testing.assert_allclose(mu, x.mean(0), rtol=1e-13)
+        np.testing.assert_allclose(M @ C @ M.T, np.eye(K), atol=1e-9)
+        assert np.all(np.triu(M, 1) == 0) and np.all(np.diag(M) > 0)
+        z = (x - mu) @ M.T
+        np.testing.assert_allclose(z.mean(0), 0, atol=1e-10)
+        np.testing.assert_allclose(z.T @ z / len(z), np.eye(K), atol=1e-9)
+    # K = 1: M = 1 / population standard deviation
+    x = rng.standard_normal((77, 1))
+    _, M = oracle.scene_whiten(x)
+    assert abs(M[0, 0] - 1.0 / x.std()) <= 1e-12 / x.std()
+
+
+def test_scene_whitening_degenerate_inputs_stay_finite():
+    mu, M = oracle.scene_whiten(np.full((10, 4), 0.25))  # constant: trace 0 -> identity
+    np.testing.assert_array_equal(M, np.eye(4))
+    np.testing.assert_allclose(mu, 0.25)
+    x = np.random.default_rng(34).standard_normal((50, 3))
+    x[:, 1] = 2.0  # one constant band: its pivot is floored
+    _, M = oracle.scene_whiten(x)
+    assert np.isfinite(M).all()
+    mu, M = oracle.scene_whiten(np.array([[1.0, 2.0]]))  # one pixel
+    np.testing.assert_array_equal(M, np.eye(2))
