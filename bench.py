@@ -161,6 +161,132 @@ def run_reference(args):
     }), flush=True)
 
 
+def _timer(stream):
+    import torch
+
+    def _time(fn, n=10, warm=2):
+        for _ in range(warm):
+            fn()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(n):
+            fn()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        return a0.elapsed_time(a1) / n
+    return _time
+
+
+def bench_batching(dev, stream, peak):
+    """64 cubes of uneven size (side U{128..1024}), band count (128/188/224), window and
+    detector in one persistent graph-captured launch, against the same jobs run one after
+    another through the single-cube entry points (DWT + detector each)."""
+    import torch
+    from paper_1201_2025_gb300 import synth, wdad
+    _time = _timer(stream)
+    specs = synth.batch_specs(64, seed=0)
+    jobs, nbytes, npx = [], 0, 0
+    for sp in specs:
+        Hh, Ww, Ll = sp["H"], sp["W"], sp["L"]
+        cube, _ = synth.make_scene_device(Hh, Ww, Ll, seed=sp["seed"], n_anom=max(1, Hh * Ww // 1300),
+                                          anom_side=(1, 3), abundance=(0.1, 0.5), margin=10, device=dev)
+        K = wdad.wdad_query_K(Ll)
+        jobs.append(dict(cube=cube, detector=sp["detector"], scores=torch.empty((Hh, Ww), device=dev),
+                         over=dict(inner=sp["inner"], outer=sp["outer"])))
+        npx += Hh * Ww
+        nbytes += Hh * Ww * (4 * Ll + 4 * K + 4 * K + 4)  # DWT read + write, detector read + score write
+    torch.cuda.synchronize()
+    res = {"jobs": len(jobs), "pixels": npx, "cube_GB": sum(j["cube"].numel() * 4 for j in jobs) / 1e9,
+           "workload": "64 cubes, side U{128..1024}, L in {128,188,224}, windows (3,9)/(5,15)/(7,21), "
+                       "one detector each (LRX/DWRX/DWEST), f32, device-generated (same recipe)"}
+    for name, tuned in (("default_plans", False), ("autotuned", True)):
+        b = wdad.wdad_batch(jobs, autotune=tuned, use_graph=True)
+        ms = _time(b.launch, n=5)
+        st, ths = b.status()
+        res[name] = {"graph_ms": ms, "Mpixel_s": npx / (ms * 1e-3) / 1e6, "status": st,
+                     "algorithmic_GBps": nbytes / (ms * 1e-3) / 1e9, "frac_of_hbm": nbytes / (ms * 1e-3) / 1e9 / peak,
+                     "tile_heights": {str(t): ths.count(t) for t in sorted(set(ths))}}
+        b.close()
+
+    def seq():
+        for j in jobs:
+            wdad.wdad_detect(j["cube"], j["detector"], reduce=True, out=j["scores"], **j["over"])
+    ms = _time(seq, n=2)
+    res["sequential"] = {"ms": ms, "Mpixel_s": npx / (ms * 1e-3) / 1e6,
+                         "algorithmic_GBps": nbytes / (ms * 1e-3) / 1e9}
+    res["speedup_graph_vs_sequential"] = ms / res["default_plans"]["graph_ms"]
+    del jobs
+    torch.cuda.empty_cache()
+    return res
+
+
+def bench_screening(dev, stream, n_train: int, train_steps: int):
+    """Learned screening on a 2048x2048x224 cube in 256-row tiles: a CNN trained on DWT-LRX
+    (5,15) scores of n_train seeded 256x256 cubes; exact LRX on the top 2% + 0.5% audit;
+    recall of implanted anomalies against the exact full-map LRX (full band and DWT)."""
+    import torch
+    from paper_1201_2025_gb300 import synth, wdad
+    _time = _timer(stream)
+    t0 = time.perf_counter()
+    data = []
+    for s in range(n_train):
+        c, _ = synth.make_scene_device(256, 256, L, seed=10000 + s, n_anom=50, anom_side=(1, 3),
+                                       abundance=(0.1, 0.5), margin=4, device=dev)
+        ap = wdad.wdad_dwt_approx(c)
+        data.append((ap, wdad.wdad_detect(ap, 0, reduce=False, inner=5, outer=15)))
+        del c
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    net = wdad.wdad_cnn(K=4, bf16_weights=True, seed=11, max_batch_pixels=8 * 32 * 32)
+    per_call = 5
+    calls = max(1, train_steps // per_call)
+    t0 = time.perf_counter()
+    for it in range(calls):
+        ap, lrx = data[it % len(data)]
+        net.train(ap, lrx, steps=per_call, batch=8, crop=32, lr=2e-3 if it < 0.7 * calls else 1e-3, seed=100 + it)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    del data
+    HS = 2048
+    cube, mask = synth.make_scene_device(HS, HS, L, seed=4242, n_anom=3200, anom_side=(1, 3), abundance=(0.1, 0.5),
+                                         margin=10, device=dev)
+    P = HS * HS
+    out = {"workload": f"{HS}x{HS}x{L} f32 cube, 3200 targets (1-3 px, f 0.1-0.5), 256-row tiles, window (5,15), "
+                       f"top 2% + 0.5% audit; CNN trained on {n_train} seeded 256x256 cubes, {calls * per_call} Adam "
+                       f"steps (batch 8, 32x32 crops)",
+           "train_data_s": gen_s, "train_s": train_s, "train_steps_per_s": calls * per_call / train_s}
+    full = torch.empty((HS, HS), device=dev)
+    ms_full = _time(lambda: wdad.wdad_detect(cube, 0, reduce=False, inner=5, outer=15, out=full), n=1, warm=0)
+    red = torch.empty((HS, HS), device=dev)
+    ms_red = _time(lambda: wdad.wdad_detect(cube, 0, reduce=True, inner=5, outer=15, out=red), n=5)
+    full_h, red_h = full.cpu().numpy(), red.cpu().numpy()
+    for name, exact_reduce, ref, ms_ref in (("fullband_lrx", False, full_h, ms_full), ("dwt_lrx", True, red_h, ms_red)):
+        box = {}
+
+        def run():
+            box["r"] = wdad.wdad_screen_run(net, cube, top_frac=0.02, audit_frac=0.005, seed=1, tile_rows=256,
+                                            exact_reduce=exact_reduce, inner=5, outer=15, want_pred=False)
+        ms = _time(run, n=3, warm=1)
+        score, _, sel, nsel = box["r"]
+        s = score.cpu().numpy()
+        selm = sel.cpu().numpy() > 0
+        truth = (mask > 0) & (ref >= np.quantile(ref, 0.98))
+        out[name] = {
+            "screened_ms": ms, "exact_map_ms": ms_ref, "speedup": ms_ref / ms,
+            "screened_Mpixel_s": P / (ms * 1e-3) / 1e6, "exact_Mpixel_s": P / (ms_ref * 1e-3) / 1e6,
+            "fraction_evaluated": nsel / P, "implanted_in_exact_top2pct": int(truth.sum()),
+            "recall": float((selm & truth).sum() / max(1, truth.sum())),
+            "auc_exact": wdad.wdad_auc(ref, mask), "auc_screened": wdad.wdad_auc(s, mask),
+            "exact_values_identical": bool(np.array_equal(s[selm], ref[selm])),
+        }
+        out[name]["dauc"] = out[name]["auc_screened"] - out[name]["auc_exact"]
+    net.close()
+    del cube, full, red
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import torch
     ws, rank, local = _dist()
@@ -310,11 +436,14 @@ def run_ours(args):
                 ent[f"{dn}_median_rel_err_vs_fp64"] = float(np.median(rel))
             mixed[name] = ent
         mixed["workload"] = "64x64x224 AR(1) rho=0.98 scene, 10 targets, windows 3/11, loading 1e-3"
+    batching = bench_batching(dev, stream, peak) if not args.no_batch else None
+    screening = bench_screening(dev, stream, args.screen_train_cubes, args.screen_train_steps) \
+        if not args.no_screen else None
     step_bytes = H * W * (BYTES_DWT_PER_PX + 3 * 3 * 4)
     breakdown = {"dwt_ms": dwt_ms, "detect_ms": dict(zip([f"{a}/{b}" for a, b in WINDOWS], det_ms)),
                  "step_algorithmic_GBps": step_bytes / (ms_step * 1e-3) / 1e9,
                  "step_frac_of_hbm": step_bytes / (ms_step * 1e-3) / 1e9 / peak, "per_detector": per_det,
-                 "fullband_fp32": full, "mixed_precision": mixed}
+                 "fullband_fp32": full, "mixed_precision": mixed, "batching": batching, "screening": screening}
 
     # end to end through the host-buffer entry point: H2D cube, DWT, 3 windows, D2H 9 maps
     hc = torch.from_numpy(sc.cube).pin_memory()
@@ -378,6 +507,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-full", action="store_true")
     ap.add_argument("--full-rows", type=int, default=16)
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-screen", action="store_true")
+    ap.add_argument("--screen-train-cubes", type=int, default=200)
+    ap.add_argument("--screen-train-steps", type=int, default=2000)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -207,16 +207,29 @@ typedef struct wdad_cnn_ctx* wdad_cnn;
 wdad_status wdad_cnn_create(wdad_handle h, int K, int bf16_weights, uint64_t seed, int64_t max_batch_pixels,
                             wdad_cnn* out);
 wdad_status wdad_cnn_destroy(wdad_cnn c);
-/* Input normalisation (host [2K]: per-channel mean then std) applied to raw approximation input. */
-wdad_status wdad_cnn_set_norm(wdad_cnn c, const float* host_mean_std);
+/* The network's input map z = M (x - mu) applied to raw approximation values x (first layer
+ * and training crops).  host_mu_M == NULL (the default of a new network) whitens every scene
+ * with its own statistics: each wdad_cnn_forward / wdad_cnn_train / wdad_screen_run call first
+ * runs wdad_scene_whitening on its input.  Otherwise host_mu_M = [mu (K), M (K x K,
+ * row-major)] is a fixed map used for every call (finite values, else WDAD_ERR_ARG).  The map
+ * is stored with the network (checkpoints included); a network serves one stream at a time. */
+wdad_status wdad_cnn_set_norm(wdad_cnn c, const float* host_mu_M);
+/* Scene whitening of the network's input: for x [P][K] (device, K in 1..8, P >= 1) writes
+ * norm_out (device, K + K*K floats) = [mu, M] with mu the mean, C = (1/P) sum (x - mu)(x - mu)^T
+ * = L L^T (Cholesky; a pivot not above 1e-12 trace(C)/K is replaced by that floor, by 1 when
+ * the trace is 0) and M = L^{-1}.  FP64 sums in a fixed order (deterministic on any GPU);
+ * uses the handle's workspace; asynchronous on `stream`.  No paper counterpart (input
+ * conditioning of the screening network). */
+wdad_status wdad_scene_whitening(wdad_handle h, const float* x, int64_t P, int K, float* norm_out, void* stream);
 /* Parameter count (and, when host != NULL, a host copy of the FP32 masters, per layer
  * weights [ci][ky*k+kx][co] then biases). */
 wdad_status wdad_cnn_params(wdad_cnn c, float* host, int64_t* count);
 /* Replace the masters (resets the Adam state). */
 wdad_status wdad_cnn_set_params(wdad_cnn c, const float* host, int64_t count);
-/* pred [B][H][W] from raw x [B][H][W][K] (device); normalisation applied inside. */
+/* pred [B][H][W] from raw x [B][H][W][K] (device); the input map is applied inside (per-scene
+ * mode: whitened with the statistics of all B * H * W input pixels). */
 wdad_status wdad_cnn_forward(wdad_cnn c, const float* x, int B, int H, int W, float* pred, void* stream);
-/* Gradients of the interior MSE (7-pixel border excluded) for normalised x [B][H][W][K] and
+/* Gradients of the interior MSE (7-pixel border excluded) for mapped input z [B][H][W][K] and
  * targets [B][H][W] (device); host_grad [count] and host_loss (both nullable); synchronises. */
 wdad_status wdad_cnn_grad(wdad_cnn c, const float* x, const float* target, int B, int H, int W, float* host_grad,
                           float* host_loss, void* stream);
@@ -225,7 +238,8 @@ wdad_status wdad_cnn_grad(wdad_cnn c, const float* x, const float* target, int B
  * log(1 + score[H][W]); host_loss (nullable) receives the last batch loss. */
 wdad_status wdad_cnn_train(wdad_cnn c, const float* approx, const float* score, int H, int W, int steps, int batch,
                            int crop, float lr, uint64_t seed, float* host_loss, void* stream);
-/* Versioned checkpoint: masters, Adam moments, step, normalisation. */
+/* Versioned checkpoint (version 2): masters, Adam moments, step, input-map mode and map.
+ * Loading a file of another version fails with WDAD_ERR_ARG. */
 wdad_status wdad_cnn_save(wdad_cnn c, const char* path);
 wdad_status wdad_cnn_load(wdad_handle h, const char* path, int64_t max_batch_pixels, wdad_cnn* out);
 /* Screened LRX: A1 on the cube, the CNN on row tiles (tile_rows + 7-row halo), the top

@@ -284,13 +284,13 @@ void cnn_free(wdad_cnn_ctx* c) {
     if (!c) return;
     auto& n = c->net;
     cudaFree(n.w); cudaFree(n.wf); cudaFree(n.m); cudaFree(n.v); cudaFree(n.grad); cudaFree(n.wt);
-    cudaFree(n.norm); cudaFree(n.act); cudaFree(n.loss); cudaFree(n.cx); cudaFree(n.ct);
+    cudaFree(n.norm); cudaFree(n.stat); cudaFree(n.act); cudaFree(n.loss); cudaFree(n.cx); cudaFree(n.ct);
     delete c;
 }
 
-// magic, version, K, bf16, step, nparam, then w, m, v (float32), norm (2K float32)
+// magic, version, K, bf16, step, norm_mode, nparam (u64), then w, m, v (float32), norm (K + K*K float32)
 constexpr uint32_t kCnnMagic = 0x4E4E4357u;  // "WCNN"
-constexpr uint32_t kCnnVersion = 1;
+constexpr uint32_t kCnnVersion = 2;
 
 void batch_free(wdad_batch_ctx* b) {
     if (!b) return;
@@ -694,15 +694,18 @@ wdad_status wdad_cnn_create(wdad_handle h, int K, int bf16_weights, uint64_t see
         for (float** pp : {&n.w, &n.wf, &n.m, &n.v, &n.grad})
             if (e == cudaSuccess) e = cudaMalloc(pp, sizeof(float) * n.nparam);
         if (e == cudaSuccess) e = cudaMalloc(&n.wt, sizeof(float) * 32 * 32 * 25);
-        if (e == cudaSuccess) e = cudaMalloc(&n.norm, sizeof(float) * 2 * K);
+        if (e == cudaSuccess) e = cudaMalloc(&n.norm, sizeof(float) * (size_t)(K + K * K));
+        if (e == cudaSuccess)
+            e = cudaMalloc(&n.stat, sizeof(double) * wdad::cnn::WHITEN_BLOCKS * wdad::cnn::WHITEN_NQ_MAX);
         if (e == cudaSuccess) e = cudaMalloc(&n.act, sizeof(float) * wdad::cnn::act_floats(max_batch_pixels));
         if (e == cudaSuccess) e = cudaMalloc(&n.loss, sizeof(float));
         if (e == cudaSuccess) e = cudaMalloc(&n.cx, sizeof(float) * (size_t)max_batch_pixels * K);
         if (e == cudaSuccess) e = cudaMalloc(&n.ct, sizeof(float) * (size_t)max_batch_pixels);
         if (e != cudaSuccess) { cnn_free(c); return cuda_fail(h, e, "cnn allocation"); }
-        std::vector<float> norm(2 * K);
-        for (int k = 0; k < K; ++k) { norm[k] = 0.f; norm[K + k] = 1.f; }
-        e = cudaMemcpy(n.norm, norm.data(), sizeof(float) * 2 * K, cudaMemcpyHostToDevice);
+        std::vector<float> norm((size_t)(K + K * K), 0.f);  // mu = 0, M = I until a scene sets it
+        for (int k = 0; k < K; ++k) norm[K + k * K + k] = 1.f;
+        n.norm_mode = 0;
+        e = cudaMemcpy(n.norm, norm.data(), sizeof(float) * norm.size(), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = wdad::cnn::net_init(n, seed, 0);
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
         if (e != cudaSuccess) { cnn_free(c); return cuda_fail(h, e, "cnn init"); }
@@ -722,13 +725,33 @@ wdad_status wdad_cnn_destroy(wdad_cnn c) {
     return WDAD_OK;
 }
 
-wdad_status wdad_cnn_set_norm(wdad_cnn c, const float* host_mean_std) {
-    if (!c || !host_mean_std) return WDAD_ERR_ARG;
+wdad_status wdad_cnn_set_norm(wdad_cnn c, const float* host_mu_M) {
+    if (!c) return WDAD_ERR_ARG;
+    auto& n = c->net;
+    if (!host_mu_M) { n.norm_mode = 0; return WDAD_OK; }
+    const int K = n.K;
+    for (int i = 0; i < K + K * K; ++i)
+        if (!std::isfinite(host_mu_M[i])) return fail(c->h, WDAD_ERR_ARG, "cnn: input map must be finite");
     DeviceGuard g(c->h->device);
-    for (int k = 0; k < c->net.K; ++k)
-        if (!(host_mean_std[c->net.K + k] > 0.f)) return fail(c->h, WDAD_ERR_ARG, "cnn: std must be > 0");
-    cudaError_t e = cudaMemcpy(c->net.norm, host_mean_std, sizeof(float) * 2 * c->net.K, cudaMemcpyHostToDevice);
-    return e == cudaSuccess ? WDAD_OK : cuda_fail(c->h, e, "cnn norm");
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(n.norm, host_mu_M, sizeof(float) * (size_t)(K + K * K), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(c->h, e, "cnn norm");
+    n.norm_mode = 1;
+    return WDAD_OK;
+}
+
+wdad_status wdad_scene_whitening(wdad_handle h, const float* x, int64_t P, int K, float* norm_out, void* stream) {
+    if (!h) return WDAD_ERR_ARG;
+    if (!x || !norm_out || P < 1 || K < 1 || K > 8) return fail(h, WDAD_ERR_ARG, "whitening: P >= 1, K in 1..8");
+    try {
+        DeviceGuard g(h->device);
+        wdad_status st = ensure_ws(h, sizeof(double) * wdad::cnn::WHITEN_BLOCKS * wdad::cnn::WHITEN_NQ_MAX);
+        if (st != WDAD_OK) return st;
+        cudaError_t e = wdad::cnn::scene_whitening(x, P, K, (double*)h->ws, norm_out, (cudaStream_t)stream);
+        return e == cudaSuccess ? WDAD_OK : cuda_fail(h, e, "scene whitening");
+    } catch (...) {
+        return fail(h, WDAD_ERR_NOMEM, "host exception");
+    }
 }
 
 wdad_status wdad_cnn_params(wdad_cnn c, float* host, int64_t* count) {
@@ -762,8 +785,11 @@ wdad_status wdad_cnn_forward(wdad_cnn c, const float* x, int B, int H, int W, fl
     wdad_status st = ensure_ws(h, sizeof(float) * (size_t)px * 96 + 256);
     if (st != WDAD_OK) return st;
     float* a0 = (float*)h->ws;
-    cudaError_t e = wdad::cnn::net_forward(c->net, x, B, H, W, c->net.norm, a0, a0 + px * 32, a0 + px * 64, pred,
-                                           (cudaStream_t)stream);
+    cudaError_t e = cudaSuccess;
+    if (c->net.norm_mode == 0) e = wdad::cnn::scene_whitening(x, px, c->net.K, c->net.stat, c->net.norm, (cudaStream_t)stream);
+    if (e == cudaSuccess)
+        e = wdad::cnn::net_forward(c->net, x, B, H, W, c->net.norm, a0, a0 + px * 32, a0 + px * 64, pred,
+                                   (cudaStream_t)stream);
     return e == cudaSuccess ? WDAD_OK : cuda_fail(h, e, "cnn forward");
 }
 
@@ -790,6 +816,7 @@ wdad_status wdad_cnn_train(wdad_cnn c, const float* approx, const float* score, 
     DeviceGuard g(c->h->device);
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaSuccess;
+    if (n.norm_mode == 0) e = wdad::cnn::scene_whitening(approx, (int64_t)H * W, n.K, n.stat, n.norm, s);
     for (int it = 0; it < steps && e == cudaSuccess; ++it) {
         e = wdad::cnn::sample_crops(n, approx, score, H, W, batch, crop, crop, seed, (uint64_t)n.step, n.cx, n.ct, s);
         if (e == cudaSuccess) e = wdad::cnn::net_grad(n, n.cx, n.ct, batch, crop, crop, s);
@@ -806,16 +833,17 @@ wdad_status wdad_cnn_save(wdad_cnn c, const char* path) {
     if (!c || !path) return WDAD_ERR_ARG;
     DeviceGuard g(c->h->device);
     auto& n = c->net;
-    std::vector<float> w(n.nparam), m(n.nparam), v(n.nparam), norm(2 * n.K);
+    std::vector<float> w(n.nparam), m(n.nparam), v(n.nparam), norm((size_t)(n.K + n.K * n.K));
     cudaError_t e = cudaDeviceSynchronize();
     if (e == cudaSuccess) e = cudaMemcpy(w.data(), n.w, sizeof(float) * n.nparam, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemcpy(m.data(), n.m, sizeof(float) * n.nparam, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemcpy(v.data(), n.v, sizeof(float) * n.nparam, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemcpy(norm.data(), n.norm, sizeof(float) * 2 * n.K, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(norm.data(), n.norm, sizeof(float) * norm.size(), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(c->h, e, "cnn save");
     FILE* f = std::fopen(path, "wb");
     if (!f) return fail(c->h, WDAD_ERR_ARG, "cannot open %s", path);
-    const uint32_t hdr[5] = {kCnnMagic, kCnnVersion, (uint32_t)n.K, (uint32_t)n.bf16, (uint32_t)n.step};
+    const uint32_t hdr[6] = {kCnnMagic, kCnnVersion, (uint32_t)n.K, (uint32_t)n.bf16, (uint32_t)n.step,
+                             (uint32_t)n.norm_mode};
     const uint64_t np = n.nparam;
     bool ok = std::fwrite(hdr, sizeof hdr, 1, f) == 1 && std::fwrite(&np, sizeof np, 1, f) == 1 &&
               std::fwrite(w.data(), sizeof(float), np, f) == np && std::fwrite(m.data(), sizeof(float), np, f) == np &&
@@ -829,10 +857,10 @@ wdad_status wdad_cnn_load(wdad_handle h, const char* path, int64_t max_batch_pix
     if (!h || !path || !out) return WDAD_ERR_ARG;
     FILE* f = std::fopen(path, "rb");
     if (!f) return fail(h, WDAD_ERR_ARG, "cannot open %s", path);
-    uint32_t hdr[5];
+    uint32_t hdr[6];
     uint64_t np = 0;
     if (std::fread(hdr, sizeof hdr, 1, f) != 1 || std::fread(&np, sizeof np, 1, f) != 1 || hdr[0] != kCnnMagic ||
-        hdr[1] != kCnnVersion || hdr[2] < 1 || hdr[2] > 8) {
+        hdr[1] != kCnnVersion || hdr[2] < 1 || hdr[2] > 8 || hdr[5] > 1) {
         std::fclose(f);
         return fail(h, WDAD_ERR_ARG, "%s is not a version-%u CNN checkpoint", path, kCnnVersion);
     }
@@ -841,7 +869,7 @@ wdad_status wdad_cnn_load(wdad_handle h, const char* path, int64_t max_batch_pix
     if (st != WDAD_OK) { std::fclose(f); return st; }
     auto& n = c->net;
     if (np != n.nparam) { std::fclose(f); wdad_cnn_destroy(c); return fail(h, WDAD_ERR_ARG, "checkpoint size mismatch"); }
-    std::vector<float> w(np), m(np), v(np), norm(2 * n.K);
+    std::vector<float> w(np), m(np), v(np), norm((size_t)(n.K + n.K * n.K));
     const bool ok = std::fread(w.data(), sizeof(float), np, f) == np && std::fread(m.data(), sizeof(float), np, f) == np &&
                     std::fread(v.data(), sizeof(float), np, f) == np &&
                     std::fread(norm.data(), sizeof(float), norm.size(), f) == norm.size();
@@ -853,6 +881,7 @@ wdad_status wdad_cnn_load(wdad_handle h, const char* path, int64_t max_batch_pix
     if (e == cudaSuccess) e = cudaMemcpy(n.v, v.data(), sizeof(float) * np, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(n.norm, norm.data(), sizeof(float) * norm.size(), cudaMemcpyHostToDevice);
     n.step = (int)hdr[4];
+    n.norm_mode = (int)hdr[5];
     if (e == cudaSuccess) e = wdad::cnn::net_refresh_forward_copy(n, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) { wdad_cnn_destroy(c); return cuda_fail(h, e, "cnn load"); }
@@ -914,6 +943,8 @@ wdad_status wdad_screen_run(wdad_handle h, wdad_cnn c, const float* cube, int H,
         if (st != WDAD_OK) return st;
         cudaError_t e = wdad::launch_dwt_approx(cube, P, L, A, K, approx, h->num_sms, s);
         if (e != cudaSuccess) return cuda_fail(h, e, "screen dwt");
+        if (n.norm_mode == 0) e = wdad::cnn::scene_whitening(approx, P, K, n.stat, n.norm, s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "screen whitening");
         // CNN over row tiles with a 7-row halo (receptive field 15)
         for (int r0 = 0; r0 < H && e == cudaSuccess; r0 += tile_rows) {
             const int r1 = std::min(H, r0 + tile_rows);

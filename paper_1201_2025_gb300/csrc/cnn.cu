@@ -12,7 +12,9 @@
 // output pixel and all output channels), conv_bwd_weight (one block per (ci, tap), fixed-
 // order block reduction), bias gradients, transposed/flipped weights (the data gradient is
 // a forward convolution of the output gradient), ReLU masks, MSE loss on the interior of
-// each crop, Adam, crop sampling, and for screening a radix threshold and an audit draw.
+// each crop, Adam, crop sampling, the scene whitening of the input (the network sees
+// z = M (x - mu), with mu and M = L^{-1}, C = L L^T, the mean and covariance of the scene's
+// approximation matrix), and for screening a radix threshold and an audit draw.
 // Random numbers come from splitmix64 (Steele, Lea, Flood 2014) on (seed, counter).
 #include <cuda_bf16.h>
 
@@ -37,7 +39,7 @@ __host__ __device__ __forceinline__ float u01(uint64_t seed, uint64_t ctr) {
 constexpr int CT = 16;  // output tile side of conv_fwd
 
 // out[b][y][x][co] = bias[co] + sum_ci sum_tap in[b][y+ky-p][x+kx-p][ci] * w[ci][tap][co]
-// (zero padding), optional ReLU, optional per-channel input normalisation.
+// (zero padding), optional ReLU, optional input map z = M (x - mu) (norm = [mu (Cin), M (Cin x Cin)]).
 template <int COUT>
 __global__ void __launch_bounds__(CT * CT) conv_fwd_kernel(const float* __restrict__ in, int B, int H, int W, int Cin,
                                                            const float* __restrict__ w, const float* __restrict__ bias,
@@ -52,15 +54,28 @@ __global__ void __launch_bounds__(CT * CT) conv_fwd_kernel(const float* __restri
     const int t = blockIdx.x % (tiles_x * tiles_y);
     const int y0 = (t / tiles_x) * CT, x0 = (t % tiles_x) * CT;
     for (int i = threadIdx.x; i < Cin * taps * COUT; i += blockDim.x) ws[i] = w[i];
-    for (int i = threadIdx.x; i < Cin * T * T; i += blockDim.x) {
-        const int ci = i / (T * T), r = (i / T) % T, c = i % T;
-        const int y = y0 + r - p, x = x0 + c - p;
-        float v = 0.f;
-        if (y >= 0 && y < H && x >= 0 && x < W) {
-            v = in[(((size_t)b * H + y) * W + x) * Cin + ci];
-            if (norm) v = (v - norm[ci]) / norm[Cin + ci];
+    if (norm) {  // first layer: z = M (x - mu) per pixel, Cin <= 8, zero padding in z
+        for (int i = threadIdx.x; i < T * T; i += blockDim.x) {
+            const int y = y0 + i / T - p, x = x0 + i % T - p;
+            float xv[8];
+            const bool inb = y >= 0 && y < H && x >= 0 && x < W;
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                xv[j] = (inb && j < Cin) ? in[(((size_t)b * H + y) * W + x) * Cin + j] - norm[j] : 0.f;
+            for (int ci = 0; ci < Cin; ++ci) {
+                float z = 0.f;
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (j < Cin) z = fmaf(norm[Cin + ci * Cin + j], xv[j], z);
+                xs[(size_t)ci * T * T + i] = z;
+            }
         }
-        xs[i] = v;
+    } else {
+        for (int i = threadIdx.x; i < Cin * T * T; i += blockDim.x) {
+            const int ci = i / (T * T), r = (i / T) % T, c = i % T;
+            const int y = y0 + r - p, x = x0 + c - p;
+            xs[i] = (y >= 0 && y < H && x >= 0 && x < W) ? in[(((size_t)b * H + y) * W + x) * Cin + ci] : 0.f;
+        }
     }
     __syncthreads();
     const int ty = threadIdx.x / CT, tx = threadIdx.x % CT;
@@ -216,7 +231,7 @@ __global__ void init_kernel(float* __restrict__ w, int n, int fan_in, uint64_t s
         w[i] = (2.f * u01(seed, ctr0 + (uint64_t)i) - 1.f) * a;
 }
 
-// B random crops (Hc x Wc) of the approximation matrix, normalised, and their targets
+// B random crops (Hc x Wc) of the approximation matrix, mapped by z = M (x - mu), and their targets
 // log(1 + score); crop positions from splitmix64(seed, step, b)
 __global__ void crops_kernel(const float* __restrict__ approx, const float* __restrict__ score, int H, int W, int K,
                              const float* __restrict__ norm, int B, int Hc, int Wc, uint64_t seed, uint64_t step,
@@ -229,9 +244,107 @@ __global__ void crops_kernel(const float* __restrict__ approx, const float* __re
         const int oy = (int)(u01(seed, base) * (float)(H - Hc + 1)) % (H - Hc + 1);
         const int ox = (int)(u01(seed, base + 1) * (float)(W - Wc + 1)) % (W - Wc + 1);
         const size_t q = (size_t)(oy + r) * W + (ox + c);
-        for (int k = 0; k < K; ++k) x[i * K + k] = (approx[q * K + k] - norm[k]) / norm[K + k];
+        for (int k = 0; k < K; ++k) {
+            float z = 0.f;
+            for (int j = 0; j < K; ++j) z = fmaf(norm[K + k * K + j], approx[q * K + j] - norm[j], z);
+            x[i * K + k] = z;
+        }
         t[i] = log1pf(fmaxf(score[q], 0.f));
     }
+}
+
+// ---------------------------------------------------------------- scene whitening
+// Pass 1: per block, FP64 sums of d = x - x_0 and of d d^T (lower triangle) over a fixed
+// contiguous pixel range; thread, warp (butterfly) and block sums in a fixed order, so the
+// result does not depend on the GPU.  One partial row of NQ doubles per block.
+template <int K>
+__global__ void __launch_bounds__(256) scene_moments_kernel(const float* __restrict__ x, int64_t P,
+                                                            double* __restrict__ part) {
+    constexpr int NQ = K + K * (K + 1) / 2;
+    __shared__ double red[8][NQ];
+    const int64_t chunk = (P + WHITEN_BLOCKS - 1) / WHITEN_BLOCKS;
+    const int64_t p0 = blockIdx.x * chunk, p1 = p0 + chunk < P ? p0 + chunk : P;
+    float x0[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) x0[j] = x[j];
+    double acc[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+    for (int64_t i = p0 + threadIdx.x; i < p1; i += blockDim.x) {
+        double d[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) d[j] = (double)x[i * K + j] - (double)x0[j];
+        int q = K;
+#pragma unroll
+        for (int a = 0; a < K; ++a) {
+            acc[a] += d[a];
+#pragma unroll
+            for (int c = 0; c <= a; ++c) acc[q++] += d[a] * d[c];
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+        for (int o = 16; o >= 1; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+    const int warp = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) red[warp][q] = acc[q];
+    }
+    __syncthreads();
+    if (threadIdx.x < NQ) {
+        double s = 0.0;
+        for (int w = 0; w < 8; ++w) s += red[w][threadIdx.x];
+        part[(size_t)blockIdx.x * NQ + threadIdx.x] = s;
+    }
+}
+
+// Pass 2 (one block): sum the partials in block order, mean and population covariance, the
+// Cholesky factor with the pivot floor 1e-12 trace / K (1 when the trace is 0), and
+// M = L^{-1}; writes norm = [mu (K), M (K x K, row-major)].
+__global__ void scene_whiten_finalize_kernel(const float* __restrict__ x, int64_t P, int K,
+                                             const double* __restrict__ part, float* __restrict__ norm) {
+    __shared__ double S[8 + 36];
+    __shared__ double C[64], Lf[64], M[64];
+    const int NQ = K + K * (K + 1) / 2;
+    if (threadIdx.x < NQ) {
+        double s = 0.0;
+        for (int b = 0; b < WHITEN_BLOCKS; ++b) s += part[(size_t)b * NQ + threadIdx.x];
+        S[threadIdx.x] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const double invP = 1.0 / (double)P;
+    double m1[8];
+    for (int a = 0; a < K; ++a) m1[a] = S[a] * invP;
+    int q = K;
+    double tr = 0.0;
+    for (int a = 0; a < K; ++a)
+        for (int c = 0; c <= a; ++c) {
+            const double v = S[q++] * invP - m1[a] * m1[c];
+            C[a * K + c] = C[c * K + a] = v;
+            if (a == c) tr += v;
+        }
+    const double floor = tr > 0.0 ? 1e-12 * tr / (double)K : 1.0;
+    for (int i = 0; i < 64; ++i) Lf[i] = 0.0;
+    for (int j = 0; j < K; ++j) {
+        double d = C[j * K + j];
+        for (int k = 0; k < j; ++k) d -= Lf[j * K + k] * Lf[j * K + k];
+        if (!(d > floor)) d = floor;
+        Lf[j * K + j] = sqrt(d);
+        for (int i = j + 1; i < K; ++i) {
+            double v = C[i * K + j];
+            for (int k = 0; k < j; ++k) v -= Lf[i * K + k] * Lf[j * K + k];
+            Lf[i * K + j] = v / Lf[j * K + j];
+        }
+    }
+    for (int c = 0; c < K; ++c)
+        for (int i = 0; i < K; ++i) {
+            double v = (i == c) ? 1.0 : 0.0;
+            for (int k = 0; k < i; ++k) v -= Lf[i * K + k] * M[k * K + c];
+            M[i * K + c] = v / Lf[i * K + i];
+        }
+    for (int a = 0; a < K; ++a) norm[a] = (float)((double)x[a] + m1[a]);
+    for (int i = 0; i < K * K; ++i) norm[K + i] = (float)M[i];
 }
 
 // order-preserving float -> uint32 key
@@ -407,6 +520,22 @@ cudaError_t net_init(Net& n, uint64_t seed, cudaStream_t s) {
 
 cudaError_t net_refresh_forward_copy(Net& n, cudaStream_t s) {
     round_copy_kernel<<<grid_for((int64_t)n.nparam, 256), 256, 0, s>>>(n.w, n.wf, (int)n.nparam, n.bf16);
+    return cudaGetLastError();
+}
+
+cudaError_t scene_whitening(const float* x, int64_t P, int K, double* part, float* norm, cudaStream_t s) {
+    if (P < 1 || K < 1 || K > 8) return cudaErrorInvalidValue;
+    switch (K) {
+        case 1: scene_moments_kernel<1><<<WHITEN_BLOCKS, 256, 0, s>>>(x, P, part); break;
+        case 2: scene_moments_kernel<2><<<WHITEN_BLOCKS, 256, 0, s>>>(x, P, part); break;
+        case 3: scene_moments_kernel<3><<<WHITEN_BLOCKS, 256, 0, s>>>(x, P, part); break;
+        case 4: scene_moments_kernel<4><<<WHITEN_BLOCKS, 256, 0, s>>>(x, P, part); break;
+        case 5: scene_moments_kernel<5><<<WHITEN_BLOCKS, 256, 0, s>>>(x, P, part); break;
+        case 6: scene_moments_kernel<6><<<WHITEN_BLOCKS, 256, 0, s>>>(x, P, part); break;
+        case 7: scene_moments_kernel<7><<<WHITEN_BLOCKS, 256, 0, s>>>(x, P, part); break;
+        default: scene_moments_kernel<8><<<WHITEN_BLOCKS, 256, 0, s>>>(x, P, part); break;
+    }
+    scene_whiten_finalize_kernel<<<1, 64, 0, s>>>(x, P, K, part, norm);
     return cudaGetLastError();
 }
 

@@ -5,6 +5,9 @@
 namespace wdad {
 namespace cnn {
 
+constexpr int WHITEN_BLOCKS = 256;  // fixed partition of the scene-moment reduction
+constexpr int WHITEN_NQ_MAX = 8 + 36;
+
 struct Net {
     int K = 4;             // input channels (DWT approximation coefficients)
     int bf16 = 1;          // forward with BF16-rounded weights
@@ -13,7 +16,9 @@ struct Net {
     int64_t max_px = 0;    // largest B * H * W of a training call
     float *w = nullptr, *wf = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
     float* wt = nullptr;   // flipped/transposed weights of one layer
-    float* norm = nullptr; // [2K] input mean, std
+    int norm_mode = 0;     // 0: whiten each scene with its own statistics; 1: fixed map (set_norm)
+    float* norm = nullptr; // [K + K*K] input map z = M (x - mu): mu, then M row-major
+    double* stat = nullptr;  // WHITEN_BLOCKS x WHITEN_NQ_MAX partial moments
     float* act = nullptr;  // activations and gradients of one training batch
     float* loss = nullptr; // device scalar
     float *cx = nullptr, *ct = nullptr;  // crop buffers
@@ -31,6 +36,8 @@ cudaError_t net_grad(Net& n, const float* x, const float* t, int B, int H, int W
 cudaError_t net_adam(Net& n, float lr, cudaStream_t s);
 cudaError_t net_init(Net& n, uint64_t seed, cudaStream_t s);
 cudaError_t net_refresh_forward_copy(Net& n, cudaStream_t s);
+// norm = [mu, M] of the scene whitening of x [P][K] (two launches on s, deterministic)
+cudaError_t scene_whitening(const float* x, int64_t P, int K, double* part, float* norm, cudaStream_t s);
 cudaError_t sample_crops(const Net& n, const float* approx, const float* score, int H, int W, int B, int Hc, int Wc,
                          uint64_t seed, uint64_t step, float* x, float* t, cudaStream_t s);
 cudaError_t top_threshold(const float* v, int64_t n, int64_t kth, unsigned int* hist, uint32_t* thr, cudaStream_t s);

@@ -96,6 +96,44 @@ def make_scene(H: int, W: int, L: int, seed: int = 0, *, n_anom: int = 10,
     return Scene(cube=cube, mask=(frac > 0).astype(np.uint8), endmembers=E, abundance=frac)
 
 
+def make_scene_device(H: int, W: int, L: int, seed: int = 0, *, n_anom: int = 10, anom_side=(2, 2),
+                      abundance=(0.3, 0.3), margin: int = 6, sigma: float = 0.005, device="cuda",
+                      row_block: int = 256):
+    """The same model as make_scene, drawn on a CUDA device for the large bench workloads.
+
+    Endmembers and target placement come from numpy's generator exactly as in make_scene;
+    the per-pixel Dirichlet(1) abundances (normalised Exp(1) draws) and the noise come from a
+    torch generator on the device seeded with `seed`, so the cube is not the one make_scene
+    returns for the same seed, only a draw from the same distribution.
+    Returns (cube [H][W][L] float32 tensor on `device`, mask [H][W] uint8 numpy array)."""
+    import torch
+    rng = np.random.default_rng(seed)
+    E = endmember_spectra(rng, L, 6)
+    frac = np.zeros((H, W), dtype=np.float64)
+    for _ in range(n_anom):
+        side = int(rng.integers(anom_side[0], anom_side[1] + 1))
+        f = float(abundance[0]) if abundance[0] == abundance[1] else float(rng.uniform(*abundance))
+        y0 = int(rng.integers(margin, max(margin, H - margin - side) + 1))
+        x0 = int(rng.integers(margin, max(margin, W - margin - side) + 1))
+        frac[y0:y0 + side, x0:x0 + side] = f
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    Ed = torch.from_numpy(E).to(device)
+    fd = torch.from_numpy(frac).to(device)
+    cube = torch.empty((H, W, L), device=device, dtype=torch.float32)
+    for r0 in range(0, H, row_block):
+        r1 = min(H, r0 + row_block)
+        u = torch.rand((r1 - r0, W, 5), generator=g, device=device, dtype=torch.float64)
+        e = -torch.log1p(-u)
+        ab = e / e.sum(-1, keepdim=True)
+        b = torch.einsum("hwk,kl->hwl", ab, Ed[:5])
+        f = fd[r0:r1, :, None]
+        z = f * Ed[5][None, None, :] + (1.0 - f) * b  # Eq. 10 (identity where f == 0)
+        z += sigma * torch.randn((r1 - r0, W, L), generator=g, device=device, dtype=torch.float64)
+        cube[r0:r1] = z.float()
+    return cube, (frac > 0).astype(np.uint8)
+
+
 # Workloads, named for what they are.
 def scene_48x48(seed: int = 0) -> Scene:
     """48x48x224, ten 2x2 targets at abundance 0.3, >= 6 px from the border."""

@@ -89,13 +89,14 @@ def lib() -> ctypes.CDLL:
                                   i32, i32, f32p, vp, vp, ctypes.POINTER(i64), vp]
     L.wdad_detect_all_noalloc.argtypes = [f32p, i32, i32, i32, pp, f32p, vp, vp]
     L.wdad_auc.argtypes = [vp, vp, i64, ctypes.POINTER(ctypes.c_double)]
+    L.wdad_scene_whitening.argtypes = [vp, f32p, i64, i32, f32p, vp]
     for name in ("wdad_create", "wdad_destroy", "wdad_last_error_detail", "wdad_dwt_approx", "wdad_detect",
                  "wdad_detect_all", "wdad_detect_all_host", "wdad_window_census", "wdad_auc",
                  "wdad_detect_all_noalloc", "wdad_window_moments", "wdad_autotune", "wdad_batch_create",
                  "wdad_batch_launch", "wdad_batch_status", "wdad_batch_destroy", "wdad_batch_run",
                  "wdad_cnn_create", "wdad_cnn_destroy", "wdad_cnn_set_norm", "wdad_cnn_params",
                  "wdad_cnn_set_params", "wdad_cnn_forward", "wdad_cnn_grad", "wdad_cnn_train", "wdad_cnn_save",
-                 "wdad_cnn_load", "wdad_screen_run"):
+                 "wdad_cnn_load", "wdad_screen_run", "wdad_scene_whitening"):
         getattr(L, name).restype = i32
     L.wdad_query_K.restype = i32
     _lib = L
@@ -361,8 +362,12 @@ class wdad_cnn:
         import torch
         return ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
 
-    def set_norm(self, mean_std):
-        a = np.ascontiguousarray(mean_std, dtype=np.float32)
+    def set_norm(self, mu_M=None):
+        """Fixed input map [mu (K), M (K x K)] with z = M (x - mu); None: whiten each scene."""
+        if mu_M is None:
+            _check(lib().wdad_cnn_set_norm(self._c, None), self._h)
+            return
+        a = np.ascontiguousarray(mu_M, dtype=np.float32).ravel()
         _check(lib().wdad_cnn_set_norm(self._c, a.ctypes.data), self._h)
 
     def params(self) -> np.ndarray:
@@ -387,7 +392,7 @@ class wdad_cnn:
         return out
 
     def grad(self, x, t):
-        """Interior-MSE loss and gradient (host) for normalised x [B, H, W, K], targets [B, H, W]."""
+        """Interior-MSE loss and gradient (host) for mapped input z [B, H, W, K], targets [B, H, W]."""
         x = x.contiguous()
         t = t.contiguous()
         B, H, W, _ = x.shape
@@ -442,6 +447,18 @@ def wdad_screen_run(net: "wdad_cnn", cube, top_frac: float = 0.02, audit_frac: f
                                  pred.data_ptr() if pred is not None else None, sel.data_ptr(), ctypes.byref(n),
                                  _stream(cube)), h)
     return score, pred, sel, n.value
+
+
+def wdad_scene_whitening(x):
+    """[mu (K), M (K x K) row-major] of the scene whitening of x [..., K] (CUDA tensor)."""
+    import torch
+    x = x.contiguous()
+    K = x.shape[-1]
+    P = x.numel() // K
+    out = torch.empty(K + K * K, device=x.device, dtype=torch.float32)
+    h = handle(x.device.index or 0)
+    _check(lib().wdad_scene_whitening(h, x.data_ptr(), P, K, out.data_ptr(), _stream(x)), h)
+    return out
 
 
 def wdad_window_census(H: int, W: int, params: wdad_params | None = None, device: int = 0, **over):

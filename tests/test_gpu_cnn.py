@@ -1,4 +1,5 @@
-"""A9 learned screening: the CNN's forward and gradients against the FP64 oracle, training,
+"""A9 learned screening: the CNN's forward and gradients against the FP64 oracle, the scene
+whitening of its input, the tiled screening pass against the oracle chain, training,
 checkpoint/resume, and screened LRX against the exact detector."""
 import numpy as np
 import pytest
@@ -7,6 +8,10 @@ import oracle
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
+
+# Screened DWT-LRX recall bar at top 5% + 1% audit on a held-out 96x96 scene (implanted pixels
+# the exact DWT-LRX map ranks in its top 5%).
+RECALL_MIN = 0.75
 
 
 @pytest.fixture(scope="module")
@@ -44,68 +49,145 @@ def test_gradients_match_fp64_oracle(wd, bf16, tol):
 
 
 def test_forward_matches_fp64_oracle(wd):
+    # a fixed input map z = M (x - mu) with a full lower-triangular M
     net = wd.wdad_cnn(K=4, bf16_weights=False, seed=4)
-    norm = np.array([2.0, 2.5, 1.5, 3.0, 0.5, 0.8, 1.2, 0.4], np.float32)
-    net.set_norm(norm)
-    x = (2.0 + np.random.default_rng(6).standard_normal((2, 20, 33, 4))).astype(np.float32)
+    rng = np.random.default_rng(6)
+    mu = np.array([2.0, 2.5, 1.5, 3.0], np.float32)
+    M = np.tril(rng.uniform(0.2, 1.0, (4, 4))).astype(np.float32)
+    net.set_norm(np.concatenate([mu, M.ravel()]))
+    x = (2.0 + rng.standard_normal((2, 20, 33, 4))).astype(np.float32)
     got = net.forward(torch.from_numpy(x).cuda()).cpu().numpy()
-    xn = (x.astype(np.float64) - norm[:4]) / norm[4:]
-    want = oracle.cnn_forward(net.params().astype(np.float64), xn)
+    z = (x.astype(np.float64) - mu) @ M.astype(np.float64).T
+    want = oracle.cnn_forward(net.params().astype(np.float64), z)
     assert np.abs(got - want).max() <= 1e-5 * np.abs(want).max()
     net.close()
 
 
-@pytest.fixture(scope="module")
-def training_set(wd):  # 4 seeded 96x96x224 scenes, DWT-LRX (5,15) targets; the last is held out
+@pytest.mark.parametrize("K,P", [(1, 1), (4, 1), (4, 5), (4, 1000), (3, 70001), (8, 4099)])
+def test_scene_whitening_matches_oracle(wd, K, P):
+    rng = np.random.default_rng(K * 100 + P)
+    A = np.eye(K) + 0.4 * rng.standard_normal((K, K))
+    x = (0.3 + 0.02 * rng.standard_normal((P, K)) @ A.T).astype(np.float32)
+    got = wd.wdad_scene_whitening(torch.from_numpy(x).cuda()).cpu().numpy()
+    mu, M = oracle.scene_whiten(x.astype(np.float64))
+    np.testing.assert_allclose(got[:K], mu, rtol=1e-6, atol=0)
+    assert np.abs(got[K:] - M.ravel()).max() <= 1e-5 * np.abs(M).max()
+
+
+def test_whitening_rejects_empty_input(wd):
+    with pytest.raises(RuntimeError):
+        wd.wdad_scene_whitening(torch.zeros((0, 4), device="cuda"))
+
+
+def test_per_scene_forward_matches_oracle(wd):
+    # default mode: the forward whitens its input with the input's own statistics
+    net = wd.wdad_cnn(K=4, bf16_weights=True, seed=5)
+    rng = np.random.default_rng(7)
+    x = (0.3 + 0.05 * rng.standard_normal((1, 31, 37, 4)) @ (np.eye(4) + 0.5 * rng.standard_normal((4, 4)))
+         ).astype(np.float32)
+    got = net.forward(torch.from_numpy(x).cuda()).cpu().numpy()
+    mu, M = oracle.scene_whiten(x.astype(np.float64))
+    z = (x.astype(np.float64) - mu) @ M.T
+    want = oracle.cnn_forward(bf16_round(net.params()).astype(np.float64), z)
+    assert np.abs(got - want).max() <= 1e-4 * np.abs(want).max()
+    net.close()
+
+
+def test_screen_predictions_match_oracle_chain(wd):
+    """The screening pass's predictions (DWT, scene whitening, CNN over row tiles with a halo)
+    against the oracle's DWT, whitening and FP64 forward of the whole map: 40 rows in tiles of
+    16 (two full tiles and a ragged one)."""
     from paper_1201_2025_gb300 import synth
+    sc = synth.make_scene(40, 52, 224, seed=21, n_anom=4, anom_side=(1, 3), abundance=(0.1, 0.5), margin=4)
+    net = wd.wdad_cnn(K=4, bf16_weights=True, seed=12)
+    _, pred, sel, nsel = wd.wdad_screen_run(net, torch.from_numpy(sc.cube).cuda(), top_frac=0.1, audit_frac=0.0,
+                                            seed=1, tile_rows=16, exact_reduce=True, inner=5, outer=15)
+    ap = oracle.dwt_approx(sc.cube)
+    mu, M = oracle.scene_whiten(ap)
+    want = oracle.cnn_forward(bf16_round(net.params()).astype(np.float64), ((ap - mu) @ M.T)[None])[0]
+    got = pred.cpu().numpy()
+    assert np.abs(got - want).max() <= 1e-4 * np.abs(want).max()
+    # with no audit the selection is exactly the predictions at or above the k-th largest
+    k = int(np.ceil(0.1 * got.size))
+    thr = np.sort(got.ravel())[-k]
+    np.testing.assert_array_equal(sel.cpu().numpy() > 0, got >= thr)
+    assert nsel == int((got >= thr).sum())
+    net.close()
+
+
+TRAIN_SEEDS = range(1, 17)
+
+
+def _scene96(seed):
+    from paper_1201_2025_gb300 import synth
+    return synth.make_scene(96, 96, 224, seed=seed, n_anom=12, anom_side=(1, 3), abundance=(0.1, 0.5), margin=4)
+
+
+@pytest.fixture(scope="module")
+def training_set(wd):  # 16 seeded 96x96x224 scenes (own endmembers each), DWT-LRX (5,15) targets
     out = []
-    for seed in range(1, 5):
-        sc = synth.make_scene(96, 96, 224, seed=seed, n_anom=12, anom_side=(1, 3), abundance=(0.1, 0.5), margin=4)
-        x = torch.from_numpy(sc.cube).cuda()
+    for seed in TRAIN_SEEDS:
+        x = torch.from_numpy(_scene96(seed).cube).cuda()
         approx = wd.wdad_dwt_approx(x)
         lrx = wd.wdad_detect(approx, 0, reduce=False, inner=5, outer=15)
         out.append((approx, lrx))
-    allv = torch.cat([a.reshape(-1, 4) for a, _ in out])
-    norm = torch.cat([allv.mean(0), allv.std(0)]).cpu().numpy()
-    return out, norm
+    return out
 
 
 def test_checkpoint_resume_is_bit_exact(wd, training_set, tmp_path):
-    data, norm = training_set
-    approx, lrx = data[0]
-    a = wd.wdad_cnn(K=4, seed=9)
-    a.set_norm(norm)
-    a.train(approx, lrx, steps=3, batch=4, crop=32, lr=1e-3, seed=1)
-    path = str(tmp_path / "cnn.ckpt")
-    a.save(path)
-    a.train(approx, lrx, steps=3, batch=4, crop=32, lr=1e-3, seed=1)
-    b = wd.wdad_cnn.load(path)
-    b.train(approx, lrx, steps=3, batch=4, crop=32, lr=1e-3, seed=1)
-    assert np.array_equal(a.params(), b.params())
-    a.close(); b.close()
+    approx, lrx = training_set[0]
+    for fixed in (False, True):
+        a = wd.wdad_cnn(K=4, seed=9)
+        if fixed:
+            a.set_norm(np.concatenate([[0.1, 0.2, 0.3, 0.4], np.eye(4).ravel() * 3.0]))
+        a.train(approx, lrx, steps=3, batch=4, crop=32, lr=1e-3, seed=1)
+        path = str(tmp_path / f"cnn{int(fixed)}.ckpt")
+        a.save(path)
+        a.train(approx, lrx, steps=3, batch=4, crop=32, lr=1e-3, seed=1)
+        b = wd.wdad_cnn.load(path)
+        b.train(approx, lrx, steps=3, batch=4, crop=32, lr=1e-3, seed=1)
+        assert np.array_equal(a.params(), b.params())
+        assert torch.equal(a.forward(approx[None].contiguous()), b.forward(approx[None].contiguous()))
+        a.close(); b.close()
 
 
-def test_screening_recall_and_exact_values(wd, training_set):
-    from paper_1201_2025_gb300 import synth
-    data, norm = training_set
+def _train(wd, data, steps=1500, per_call=5, lr=2e-3):
+    """Adam on crops of the scenes in turn, `per_call` steps per scene; lr halved for the last 30%."""
     net = wd.wdad_cnn(K=4, seed=11)
-    net.set_norm(norm)
-    # a fixed validation batch: the full (normalised) last training cube and its targets
-    approx_v, lrx_v = data[-1]
-    nt = torch.from_numpy(norm).cuda()
-    xv = ((approx_v - nt[:4]) / nt[4:]).unsqueeze(0).contiguous()
-    tv = torch.log1p(lrx_v.clamp_min(0)).unsqueeze(0).contiguous()
-    before, _ = net.grad(xv, tv)
-    for epoch in range(6):
-        for approx, lrx in data[:-1]:
-            net.train(approx, lrx, steps=40, batch=8, crop=32, lr=2e-3, seed=100 + epoch)
-    after, _ = net.grad(xv, tv)
-    assert after < 0.7 * before, (before, after)
-    test = synth.make_scene(96, 96, 224, seed=77, n_anom=12, anom_side=(1, 3), abundance=(0.1, 0.5), margin=4)
+    calls = steps // per_call
+    for it in range(calls):
+        approx, lrx = data[it % len(data)]
+        net.train(approx, lrx, steps=per_call, batch=8, crop=32, lr=lr if it < 0.7 * calls else lr / 2, seed=100 + it)
+    return net
+
+
+@pytest.fixture(scope="module")
+def trained(wd, training_set):
+    net = _train(wd, training_set[:-1])
+    yield net
+    net.close()
+
+
+def test_training_lowers_held_out_loss(wd, training_set, trained):
+    approx_v, lrx_v = training_set[-1]  # held out
+    nm = wd.wdad_scene_whitening(approx_v)
+    z = ((approx_v - nm[:4]) @ nm[4:].reshape(4, 4).T).unsqueeze(0).contiguous()
+    t = torch.log1p(lrx_v.clamp_min(0)).unsqueeze(0).contiguous()
+    fresh = wd.wdad_cnn(K=4, seed=11)
+    before, _ = fresh.grad(z, t)
+    after, _ = trained.grad(z, t)
+    print(f"held-out interior MSE {before:.3f} -> {after:.3f}")
+    assert after < 0.2 * before, (before, after)
+    fresh.close()
+
+
+@pytest.mark.parametrize("seed", [77, 78])
+def test_screening_recall_and_exact_values(wd, trained, seed):
+    test = _scene96(seed)
     x = torch.from_numpy(test.cube).cuda()
     # screened DWT-LRX (the detector the network learned): recall of implanted anomalies that the
-    # exact DWT-LRX map ranks in its top 5%, evaluating 6% of the pixels exactly
-    score, pred, sel, nsel = wd.wdad_screen_run(net, x, top_frac=0.05, audit_frac=0.01, seed=3, tile_rows=40,
+    # exact DWT-LRX map ranks in its top 5%, with 6% of the pixels evaluated exactly
+    score, pred, sel, nsel = wd.wdad_screen_run(trained, x, top_frac=0.05, audit_frac=0.01, seed=3, tile_rows=40,
                                                 exact_reduce=True, inner=5, outer=15)
     s = score.cpu().numpy()
     selm = sel.cpu().numpy() > 0
@@ -115,10 +197,11 @@ def test_screening_recall_and_exact_values(wd, training_set):
     truth = (test.mask > 0) & (red >= np.quantile(red, 0.95))
     assert truth.sum() >= 5
     recall = (selm & truth).sum() / truth.sum()
+    # without the network, the same budget of pixels drawn at random finds about selm.mean()
     print(f"screened DWT-LRX recall {recall:.3f} with {selm.mean():.3f} of pixels evaluated")
-    assert recall >= 0.8 and recall > 5 * selm.mean(), (recall, selm.mean())
+    assert recall >= RECALL_MIN and recall > 10 * selm.mean(), (recall, selm.mean())
     # screened full-band LRX: exact values bit-identical to the full map at the selected pixels
-    score, _, sel, nsel = wd.wdad_screen_run(net, x, top_frac=0.05, audit_frac=0.01, seed=3, tile_rows=40,
+    score, _, sel, nsel = wd.wdad_screen_run(trained, x, top_frac=0.05, audit_frac=0.01, seed=3, tile_rows=40,
                                              exact_reduce=False, inner=5, outer=15, want_pred=False)
     s = score.cpu().numpy()
     selm = sel.cpu().numpy() > 0
@@ -129,4 +212,3 @@ def test_screening_recall_and_exact_values(wd, training_set):
     print(f"screened full-band LRX recall {recall_full:.3f} (the approximation-space network cannot see "
           f"what only the full band separates)")
     assert recall_full > selm.mean()
-    net.close()
