@@ -243,7 +243,9 @@ wdad_status wdad_cnn_train(wdad_cnn c, const float* approx, const float* score, 
 wdad_status wdad_cnn_save(wdad_cnn c, const char* path);
 wdad_status wdad_cnn_load(wdad_handle h, const char* path, int64_t max_batch_pixels, wdad_cnn* out);
 /* Screened LRX: A1 on the cube, the CNN on row tiles (tile_rows + 7-row halo), the top
- * top_frac of its predictions plus a random audit of audit_frac (splitmix64(seed, pixel)),
+ * top_frac of its predictions (every pixel whose prediction is at least the k-th largest,
+ * k = max(1, ceil(top_frac * H * W)) up to one float rounding of top_frac; ties at the
+ * threshold are all taken) plus a random audit of audit_frac (splitmix64(seed, pixel)),
  * then the exact LRX (exact_reduce = 0: full band; 1: on the reduced cube) on the selected
  * pixels only.  score [H][W]: exact LRX where selected, -inf elsewhere.  pred [H][W] and
  * selected [H][W] (1 = top, 2 = audit, 0 = skipped) are nullable; *n_selected (host,

@@ -1,15 +1,19 @@
 // A8 — many cubes of uneven size, band count, window and detector in one persistent
 // launch (captured once into a CUDA graph and replayed).
 //
-// The host builds a work list: first every cube's DWT items (ranges of 8-pixel groups),
-// then every cube's detector tiles.  Persistent CTAs pop items with one atomic counter.
-// A tile of cube j may only start once all DWT items of cube j have finished: the DWT
-// items bump done[j] after a fence, and the tile's first thread waits for
-// done[j] == dwt_items[j] with a bounded spin.  Items are popped in list order, so every
-// DWT item a tile waits on is already held by a running CTA that will finish it; if the
-// spin still runs out (about a second), the tile is skipped and the launch status becomes
-// WDAD_ERR_TIMEOUT instead of hanging.  The per-item arithmetic is the same device code
-// as the standalone kernels, with the same tile plan, so a batched job's scores are
+// The host builds a work list of DWT items (ranges of 4-pixel groups of one cube) and
+// detector tiles, software-pipelined by one job: the DWT items of cube j + 1 are interleaved,
+// in proportion to their counts, with the tiles of cube j, so that HBM-bound DWT items and
+// ALU-bound tiles run side by side on each SM (two 512-thread CTAs per SM when the largest
+// tile plan fits).  Persistent CTAs pop items with one atomic counter.  A tile of cube j may
+// only start once all DWT items of cube j have finished: the DWT items bump done[j] after a
+// fence, and the tile's first thread waits for done[j] == dwt_items[j] with a bounded spin.
+// Items are popped in list order and every DWT item of cube j precedes every tile of cube j,
+// so each DWT item a tile waits on is already held by a running CTA that will finish it (DWT
+// items never wait); if the spin still runs out (about a second), the tile is skipped and the
+// launch status becomes WDAD_ERR_TIMEOUT instead of hanging.  The per-item arithmetic gives
+// the same bits as the standalone kernels with the same tile plan (the DWT reads its matrix
+// from shared memory but sums in the same order), so a batched job's scores are
 // bit-identical to the same job run alone.
 #include <cstdlib>
 
@@ -20,14 +24,17 @@
 namespace wdad {
 
 constexpr int BATCH_THREADS = 512;
-constexpr int kGroupsPerDwtItem = 512;  // 4096 pixels per DWT item
+constexpr int kGroupsPerDwtItem = 1024;  // 4-pixel groups: 4096 pixels per DWT item
 
-__global__ void __launch_bounds__(BATCH_THREADS, 1)
+__global__ void __launch_bounds__(BATCH_THREADS, 2)
     batch_kernel(const BatchJob* __restrict__ jobs, const BatchItem* __restrict__ items, int nitems, int* counter,
                  int* done, int* status, uint32_t spin_limit) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
     __shared__ int s_ready;
+    // the tile's arguments live in shared memory (a kernel parameter in the standalone
+    // kernel), which keeps them out of the 64 registers a thread has at two CTAs per SM
+    __shared__ DetectArgs s_args;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
         __syncthreads();
@@ -39,10 +46,18 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1)
         if (bi.kind == 0) {
             const int64_t P = (int64_t)j.H * j.W;
             const int64_t warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+            // the job's K x L DWT matrix into shared memory, rows of LS floats, zero-padded
+            float* A_s = reinterpret_cast<float*>(smem_raw);
+            const int LS = j.variant == 0 ? 128 : 256;
+            for (int i = threadIdx.x; i < 4 * LS; i += blockDim.x) {
+                const int k = i / LS, c = i % LS;
+                A_s[i] = (k < j.K && c < j.L) ? j.A[(size_t)k * j.L + c] : 0.0f;
+            }
+            __syncthreads();
             if (j.variant == 0)
-                dwt_groups<4, 1, 4>(j.cube, P, j.L, j.A, j.K, j.approx, bi.a, bi.b, warp, nw);
+                dwt_groups_sA<1>(j.cube, P, j.L, A_s, j.K, j.approx, bi.a, bi.b, warp, nw);
             else
-                dwt_groups<4, 2, 4>(j.cube, P, j.L, j.A, j.K, j.approx, bi.a, bi.b, warp, nw);
+                dwt_groups_sA<2>(j.cube, P, j.L, A_s, j.K, j.approx, bi.a, bi.b, warp, nw);
             __syncthreads();
             if (threadIdx.x == 0) {
                 __threadfence();
@@ -63,20 +78,21 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1)
                 }
                 __threadfence();
                 s_ready = ok;
-            }
-            __syncthreads();
-            if (s_ready) {
-                DetectArgs a{};
+                DetectArgs& a = s_args;
                 a.x = j.approx; a.H = j.H; a.W = j.W; a.D = j.K;
                 a.inner = j.inner; a.outer = j.outer; a.loading = j.loading; a.border = j.border;
                 a.dwest_mode = j.dwest_mode; a.dwest_tau = j.tau;
                 for (int t = 0; t < 3; ++t) a.out[t] = j.out[t];
                 a.flags = j.flags;
-                switch (j.K) {
-                    case 1: detect_tile<1>(a, j.th, bi.a, bi.b, smem_raw); break;
-                    case 2: detect_tile<2>(a, j.th, bi.a, bi.b, smem_raw); break;
-                    case 3: detect_tile<3>(a, j.th, bi.a, bi.b, smem_raw); break;
-                    default: detect_tile<4>(a, j.th, bi.a, bi.b, smem_raw); break;
+            }
+            __syncthreads();
+            if (s_ready) {
+                const int th = j.th;
+                switch (s_args.D) {
+                    case 1: detect_tile<1>(s_args, th, bi.a, bi.b, smem_raw); break;
+                    case 2: detect_tile<2>(s_args, th, bi.a, bi.b, smem_raw); break;
+                    case 3: detect_tile<3>(s_args, th, bi.a, bi.b, smem_raw); break;
+                    default: detect_tile<4>(s_args, th, bi.a, bi.b, smem_raw); break;
                 }
             }
             __syncthreads();
@@ -88,24 +104,38 @@ bool batch_job_supported(int L, int K) { return L % 4 == 0 && L <= 256 && K >= 1
 
 int batch_variant(int L) { return L <= 128 ? 0 : 1; }
 
+size_t batch_dwt_smem(int L) { return sizeof(float) * 4 * (size_t)(batch_variant(L) == 0 ? 128 : 256); }
+
 void batch_build_items(const std::vector<BatchJob>& jobs, std::vector<BatchItem>& items, std::vector<int>& dwt_items,
                        int drop_job) {
-    items.clear();
-    dwt_items.assign(jobs.size(), 0);
-    for (size_t j = 0; j < jobs.size(); ++j) {
+    const size_t n = jobs.size();
+    std::vector<std::vector<BatchItem>> dw(n), tl(n);
+    dwt_items.assign(n, 0);
+    for (size_t j = 0; j < n; ++j) {
         const int64_t P = (int64_t)jobs[j].H * jobs[j].W;
-        const int64_t ngroups = (P + 7) / 8;
+        const int64_t ngroups = (P + 3) / 4;
         bool dropped = false;
         for (int64_t g0 = 0; g0 < ngroups; g0 += kGroupsPerDwtItem) {
             dwt_items[j]++;
             if ((int)j == drop_job && !dropped) { dropped = true; continue; }  // fault injection (host only)
-            items.push_back({(int)j, 0, (int)g0, (int)std::min<int64_t>(ngroups, g0 + kGroupsPerDwtItem)});
+            dw[j].push_back({(int)j, 0, (int)g0, (int)std::min<int64_t>(ngroups, g0 + kGroupsPerDwtItem)});
         }
-    }
-    for (size_t j = 0; j < jobs.size(); ++j) {
         const int tx = (jobs[j].W + 31) / 32, ty = (jobs[j].H + jobs[j].th - 1) / jobs[j].th;
         for (int y = 0; y < ty; ++y)
-            for (int x = 0; x < tx; ++x) items.push_back({(int)j, 1, x, y});
+            for (int x = 0; x < tx; ++x) tl[j].push_back({(int)j, 1, x, y});
+    }
+    // stage s: DWT items of job s interleaved (proportionally) with the tiles of job s - 1
+    items.clear();
+    static const std::vector<BatchItem> none;
+    for (size_t st = 0; st <= n; ++st) {
+        const std::vector<BatchItem>& A = st < n ? dw[st] : none;
+        const std::vector<BatchItem>& B = st > 0 ? tl[st - 1] : none;
+        const size_t a = A.size(), b = B.size();
+        size_t ia = 0, ib = 0;
+        while (ia < a || ib < b) {
+            if (ib >= b || (ia < a && ia * b <= ib * a)) items.push_back(A[ia++]);
+            else items.push_back(B[ib++]);
+        }
     }
 }
 

@@ -22,12 +22,14 @@ struct BatchJob {
 
 struct BatchItem {
     int job;
-    int kind;  // 0 = DWT pixel groups [a, b), 1 = detector tile (a, b) = (tile_x, tile_y)
+    int kind;  // 0 = DWT 4-pixel groups [a, b), 1 = detector tile (a, b) = (tile_x, tile_y)
     int a, b;
 };
 
 bool batch_job_supported(int L, int K);
 int batch_variant(int L);
+// shared memory a DWT item needs (the job's DWT matrix, zero-padded rows)
+size_t batch_dwt_smem(int L);
 // drop_job >= 0 removes that job's first DWT item from the list (host-side fault injection
 // for tests of the bounded wait); -1 in normal use.
 void batch_build_items(const std::vector<BatchJob>& jobs, std::vector<BatchItem>& items, std::vector<int>& dwt_items,

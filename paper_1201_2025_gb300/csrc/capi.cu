@@ -571,6 +571,7 @@ wdad_status wdad_batch_create(wdad_handle h, int n, const wdad_job* jobs, int au
             }
             if (th < 1) return fail(h, WDAD_ERR_UNSUPPORTED, "batch job %d: window too large", i);
             smem = std::max(smem, wdad::detect_small_smem(K, j.params.inner, j.params.outer, th));
+            smem = std::max(smem, wdad::batch_dwt_smem(j.L));
             wdad::BatchJob& bj = hj[(size_t)i];
             bj = wdad::BatchJob{};
             bj.cube = j.cube; bj.A = A; bj.flags = j.flags;
@@ -966,7 +967,10 @@ wdad_status wdad_screen_run(wdad_handle h, wdad_cnn c, const float* cube, int H,
             if (e != cudaSuccess) return cuda_fail(h, e, "screen pred copy");
         }
         // top fraction threshold, audit draw, compaction
-        const int64_t kth = std::max<int64_t>(1, (int64_t)std::ceil((double)top_frac * (double)P));
+        // ceil(top_frac * P) with a slack of one float rounding of top_frac, so that e.g. 0.1f of
+        // 2080 pixels counts 208 (0.1f is 0.100000001...)
+        const int64_t kth =
+            std::max<int64_t>(1, (int64_t)std::ceil((double)top_frac * (double)P * (1.0 - 1.2e-7)));
         uint32_t thr = 0;
         e = wdad::cnn::top_threshold(pred, P, kth, hist, &thr, s);
         if (e == cudaSuccess) e = wdad::cnn::select_pixels(pred, P, thr, audit_frac, seed, selected, list, cnt, s);

@@ -27,6 +27,76 @@ __device__ __forceinline__ float butterfly32(float (&v)[32], int lane) {
     return v[0];
 }
 
+// Reduce-scatter of 16 per-lane values over the 32 lanes: afterwards lanes l and l ^ 16 both
+// hold the sum over all lanes of v[l & 15].  The summation tree (lane pairs over bit 4, then
+// bits 3, 2, 1, 0, each addition own + partner) is the one butterfly32 builds for its value
+// indices, so the two give bit-identical sums for the same per-lane inputs.
+__device__ __forceinline__ float butterfly16x2(float (&v)[16], int lane) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] += __shfl_xor_sync(0xffffffffu, v[j], 16);
+#pragma unroll
+    for (int off = 8; off >= 1; off >>= 1) {
+        const bool upper = (lane & off) != 0;
+#pragma unroll
+        for (int j = 0; j < off; ++j) {
+            const float send = upper ? v[j] : v[j + off];
+            const float keep = upper ? v[j + off] : v[j];
+            v[j] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+    }
+    return v[0];
+}
+
+// Variant of dwt_groups for the persistent batch kernel (16-byte chunks, K <= 4, 4 pixels per
+// warp step): the DWT matrix comes from shared memory, A_s[k * NCH*128 + c] (zero for c >= L
+// and k >= K), instead of registers, which keeps the kernel within 64 registers a thread.  The
+// per-lane sums take the same (chunk, element) order and butterfly16x2 builds the same lane
+// tree as dwt_groups' butterfly32, so the coefficients are bit-identical to dwt_apply_kernel's.
+// Groups are 4-pixel groups here.
+template <int NCH>
+__device__ __forceinline__ void dwt_groups_sA(const float* __restrict__ cube, int64_t P, int L,
+                                              const float* __restrict__ A_s, int K, float* __restrict__ out,
+                                              int64_t g_begin, int64_t g_end, int64_t warp, int64_t nwarps) {
+    constexpr int PX = 4, KP = 4, LS = NCH * 128;
+    const int lane = threadIdx.x & 31;
+    const int LV = L / 4;
+    for (int64_t g = g_begin + warp; g < g_end; g += nwarps) {
+        const int64_t p0 = g * PX;
+        float x[PX][NCH][4];
+#pragma unroll
+        for (int p = 0; p < PX; ++p)
+#pragma unroll
+            for (int i = 0; i < NCH; ++i) {
+                const int c = lane + 32 * i;
+                float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+                if ((p0 + p < P) && (c < LV)) t = __ldcs(reinterpret_cast<const float4*>(cube + (p0 + p) * L) + c);
+                x[p][i][0] = t.x; x[p][i][1] = t.y; x[p][i][2] = t.z; x[p][i][3] = t.w;
+            }
+        float v[16];
+#pragma unroll
+        for (int k = 0; k < KP; ++k) {
+            float s[PX];
+#pragma unroll
+            for (int p = 0; p < PX; ++p) s[p] = 0.0f;
+#pragma unroll
+            for (int i = 0; i < NCH; ++i) {
+                const float4 a4 = *reinterpret_cast<const float4*>(A_s + k * LS + (lane + 32 * i) * 4);
+#pragma unroll
+                for (int p = 0; p < PX; ++p) {
+                    s[p] = fmaf(x[p][i][0], a4.x, s[p]);
+                    s[p] = fmaf(x[p][i][1], a4.y, s[p]);
+                    s[p] = fmaf(x[p][i][2], a4.z, s[p]);
+                    s[p] = fmaf(x[p][i][3], a4.w, s[p]);
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < PX; ++p) v[p * KP + k] = s[p];
+        }
+        const float r = butterfly16x2(v, lane);
+        const int t = lane & 15, p = t / KP, k = t % KP;
+        if (lane < 16 && k < K && p0 + p < P) out[(p0 + p) * K + k] = r;
+    }
+}
 
 // VEC = 4: 16-byte chunks (L % 4 == 0); VEC = 1: 4-byte elements.
 // NCH = chunks per lane (NCH * 32 * VEC >= L); KP = K padded to a power of two <= 8.
