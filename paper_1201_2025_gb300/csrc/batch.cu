@@ -2,16 +2,17 @@
 // launch (captured once into a CUDA graph and replayed).
 //
 // The host builds a work list of DWT items (ranges of 4-pixel groups of one cube) and
-// detector tiles, software-pipelined by one job: the DWT items of cube j + 1 are interleaved,
-// in proportion to their counts, with the tiles of cube j, so that HBM-bound DWT items and
-// ALU-bound tiles run side by side on each SM (two 512-thread CTAs per SM when the largest
-// tile plan fits).  Persistent CTAs pop items with one atomic counter.  A tile of cube j may
-// only start once all DWT items of cube j have finished: the DWT items bump done[j] after a
-// fence, and the tile's first thread waits for done[j] == dwt_items[j] with a bounded spin.
-// Items are popped in list order and every DWT item of cube j precedes every tile of cube j,
-// so each DWT item a tile waits on is already held by a running CTA that will finish it (DWT
-// items never wait); if the spin still runs out (about a second), the tile is skipped and the
-// launch status becomes WDAD_ERR_TIMEOUT instead of hanging.  The per-item arithmetic gives
+// detector tiles: the two streams are merged in proportion to their lengths, so that
+// HBM-bound DWT items and ALU-bound tiles run side by side on each SM (two 512-thread CTAs
+// per SM when the largest tile plan fits), and every tile of cube j is placed after all DWT
+// items of cube j plus a lag of about four times the grid's CTAs.  Persistent CTAs pop items
+// with one atomic counter.  A tile of cube j may only start once all DWT items of cube j have
+// finished: the DWT items bump done[j] after a fence, and the tile's first thread waits for
+// done[j] == dwt_items[j] with a bounded spin.  Items are popped in list order and every DWT
+// item of cube j precedes every tile of cube j, so each DWT item a tile waits on is already
+// held by a running CTA that will finish it (DWT items never wait); if the spin still runs out
+// (about a second), the tile is skipped and the launch status becomes WDAD_ERR_TIMEOUT instead
+// of hanging.  The per-item arithmetic gives
 // the same bits as the standalone kernels with the same tile plan (the DWT reads its matrix
 // from shared memory but sums in the same order), so a batched job's scores are
 // bit-identical to the same job run alone.
@@ -24,7 +25,7 @@
 namespace wdad {
 
 constexpr int BATCH_THREADS = 512;
-constexpr int kGroupsPerDwtItem = 1024;  // 4-pixel groups: 4096 pixels per DWT item
+constexpr int kGroupsPerDwtItem = 512;  // 4-pixel groups: 2048 pixels per DWT item
 
 __global__ void __launch_bounds__(BATCH_THREADS, 2)
     batch_kernel(const BatchJob* __restrict__ jobs, const BatchItem* __restrict__ items, int nitems, int* counter,
@@ -107,9 +108,10 @@ int batch_variant(int L) { return L <= 128 ? 0 : 1; }
 size_t batch_dwt_smem(int L) { return sizeof(float) * 4 * (size_t)(batch_variant(L) == 0 ? 128 : 256); }
 
 void batch_build_items(const std::vector<BatchJob>& jobs, std::vector<BatchItem>& items, std::vector<int>& dwt_items,
-                       int drop_job) {
+                       int drop_job, int lag) {
     const size_t n = jobs.size();
-    std::vector<std::vector<BatchItem>> dw(n), tl(n);
+    std::vector<BatchItem> dw, tl;
+    std::vector<int64_t> left(n, 0);  // DWT items of a job not yet placed
     dwt_items.assign(n, 0);
     for (size_t j = 0; j < n; ++j) {
         const int64_t P = (int64_t)jobs[j].H * jobs[j].W;
@@ -118,24 +120,35 @@ void batch_build_items(const std::vector<BatchJob>& jobs, std::vector<BatchItem>
         for (int64_t g0 = 0; g0 < ngroups; g0 += kGroupsPerDwtItem) {
             dwt_items[j]++;
             if ((int)j == drop_job && !dropped) { dropped = true; continue; }  // fault injection (host only)
-            dw[j].push_back({(int)j, 0, (int)g0, (int)std::min<int64_t>(ngroups, g0 + kGroupsPerDwtItem)});
+            dw.push_back({(int)j, 0, (int)g0, (int)std::min<int64_t>(ngroups, g0 + kGroupsPerDwtItem)});
+            left[j]++;
         }
+    }
+    for (size_t j = 0; j < n; ++j) {
         const int tx = (jobs[j].W + 31) / 32, ty = (jobs[j].H + jobs[j].th - 1) / jobs[j].th;
         for (int y = 0; y < ty; ++y)
-            for (int x = 0; x < tx; ++x) tl[j].push_back({(int)j, 1, x, y});
+            for (int x = 0; x < tx; ++x) tl.push_back({(int)j, 1, x, y});
     }
-    // stage s: DWT items of job s interleaved (proportionally) with the tiles of job s - 1
+    // Merge the two streams in proportion to their lengths.  A tile of job j is placed only
+    // once every DWT item of job j is in the list and `lag` further items follow the last of
+    // them, so that by the time a CTA pops the tile the DWT item has most likely finished.
+    std::vector<int64_t> last(n, -(int64_t)1 << 40);
+    const size_t nd = dw.size(), nt = tl.size();
+    size_t ia = 0, ib = 0;
     items.clear();
-    static const std::vector<BatchItem> none;
-    for (size_t st = 0; st <= n; ++st) {
-        const std::vector<BatchItem>& A = st < n ? dw[st] : none;
-        const std::vector<BatchItem>& B = st > 0 ? tl[st - 1] : none;
-        const size_t a = A.size(), b = B.size();
-        size_t ia = 0, ib = 0;
-        while (ia < a || ib < b) {
-            if (ib >= b || (ia < a && ia * b <= ib * a)) items.push_back(A[ia++]);
-            else items.push_back(B[ib++]);
-        }
+    items.reserve(nd + nt);
+    auto put_dwt = [&]() {
+        const BatchItem it = dw[ia++];
+        if (--left[(size_t)it.job] == 0) last[(size_t)it.job] = (int64_t)items.size();
+        items.push_back(it);
+    };
+    while (ia < nd || ib < nt) {
+        const bool tile_turn = ib < nt && (ia >= nd || (double)ib * (double)nd <= (double)ia * (double)nt);
+        if (!tile_turn) { put_dwt(); continue; }
+        const size_t j = (size_t)tl[ib].job;
+        const bool ready = left[j] == 0 && (int64_t)items.size() >= last[j] + lag;
+        if (!ready && ia < nd) { put_dwt(); continue; }
+        items.push_back(tl[ib++]);
     }
 }
 

@@ -31,9 +31,10 @@ int batch_variant(int L);
 // shared memory a DWT item needs (the job's DWT matrix, zero-padded rows)
 size_t batch_dwt_smem(int L);
 // drop_job >= 0 removes that job's first DWT item from the list (host-side fault injection
-// for tests of the bounded wait); -1 in normal use.
+// for tests of the bounded wait); -1 in normal use.  lag: items placed between a job's last
+// DWT item and its first tile (when DWT items remain to fill the gap).
 void batch_build_items(const std::vector<BatchJob>& jobs, std::vector<BatchItem>& items, std::vector<int>& dwt_items,
-                       int drop_job);
+                       int drop_job, int lag);
 cudaError_t batch_launch(const BatchJob* d_jobs, const BatchItem* d_items, int nitems, int* d_counters, int njobs,
                          size_t smem, int num_sms, cudaStream_t s);
 

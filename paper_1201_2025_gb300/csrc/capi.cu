@@ -590,7 +590,7 @@ wdad_status wdad_batch_create(wdad_handle h, int n, const wdad_job* jobs, int au
         if (const char* e = std::getenv("WDAD_FAULT_DROP_DWT_ITEM")) drop = std::atoi(e);
         std::vector<wdad::BatchItem> items;
         std::vector<int> dwt_items;
-        wdad::batch_build_items(hj, items, dwt_items, drop);
+        wdad::batch_build_items(hj, items, dwt_items, drop, 4 * 2 * h->num_sms);
         b = new wdad_batch_ctx();
         b->h = h;
         b->n = n;
