@@ -58,12 +58,14 @@ static int spec_nc(int D) { return D + D * (D + 1) / 2; }
 static int spec_dp(int D) { return D <= 4 ? 4 : 8; }
 
 size_t detect_small_smem(int D, int inner, int outer, int tile_h) {
-    return smem_bytes(spec_dp(D), spec_nc(D), 4, inner, outer, tile_h);
+    return smem_bytes(spec_dp(D), spec_nc(D), 4, inner, outer, tile_h) + sizeof(float) * (16 * 8 + 8);
 }
 
 // Tallest tile (<= want) that lets two CTAs share an SM; else the tallest that fits one.
+// Two CTAs fit when each takes at most half of the SM's 228 KiB, less the 1 KiB the runtime
+// reserves per CTA and 128 B for the kernels' own static shared variables.
 static int pick_th(int D, int inner, int outer, int want) {
-    constexpr size_t kTwoPerSm = 113 * 1024;
+    constexpr size_t kTwoPerSm = 228 * 1024 / 2 - 1024 - 128;
     for (int th = want; th >= 8; th >>= 1)
         if (detect_small_smem(D, inner, outer, th) <= kTwoPerSm) return th;
     for (int th = want; th >= 1; th >>= 1)

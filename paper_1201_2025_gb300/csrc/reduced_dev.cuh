@@ -406,8 +406,10 @@ __device__ void detect_tile(const DetectArgs& a, int th, int tile_x, int tile_y,
     float* xs = reinterpret_cast<float*>(smem_raw);
     float* hso = xs + (size_t)g.HR * g.XP * P::DP;
     float* hsi = hso + (size_t)NC * g.HR * HP;
-    __shared__ float cref[8];
-    __shared__ float red[16][8];
+    // tile-mean scratch after the inner sums (in the dynamic buffer, not static shared
+    // memory, so that a kernel holding several instantiations keeps its static size small)
+    float* red = hsi + (size_t)NC * g.nin * HP;  // [16][8]
+    float* cref = red + 16 * 8;                  // [8]
 
     // stage 0 + tile reference: the mean of the halo region, as 16 fixed partial sums (halo
     // rows r = v mod 16) combined in a fixed order, whatever the block size
@@ -430,13 +432,13 @@ __device__ void detect_tile(const DetectArgs& a, int th, int tile_x, int tile_y,
             float t = acc[k];
 #pragma unroll
             for (int o = 16; o >= 1; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-            if (lane == 0) red[v][k] = t;
+            if (lane == 0) red[v * 8 + k] = t;
         }
     }
     __syncthreads();
     if (threadIdx.x < D) {
         float t = 0.f;
-        for (int v = 0; v < 16; ++v) t += red[v][threadIdx.x];
+        for (int v = 0; v < 16; ++v) t += red[v * 8 + threadIdx.x];
         cref[threadIdx.x] = t / (float)(g.HR * g.WR);
     }
     __syncthreads();
