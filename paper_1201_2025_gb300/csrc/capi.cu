@@ -239,8 +239,11 @@ __global__ void fill_pattern_kernel(float* x, int64_t n) {
 }
 
 // Time every feasible tile height on a synthetic 256 x 256 x D cube and keep the fastest.
-wdad_status autotune(wdad_ctx* h, int D, int inner, int outer, int* out, cudaStream_t s) {
-    const long long key = tune_key(D, inner, outer);
+// Fastest tile height for D bands and a window, timed on a 256 x 256 pattern.  two_per_sm:
+// only plans that keep two CTAs on an SM (the batch kernel shares one plan size across all
+// of its jobs, so a taller tile for one job would halve the occupancy of the whole batch).
+wdad_status autotune(wdad_ctx* h, int D, int inner, int outer, int* out, cudaStream_t s, bool two_per_sm = false) {
+    const long long key = tune_key(D, inner, outer) * 2 + (two_per_sm ? 1 : 0);
     auto it = h->tuned.find(key);
     if (it != h->tuned.end()) { *out = it->second; return WDAD_OK; }
     const int S = 256;
@@ -262,7 +265,8 @@ wdad_status autotune(wdad_ctx* h, int D, int inner, int outer, int* out, cudaStr
     // sliding box sums restart every th rows; th <= 16 keeps the FP32 error at the level the
     // parity tests pin
     for (int th : {16, 8, 4, 2}) {
-        if (wdad::detect_small_smem(D, inner, outer, th) > 227 * 1024) continue;
+        const size_t need = wdad::detect_small_smem(D, inner, outer, th);
+        if (need > 227 * 1024 || (two_per_sm && need > wdad::detect_small_two_per_sm_bytes())) continue;
         if (wdad::launch_detect_small_th(a, th, s) != cudaSuccess) { cudaGetLastError(); continue; }
         cudaEventRecord(e0, s);
         for (int r = 0; r < 3; ++r) wdad::launch_detect_small_th(a, th, s);
@@ -274,6 +278,7 @@ wdad_status autotune(wdad_ctx* h, int D, int inner, int outer, int* out, cudaStr
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (best == 0 && two_per_sm) return autotune(h, D, inner, outer, out, s, false);
     if (best == 0) return fail(h, WDAD_ERR_UNSUPPORTED, "no tile height fits window %d/%d for %d bands", inner, outer, D);
     h->tuned[key] = best;
     *out = best;
@@ -566,7 +571,7 @@ wdad_status wdad_batch_create(wdad_handle h, int n, const wdad_job* jobs, int au
             if (st != WDAD_OK) return st;
             int th = wdad::detect_small_default_th(K, j.params.inner, j.params.outer);
             if (autotune_plans) {
-                st = autotune(h, K, j.params.inner, j.params.outer, &th, s);
+                st = autotune(h, K, j.params.inner, j.params.outer, &th, s, true);
                 if (st != WDAD_OK) return st;
             }
             if (th < 1) return fail(h, WDAD_ERR_UNSUPPORTED, "batch job %d: window too large", i);

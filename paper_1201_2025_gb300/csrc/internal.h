@@ -57,6 +57,8 @@ cudaError_t launch_detect_small(const DetectArgs& a, int tile_h, cudaStream_t s)
 // exact tile height (the plan); default plan of a configuration
 cudaError_t launch_detect_small_th(const DetectArgs& a, int th, cudaStream_t s);
 int detect_small_default_th(int D, int inner, int outer);
+// largest dynamic shared memory of a detector tile plan that still lets two CTAs share an SM
+size_t detect_small_two_per_sm_bytes();
 cudaError_t launch_window_census(int H, int W, int inner, int outer, int border, int64_t* out,
                                  cudaStream_t s);
 size_t detect_small_smem(int D, int inner, int outer, int tile_h);

@@ -64,8 +64,10 @@ size_t detect_small_smem(int D, int inner, int outer, int tile_h) {
 // Tallest tile (<= want) that lets two CTAs share an SM; else the tallest that fits one.
 // Two CTAs fit when each takes at most half of the SM's 228 KiB, less the 1 KiB the runtime
 // reserves per CTA and 128 B for the kernels' own static shared variables.
+constexpr size_t kTwoPerSm = 228 * 1024 / 2 - 1024 - 128;
+size_t detect_small_two_per_sm_bytes() { return kTwoPerSm; }
+
 static int pick_th(int D, int inner, int outer, int want) {
-    constexpr size_t kTwoPerSm = 228 * 1024 / 2 - 1024 - 128;
     for (int th = want; th >= 8; th >>= 1)
         if (detect_small_smem(D, inner, outer, th) <= kTwoPerSm) return th;
     for (int th = want; th >= 1; th >>= 1)
