@@ -501,6 +501,47 @@ def run_ours(args):
     }), flush=True)
 
 
+def run_profile_case(case: str):
+    """Small workloads for ncu captures of kernels outside the timed step (a few GB at most):
+    batch (8 cubes, side <= 512), screen (1024x1024x224 screening pass), mixed (64x64x224 AR(1)
+    full-band LRX, MIXED then FP32).  Each runs its workload twice and exits."""
+    import torch
+    from paper_1201_2025_gb300 import synth, wdad
+    dev = torch.device("cuda", 0)
+    if case == "batch":
+        jobs = []
+        for sp in synth.batch_specs(8, seed=0):
+            S = min(sp["H"], 512)
+            cube, _ = synth.make_scene_device(S, S, sp["L"], seed=sp["seed"], n_anom=20, anom_side=(1, 3),
+                                              abundance=(0.1, 0.5), margin=10, device=dev)
+            jobs.append(dict(cube=cube, detector=sp["detector"], scores=torch.empty((S, S), device=dev),
+                             over=dict(inner=sp["inner"], outer=sp["outer"])))
+        b = wdad.wdad_batch(jobs, autotune=False, use_graph=True)
+        for _ in range(2):
+            b.launch()
+        st, _ = b.status()
+        b.close()
+        if st != 0:
+            raise SystemExit(f"batch status {st}")
+    elif case == "screen":
+        net = wdad.wdad_cnn(K=4, seed=1)
+        cube, _ = synth.make_scene_device(1024, 1024, L, seed=5, n_anom=800, anom_side=(1, 3), abundance=(0.1, 0.5),
+                                          margin=10, device=dev)
+        for _ in range(2):
+            wdad.wdad_screen_run(net, cube, top_frac=0.02, audit_frac=0.005, seed=1, tile_rows=256, exact_reduce=True,
+                                 inner=5, outer=15)
+        net.close()
+    elif case == "mixed":
+        sc = synth.make_scene(64, 64, L, seed=7, n_anom=10, anom_side=(1, 3), abundance=(0.1, 0.5), margin=6,
+                              ar_rho=0.98)
+        x = torch.from_numpy(sc.cube).to(dev)
+        for _ in range(2):
+            wdad.wdad_detect(x, 0, reduce=False, inner=3, outer=11, precision=1, cond_gate=1e6)
+            wdad.wdad_detect(x, 0, reduce=False, inner=3, outer=11, precision=0)
+    torch.cuda.synchronize()
+    print("profile case", case, "ok")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -518,8 +559,12 @@ def main():
     ap.add_argument("--no-screen", action="store_true")
     ap.add_argument("--screen-train-cubes", type=int, default=200)
     ap.add_argument("--screen-train-steps", type=int, default=2000)
+    ap.add_argument("--profile-case", choices=["batch", "screen", "mixed"], default=None,
+                    help="run one small workload for an ncu capture and exit")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.profile_case:
+        run_profile_case(args.profile_case)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
