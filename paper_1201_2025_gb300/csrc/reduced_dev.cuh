@@ -249,9 +249,11 @@ __device__ __forceinline__ void vertical_sums_inplace(const TileGeom& g, typenam
 }
 
 // ---------------------------------------------------------------- small dense algebra in registers
-// Fails when a pivot is not above `floor` (a multiple of the FP32 rounding level of
-// the moments the matrix was formed from), so exactly singular covariances are
-// reported instead of factorised from rounding noise.
+// Cholesky G = L L^T in place: the strict lower triangle receives L and the diagonal the
+// reciprocal pivots 1 / L_jj (one rsqrtf each, so the solves multiply instead of divide).
+// Fails when a pivot is not above `floor` (a multiple of the FP32 rounding level of the
+// moments the matrix was formed from), so exactly singular covariances are reported instead
+// of factorised from rounding noise.
 template <int D>
 __device__ __forceinline__ bool chol_inplace(float (&G)[D][D], float floor) {
 #pragma unroll
@@ -260,8 +262,8 @@ __device__ __forceinline__ bool chol_inplace(float (&G)[D][D], float floor) {
 #pragma unroll
         for (int k = 0; k < j; ++k) s = fmaf(-G[j][k], G[j][k], s);
         if (!(s > floor)) return false;
-        const float gjj = sqrtf(s), inv = 1.0f / gjj;
-        G[j][j] = gjj;
+        const float inv = rsqrtf(s);
+        G[j][j] = inv;
 #pragma unroll
         for (int i = j + 1; i < D; ++i) {
             float t = G[i][j];
@@ -273,7 +275,7 @@ __device__ __forceinline__ bool chol_inplace(float (&G)[D][D], float floor) {
     return true;
 }
 
-// ||G^{-1} d||^2 = d^T (G G^T)^{-1} d
+// ||L^{-1} d||^2 = d^T (L L^T)^{-1} d for the factor chol_inplace leaves in G
 template <int D>
 __device__ __forceinline__ float chol_quad(const float (&G)[D][D], const float (&d)[D]) {
     float y[D];
@@ -283,7 +285,7 @@ __device__ __forceinline__ float chol_quad(const float (&G)[D][D], const float (
         float t = d[i];
 #pragma unroll
         for (int k = 0; k < i; ++k) t = fmaf(-G[i][k], y[k], t);
-        y[i] = t / G[i][i];
+        y[i] = t * G[i][i];
         q = fmaf(y[i], y[i], q);
     }
     return q;
@@ -301,10 +303,11 @@ __host__ __device__ constexpr int rr_second(int E, int r, int k) {
 // Golub & Van Loan Sec. 8.5; the round-robin ordering lets the rotations of one
 // round, which act on disjoint index pairs, be computed and applied together).
 // Each rotation zeroes a_pq and moves a_pp, a_qq by -/+ t a_pq; the blocks between
-// two pairs transform as R_i^T B R_j.  Entries at or below the FP32 rounding level of
-// the matrix (2^-22 ||A||_F) are left alone; sweeps end with the first sweep that
-// rotates nothing.  On return A's diagonal holds the eigenvalues, V's columns the
-// eigenvectors.
+// two pairs transform as R_i^T B R_j.  A is first scaled to unit Frobenius norm, so every
+// rotation's operands stay normal whatever the data's scale.  Entries at or below the FP32
+// rounding level (2^-22 of the norm) are left alone; sweeps end with the first sweep that
+// rotates nothing.  On return A's diagonal holds the eigenvalues divided by ||A||_F (their
+// signs and ratios, which is all the DWEST selection uses), V's columns the eigenvectors.
 template <int D>
 __device__ __forceinline__ void jacobi_inplace(float (&A)[D][D], float (&V)[D][D]) {
     constexpr int E = D + (D & 1);
@@ -319,7 +322,13 @@ __device__ __forceinline__ void jacobi_inplace(float (&A)[D][D], float (&V)[D][D
     for (int a = 0; a < D; ++a)
 #pragma unroll
         for (int b = 0; b < D; ++b) fro = fmaf(A[a][b], A[a][b], fro);
-    const float tol = 2.384185791e-7f * sqrtf(fro);  // 2^-22 ||A||_F
+    if (!(fro > 0.f)) return;  // zero matrix: already diagonal (NaN input stays NaN)
+    const float unit = rsqrtf(fro);
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = 0; b < D; ++b) A[a][b] *= unit;
+    const float tol = 2.384185791e-7f;  // 2^-22 of the (unit) norm
     constexpr int kSweeps = (D <= 4) ? 8 : 12;
     for (int sweep = 0; sweep < kSweeps; ++sweep) {
         bool rotated = false;
@@ -336,8 +345,15 @@ __device__ __forceinline__ void jacobi_inplace(float (&A)[D][D], float (&V)[D][D
                 const float apq = A[p][q];
                 if (!(fabsf(apq) > tol)) continue;
                 rotated = true;
-                const float theta = (A[q][q] - A[p][p]) * __frcp_rn(2.f * apq);
-                const float t = copysignf(__frcp_rn(fabsf(theta) + sqrtf(fmaf(theta, theta, 1.f))), theta);
+                // t = sgn(theta) / (|theta| + sqrt(theta^2 + 1)) with theta = dq / h, dq = a_qq - a_pp,
+                // h = 2 a_pq, written as sgn(dq) h / (|dq| + sqrt(dq^2 + h^2)): one rsqrtf and one
+                // approximate division.  c^2 + s^2 = 1 holds to the rsqrtf error, and an inexact
+                // angle only changes how much of a_pq the next sweeps still have to remove.
+                const float dq = A[q][q] - A[p][p], h = 2.f * apq;
+                const float ss = fmaf(dq, dq, h * h);
+                const float r = ss * rsqrtf(ss);
+                const float tt = __fdividef(h, fabsf(dq) + r);
+                const float t = (dq < 0.f) ? -tt : tt;
                 c[k] = rsqrtf(fmaf(t, t, 1.f));
                 sn[k] = t * c[k];
                 A[p][p] = fmaf(-t, apq, A[p][p]);
