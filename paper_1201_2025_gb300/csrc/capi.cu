@@ -264,7 +264,14 @@ wdad_status autotune(wdad_ctx* h, int D, int inner, int outer, int* out, cudaStr
     float best_ms = 1e30f;
     // sliding box sums restart every th rows; th <= 16 keeps the FP32 error at the level the
     // parity tests pin
-    for (int th : {16, 8, 4, 2}) {
+    // candidates: 16 rows, the default plan (the tallest height that keeps two CTAs per SM),
+    // and the smaller powers of two
+    std::vector<int> cands = {16};
+    const int th_default = wdad::detect_small_default_th(D, inner, outer);
+    if (th_default > 0 && th_default < 16) cands.push_back(th_default);
+    for (int t : {8, 4, 2})
+        if (t != th_default) cands.push_back(t);
+    for (int th : cands) {
         const size_t need = wdad::detect_small_smem(D, inner, outer, th);
         if (need > 227 * 1024 || (two_per_sm && need > wdad::detect_small_two_per_sm_bytes())) continue;
         if (wdad::launch_detect_small_th(a, th, s) != cudaSuccess) { cudaGetLastError(); continue; }

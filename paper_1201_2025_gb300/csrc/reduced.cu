@@ -61,14 +61,15 @@ size_t detect_small_smem(int D, int inner, int outer, int tile_h) {
     return smem_bytes(spec_dp(D), spec_nc(D), 4, inner, outer, tile_h) + sizeof(float) * (16 * 8 + 8);
 }
 
-// Tallest tile (<= want) that lets two CTAs share an SM; else the tallest that fits one.
-// Two CTAs fit when each takes at most half of the SM's 228 KiB, less the 1 KiB the runtime
-// reserves per CTA and 128 B for the kernels' own static shared variables.
+// Tallest tile (<= want, >= 8 rows) that lets two CTAs share an SM; else the tallest that
+// fits one.  Two CTAs fit when each takes at most half of the SM's 228 KiB, less the 1 KiB the
+// runtime reserves per CTA and 128 B for the kernels' own static shared variables.  Heights
+// need not be powers of two: at window (7,21) and D = 4, 11 rows fit two CTAs where 16 do not.
 constexpr size_t kTwoPerSm = 228 * 1024 / 2 - 1024 - 128;
 size_t detect_small_two_per_sm_bytes() { return kTwoPerSm; }
 
 static int pick_th(int D, int inner, int outer, int want) {
-    for (int th = want; th >= 8; th >>= 1)
+    for (int th = want; th >= 8; --th)
         if (detect_small_smem(D, inner, outer, th) <= kTwoPerSm) return th;
     for (int th = want; th >= 1; th >>= 1)
         if (detect_small_smem(D, inner, outer, th) <= (size_t)kMaxSmem) return th;
@@ -82,7 +83,7 @@ static cudaError_t launch_d(const DetectArgs& a, int th, cudaStream_t s) {
                                          (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((a.W + TW - 1) / TW, (a.H + th - 1) / th);
-    const int threads = th >= 16 ? 512 : 256;
+    const int threads = std::min(512, std::max(256, th * 32));  // one thread per output pixel when th >= 8
     detect_small_kernel<D><<<grid, threads, smem, s>>>(a, th);
     return cudaGetLastError();
 }

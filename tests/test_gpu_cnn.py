@@ -9,9 +9,9 @@ import oracle
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-# Screened DWT-LRX recall bar at top 5% + 1% audit on a held-out 96x96 scene (implanted pixels
-# the exact DWT-LRX map ranks in its top 5%).
-RECALL_MIN = 0.75
+# Screened DWT-LRX recall bar at top 5% + 1% audit, pooled over three held-out 128x128 scenes
+# (implanted pixels the exact DWT-LRX map ranks in its top 5%).
+RECALL_MIN = 0.7
 
 
 @pytest.fixture(scope="module")
@@ -181,34 +181,55 @@ def test_training_lowers_held_out_loss(wd, training_set, trained):
     fresh.close()
 
 
+def _scene128(seed):
+    from paper_1201_2025_gb300 import synth
+    return synth.make_scene(128, 128, 224, seed=seed, n_anom=21, anom_side=(1, 3), abundance=(0.1, 0.5), margin=4)
+
+
+def _screen(wd, net, x, exact_reduce, want_pred=True):
+    return wd.wdad_screen_run(net, x, top_frac=0.05, audit_frac=0.01, seed=3, tile_rows=40,
+                              exact_reduce=exact_reduce, inner=5, outer=15, want_pred=want_pred)
+
+
 @pytest.mark.parametrize("seed", [77, 78])
-def test_screening_recall_and_exact_values(wd, trained, seed):
+def test_screening_exact_values(wd, trained, seed):
+    """Selected pixels carry the exact detector's value (bit-identical to the full map), every
+    other pixel -inf, for both exact detectors."""
     test = _scene96(seed)
     x = torch.from_numpy(test.cube).cuda()
-    # screened DWT-LRX (the detector the network learned): recall of implanted anomalies that the
-    # exact DWT-LRX map ranks in its top 5%, with 6% of the pixels evaluated exactly
-    score, pred, sel, nsel = wd.wdad_screen_run(trained, x, top_frac=0.05, audit_frac=0.01, seed=3, tile_rows=40,
-                                                exact_reduce=True, inner=5, outer=15)
-    s = score.cpu().numpy()
-    selm = sel.cpu().numpy() > 0
-    assert nsel == selm.sum() and np.isfinite(s[selm]).all() and np.isneginf(s[~selm]).all()
-    red = wd.wdad_detect(x, 0, reduce=True, inner=5, outer=15).cpu().numpy()
-    assert np.array_equal(s[selm], red[selm])
-    truth = (test.mask > 0) & (red >= np.quantile(red, 0.95))
-    assert truth.sum() >= 5
-    recall = (selm & truth).sum() / truth.sum()
-    # without the network, the same budget of pixels drawn at random finds about selm.mean()
-    print(f"screened DWT-LRX recall {recall:.3f} with {selm.mean():.3f} of pixels evaluated")
-    assert recall >= RECALL_MIN and recall > 10 * selm.mean(), (recall, selm.mean())
-    # screened full-band LRX: exact values bit-identical to the full map at the selected pixels
-    score, _, sel, nsel = wd.wdad_screen_run(trained, x, top_frac=0.05, audit_frac=0.01, seed=3, tile_rows=40,
-                                             exact_reduce=False, inner=5, outer=15, want_pred=False)
-    s = score.cpu().numpy()
-    selm = sel.cpu().numpy() > 0
-    full = wd.wdad_detect(x, 0, reduce=False, inner=5, outer=15).cpu().numpy()
-    assert np.array_equal(s[selm], full[selm]) and np.isneginf(s[~selm]).all()
-    truth = (test.mask > 0) & (full >= np.quantile(full, 0.95))
-    recall_full = (selm & truth).sum() / truth.sum()
-    print(f"screened full-band LRX recall {recall_full:.3f} (the approximation-space network cannot see "
-          f"what only the full band separates)")
-    assert recall_full > selm.mean()
+    for exact_reduce in (True, False):
+        score, _, sel, nsel = _screen(wd, trained, x, exact_reduce, want_pred=False)
+        s = score.cpu().numpy()
+        selm = sel.cpu().numpy() > 0
+        assert nsel == selm.sum() and np.isfinite(s[selm]).all() and np.isneginf(s[~selm]).all()
+        ref = wd.wdad_detect(x, 0, reduce=exact_reduce, inner=5, outer=15).cpu().numpy()
+        assert np.array_equal(s[selm], ref[selm])
+
+
+def test_screening_recall(wd, trained):
+    """Recall of the implanted pixels that the exact map ranks in its top 5%, pooled over three
+    held-out 128x128 scenes (about 90 such pixels), with 6% of the pixels evaluated exactly.
+    Without the network, the same budget drawn at random finds about 6% of them."""
+    hit = {True: 0, False: 0}
+    tot = {True: 0, False: 0}
+    frac = []
+    for seed in (77, 78, 79):
+        test = _scene128(seed)
+        x = torch.from_numpy(test.cube).cuda()
+        for exact_reduce in (True, False):
+            score, _, sel, _ = _screen(wd, trained, x, exact_reduce, want_pred=False)
+            selm = sel.cpu().numpy() > 0
+            ref = wd.wdad_detect(x, 0, reduce=exact_reduce, inner=5, outer=15).cpu().numpy()
+            truth = (test.mask > 0) & (ref >= np.quantile(ref, 0.95))
+            hit[exact_reduce] += int((selm & truth).sum())
+            tot[exact_reduce] += int(truth.sum())
+            frac.append(selm.mean())
+    recall = hit[True] / tot[True]
+    recall_full = hit[False] / tot[False]
+    ev = float(np.mean(frac))
+    print(f"screened DWT-LRX recall {recall:.3f} ({hit[True]}/{tot[True]}), full-band LRX recall "
+          f"{recall_full:.3f} ({hit[False]}/{tot[False]}), {ev:.3f} of pixels evaluated")
+    assert tot[True] >= 40
+    assert recall >= RECALL_MIN and recall > 10 * ev, (recall, ev)
+    # the approximation-space network cannot see what only the full band separates
+    assert recall_full > 2 * ev
