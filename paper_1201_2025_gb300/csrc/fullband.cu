@@ -6,8 +6,8 @@
 // centred Gram  sum (x - mu)(x - mu)^T  accumulated into a symmetric matrix stored
 // as 4x4 tiles of its lower triangle ("tile-packed").
 //   LRX / DWRX (Eq. 1, 5): C_o + delta I, delta = loading * trace(C_o) / D, blocked
-//     Cholesky on the tiles, one forward solve for the two right-hand sides
-//     r - mu_o and mu_i - mu_o, score = ||L^-1 d||^2.
+//     Cholesky on the tiles bordered by the two right-hand sides r - mu_o and
+//     mu_i - mu_o (so it also yields L^-1 d), score = ||L^-1 d||^2.
 //   DWEST (Eq. 2-4): C_diff = C_i - C_o; Householder tridiagonalisation; the
 //     eigenvalues above tau = dwest_tau * max|lambda| by Sturm-count bisection (a
 //     warp evaluates 32 points per step); their eigenvectors by inverse iteration on
@@ -149,23 +149,49 @@ __host__ __device__ inline size_t fb_smem_vectors_bytes(int Dp, int S, int mcap)
 constexpr size_t kTcBufBytes = 2 * 256 * 64 * 2;  // two BF16 chunk buffers (TC_MB x TC_KC)
 
 // ---- statistics ---------------------------------------------------------------
-// mean over a sample list (kind 0 = background, 1 = inner) into out[0..Dp)
+// mean over a sample list (kind 0 = background, 1 = inner) into out[0..Dp).  The samples
+// are split into G interleaved groups (G threads per band, G <= S so that the partial sums
+// fit the sample-chunk buffer `part`); each thread keeps four loads in flight, and the G
+// partial sums of a band are added in group order.  Ends with a barrier.
 template <typename T>
-__device__ void sample_mean(const float* __restrict__ x, int H, int W, int D, int Dp, int py, int px, int kind,
-                            int n, int ro, int ri, T* out) {
-    for (int b = threadIdx.x; b < Dp; b += FB_THREADS) {
-        T acc = T(0);
+__device__ void sample_mean(const float* __restrict__ x, int H, int W, const Geo& g, int py, int px, int kind,
+                            int n, int ro, int ri, T* out, T* part) {
+    const int D = g.D, Dp = g.Dp;
+    const int G = max(1, min(FB_THREADS / Dp, g.S));
+    __syncthreads();  // part may still be read by a previous call
+    for (int t = threadIdx.x; t < G * Dp; t += FB_THREADS) {
+        const int grp = t / Dp, b = t - grp * Dp;
+        T acc[4] = {T(0), T(0), T(0), T(0)};
         if (b < D) {
-            for (int s = 0; s < n; ++s) {
+            int s = grp;
+            for (; s + 3 * G < n; s += 4 * G) {
+                float v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    int dy, dx;
+                    if (kind == 0) bg_offset(s + u * G, ro, ri, dy, dx); else in_offset(s + u * G, ri, dy, dx);
+                    const size_t q = (size_t)reflect101(py + dy, H) * W + reflect101(px + dx, W);
+                    v[u] = __ldg(x + q * D + b);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc[u] += (T)v[u];
+            }
+            for (; s < n; s += G) {
                 int dy, dx;
                 if (kind == 0) bg_offset(s, ro, ri, dy, dx); else in_offset(s, ri, dy, dx);
                 const size_t q = (size_t)reflect101(py + dy, H) * W + reflect101(px + dx, W);
-                acc += (T)__ldg(x + q * D + b);
+                acc[0] += (T)__ldg(x + q * D + b);
             }
-            acc /= (T)n;
         }
-        out[b] = acc;
+        part[t] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
     }
+    __syncthreads();
+    for (int b = threadIdx.x; b < Dp; b += FB_THREADS) {
+        T sum = T(0);
+        for (int gi = 0; gi < G; ++gi) sum += part[gi * Dp + b];
+        out[b] = b < D ? sum / (T)n : T(0);
+    }
+    __syncthreads();
 }
 
 // A += sum over samples of (sc (x - mu)) (sc (x - mu))^T, tile by tile, S samples per chunk
@@ -336,111 +362,132 @@ __device__ void mat_scale(T* A, const Geo& g, T s) {
     __syncthreads();
 }
 
-// ---- blocked Cholesky on the tiles (padding rows are identity).  Returns false if a
-// pivot is not above `floor`.
+// ---- blocked Cholesky of the tile-packed matrix, bordered by the two right-hand sides.
+// Right-looking in steps of NB = 32 columns (8 tile columns): (1) one warp factors the
+// 32 x 32 diagonal block in registers, lane i holding row i (the column of L that each step
+// needs comes by shuffles); (2) one thread per row below the block, and one for each
+// right-hand side, solves X = A_panel L_kk^-T (the rows of the block in registers, L_kk read
+// as shared-memory broadcasts); (3) the trailing tiles take A_IK -= sum_J A_IJ A_KJ^T over the
+// block's tile columns J, and the right-hand sides y -= X_b X^T.  The right-hand sides behave
+// as two extra rows appended below the matrix, so on return y1 = L^-1 r1 and y2 = L^-1 r2 and
+// no separate solve is needed.  Padding rows (D <= b < Dp) are identity.  Returns false,
+// leaving *flag = 1, if a pivot is not above `floor`; L_ii stays on the diagonal.
+constexpr int NB = 32;
+
 template <typename T>
-__device__ bool cholesky_tiles(T* A, const Geo& g, T floor, int* flag) {
-    const int ntl = g.ntl;
+__device__ bool cholesky_bordered(T* A, const Geo& g, T floor, int* flag, T* y1, T* y2, T* invd) {
+    const int ntl = g.ntl, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) *flag = 0;
     for (int b = g.D + threadIdx.x; b < g.Dp; b += FB_THREADS) el(A, ntl, b, b) = T(1);
     __syncthreads();
-    for (int J = 0; J < g.nt; ++J) {
-        if (threadIdx.x == 0) {
-            T t[16];
-            const int u = tile_idx(J, J);
-            tile_load(A, ntl, u, t);
+    for (int c0 = 0; c0 < g.Dp; c0 += NB) {
+        const int nb = min(NB, g.Dp - c0);  // a multiple of 4
+        // (1) diagonal block
+        if (warp == 0) {
+            T a[NB];
+#pragma unroll
+            for (int c = 0; c < NB; ++c)
+                a[c] = (lane < nb && c <= lane) ? el(A, ntl, c0 + lane, c0 + c) : T(0);
             bool ok = true;
-            for (int j = 0; j < 4 && ok; ++j) {
-                T s = t[j * 4 + j];
-                for (int k = 0; k < j; ++k) s -= t[j * 4 + k] * t[j * 4 + k];
-                if (!(s > floor)) { ok = false; break; }
-                const T l = Num<T>::sqrt_(s);
-                t[j * 4 + j] = l;
-                for (int i = j + 1; i < 4; ++i) {
-                    T v = t[i * 4 + j];
-                    for (int k = 0; k < j; ++k) v -= t[i * 4 + k] * t[j * 4 + k];
-                    t[i * 4 + j] = v / l;
+#pragma unroll
+            for (int j = 0; j < NB; ++j) {
+                const T d = __shfl_sync(0xffffffffu, a[j], j);
+                if (j < nb && ok) {  // warp-uniform
+                    if (!(d > floor)) ok = false;
+                }
+                if (j < nb && ok) {
+                    const T l = Num<T>::sqrt_(d), inv = T(1) / l;
+                    if (lane == j) { a[j] = l; invd[j] = inv; }
+                    else if (lane > j) a[j] *= inv;
+                    const T lij = a[j];
+#pragma unroll
+                    for (int c = j + 1; c < NB; ++c) {
+                        const T lcj = __shfl_sync(0xffffffffu, a[j], c);
+                        if (lane >= c) a[c] -= lij * lcj;
+                    }
                 }
             }
-            tile_store(A, ntl, u, t);
-            if (!ok) *flag = 1;
+            if (ok) {
+#pragma unroll
+                for (int c = 0; c < NB; ++c)
+                    if (lane < nb && c <= lane) el(A, ntl, c0 + lane, c0 + c) = a[c];
+            } else if (lane == 0) {
+                *flag = 1;
+            }
         }
         __syncthreads();
         if (*flag) return false;
-        // panel: A_IJ <- A_IJ L_JJ^-T
-        for (int I = J + 1 + threadIdx.x; I < g.nt; I += FB_THREADS) {
-            T l[16], b[16];
-            tile_load(A, ntl, tile_idx(J, J), l);
-            tile_load(A, ntl, tile_idx(I, J), b);
+        // (2) panel rows and the two right-hand sides
+        const int r0 = c0 + nb, nrows = g.Dp - r0;
+        for (int t = threadIdx.x; t < nrows + 2; t += FB_THREADS) {
+            T x[NB];
+            T* yv = t == nrows ? y1 : y2;
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
+            for (int c = 0; c < NB; ++c)
+                x[c] = c < nb ? (t < nrows ? el(A, ntl, r0 + t, c0 + c) : yv[c0 + c]) : T(0);
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    T v = b[r * 4 + c];
+            for (int c = 0; c < NB; ++c) {
+                if (c < nb) {
+                    T v = x[c];
 #pragma unroll
-                    for (int k = 0; k < c; ++k) v -= b[r * 4 + k] * l[c * 4 + k];
-                    b[r * 4 + c] = v / l[c * 4 + c];
+                    for (int k = 0; k < c; ++k) v -= x[k] * el(A, ntl, c0 + c, c0 + k);
+                    x[c] = v * invd[c];
                 }
-            tile_store(A, ntl, tile_idx(I, J), b);
+            }
+#pragma unroll
+            for (int c = 0; c < NB; ++c)
+                if (c < nb) {
+                    if (t < nrows) el(A, ntl, r0 + t, c0 + c) = x[c];
+                    else yv[c0 + c] = x[c];
+                }
         }
         __syncthreads();
-        // trailing: A_IK -= A_IJ A_KJ^T, I >= K > J
-        const int m = g.nt - J - 1;
-        for (int u = threadIdx.x; u < ntiles_of(m); u += FB_THREADS) {
-            int i2, k2;
-            tri_rc(u, i2, k2);
-            const int I = J + 1 + i2, K = J + 1 + k2;
-            T av[16], bv[16], c[16];
-            tile_load(A, ntl, tile_idx(I, J), av);
-            tile_load(A, ntl, tile_idx(K, J), bv);
-            const int uc = tile_idx(I, K);
-            tile_load(A, ntl, uc, c);
+        // (3) trailing tiles and right-hand sides
+        const int T0 = r0 / 4, m = g.nt - T0, J0 = c0 / 4, nJ = nb / 4;
+        const int ntri = ntiles_of(m);
+        for (int u = threadIdx.x; u < ntri + 2 * m; u += FB_THREADS) {
+            if (u < ntri) {
+                int i2, k2;
+                tri_rc(u, i2, k2);
+                const int I = T0 + i2, K = T0 + k2, uc = tile_idx(I, K);
+                T acc[16];
+                tile_load(A, ntl, uc, acc);
+                for (int J = J0; J < J0 + nJ; ++J) {
+                    T av[16], bv[16];
+                    tile_load(A, ntl, tile_idx(I, J), av);
+                    tile_load(A, ntl, tile_idx(K, J), bv);
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
+                    for (int rr = 0; rr < 4; ++rr)
 #pragma unroll
-                for (int cc = 0; cc < 4; ++cc) {
-                    T v = c[r * 4 + cc];
+                        for (int cc = 0; cc < 4; ++cc) {
+                            T v = acc[rr * 4 + cc];
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) v -= av[r * 4 + k] * bv[cc * 4 + k];
-                    c[r * 4 + cc] = v;
+                            for (int k = 0; k < 4; ++k) v -= av[rr * 4 + k] * bv[cc * 4 + k];
+                            acc[rr * 4 + cc] = v;
+                        }
                 }
-            tile_store(A, ntl, uc, c);
+                tile_store(A, ntl, uc, acc);
+            } else {
+                const int v0 = u - ntri, K = T0 + v0 % m;
+                T* yv = v0 < m ? y1 : y2;
+                T acc[4];
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) acc[cc] = yv[4 * K + cc];
+                for (int J = J0; J < J0 + nJ; ++J) {
+                    T bv[16];
+                    tile_load(A, ntl, tile_idx(K, J), bv);
+#pragma unroll
+                    for (int cc = 0; cc < 4; ++cc)
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) acc[cc] -= yv[4 * J + k] * bv[cc * 4 + k];
+                }
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) yv[4 * K + cc] = acc[cc];
+            }
         }
         __syncthreads();
     }
     return true;
-}
-
-// y <- L^-1 y for two right-hand sides (tile forward substitution)
-template <typename T>
-__device__ void forward_solve2(const T* A, const Geo& g, T* y1, T* y2) {
-    const int ntl = g.ntl;
-    for (int J = 0; J < g.nt; ++J) {
-        if (threadIdx.x < 2) {
-            T* y = threadIdx.x == 0 ? y1 : y2;
-            T l[16];
-            tile_load(A, ntl, tile_idx(J, J), l);
-            for (int r = 0; r < 4; ++r) {
-                T v = y[4 * J + r];
-                for (int k = 0; k < r; ++k) v -= l[r * 4 + k] * y[4 * J + k];
-                y[4 * J + r] = v / l[r * 4 + r];
-            }
-        }
-        __syncthreads();
-        for (int u = J + 1 + threadIdx.x / 2; u < g.nt; u += FB_THREADS / 2) {
-            T* y = (threadIdx.x & 1) ? y2 : y1;
-            T l[16];
-            tile_load(A, ntl, tile_idx(u, J), l);
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                T v = y[4 * u + r];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) v -= l[r * 4 + k] * y[4 * J + k];
-                y[4 * u + r] = v;
-            }
-        }
-        __syncthreads();
-    }
 }
 
 // ---- Householder tridiagonalisation (in place; reflector k stored in column k below
@@ -728,8 +775,8 @@ __device__ unsigned process_pixel(const FullArgs& a, const Geo& g, Smem<T>& m, S
     unsigned redo = 0;
     m.flag = sflag;
     __syncthreads();
-    sample_mean<T>(a.x, a.H, a.W, D, g.Dp, py, px, 0, N, ro, ri, m.mu_o);
-    sample_mean<T>(a.x, a.H, a.W, D, g.Dp, py, px, 1, ni, ro, ri, m.mu_i);
+    sample_mean<T>(a.x, a.H, a.W, g, py, px, 0, N, ro, ri, m.mu_o, m.xs);
+    sample_mean<T>(a.x, a.H, a.W, g, py, px, 1, ni, ro, ri, m.mu_i, m.xs);
     __syncthreads();
     if (want & 3u) {
         for (int b = threadIdx.x; b < g.Dp; b += FB_THREADS) {
@@ -755,7 +802,7 @@ __device__ unsigned process_pixel(const FullArgs& a, const Geo& g, Smem<T>& m, S
         const T delta = (T)a.loading * tr / (T)D;
         for (int b = threadIdx.x; b < D; b += FB_THREADS) el(m.A, g.ntl, b, b) += delta;
         __syncthreads();
-        bool ok = cholesky_tiles(m.A, g, T(16) * Num<T>::eps * (dmax + delta), m.flag);
+        bool ok = cholesky_bordered(m.A, g, T(16) * Num<T>::eps * (dmax + delta), m.flag, m.r1, m.r2, m.v);
         if (ok && gate) {
             // kappa estimate from the factor's diagonal: (max L_ii / min L_ii)^2
             T lmax = T(0), lmin = T(3e38);
@@ -771,7 +818,6 @@ __device__ unsigned process_pixel(const FullArgs& a, const Geo& g, Smem<T>& m, S
         }
         if (!ok && gate) redo |= want & 3u;
         if (ok) {
-            forward_solve2(m.A, g, m.r1, m.r2);
             T q1 = T(0), q2 = T(0);
             for (int b = threadIdx.x; b < D; b += FB_THREADS) { q1 += m.r1[b] * m.r1[b]; q2 += m.r2[b] * m.r2[b]; }
             q1 = block_sum(q1, m.red);
@@ -1055,7 +1101,7 @@ __global__ void __launch_bounds__(FB_THREADS, 1) moments_kernel(FullArgs a, Geo 
         const int64_t p = pix[t];
         const int py = (int)(p / a.W), px = (int)(p % a.W);
         __syncthreads();
-        sample_mean<T>(a.x, a.H, a.W, D, g.Dp, py, px, 0, N, ro, ri, mu);
+        sample_mean<T>(a.x, a.H, a.W, g, py, px, 0, N, ro, ri, mu, xs);
         __syncthreads();
         mat_zero(A, g);
         if constexpr (sizeof(T) == 4) {
