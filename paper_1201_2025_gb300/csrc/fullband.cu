@@ -131,13 +131,16 @@ struct Smem {
     T* lam;   // [mcap] selected eigenvalues
     T* res;   // [mcap * 2] per-vector sign*projection, projection
     T* red;   // [FB_WARPS]
+    T* pan;   // Cholesky panel buffer [Dp + NB + 2][PP]
     int* flag;
 };
 
 struct Geo {
     int D, Dp, nt, ntl, S, mcap;
     bool a_in_smem;
-    bool tc;  // window Gram on the tensor cores (mixed precision, D <= 256)
+    bool tc;           // window Gram on the tensor cores (mixed precision, D <= 256)
+    bool pan_in_tc;    // Cholesky panel buffer inside the (then idle) tensor-core chunk buffers
+    bool pan_in_smem;  // else in shared memory after the vectors, else in the slab
 };
 
 __host__ __device__ inline int fb_chunk(int elem_size) { return elem_size == 4 ? 32 : 8; }
@@ -363,27 +366,54 @@ __device__ void mat_scale(T* A, const Geo& g, T s) {
 }
 
 // ---- blocked Cholesky of the tile-packed matrix, bordered by the two right-hand sides.
-// Right-looking in steps of NB = 32 columns (8 tile columns): (1) one warp factors the
-// 32 x 32 diagonal block in registers, lane i holding row i (the column of L that each step
-// needs comes by shuffles); (2) one thread per row below the block, and one for each
-// right-hand side, solves X = A_panel L_kk^-T (the rows of the block in registers, L_kk read
-// as shared-memory broadcasts); (3) the trailing tiles take A_IK -= sum_J A_IJ A_KJ^T over the
-// block's tile columns J, and the right-hand sides y -= X_b X^T.  The right-hand sides behave
-// as two extra rows appended below the matrix, so on return y1 = L^-1 r1 and y2 = L^-1 r2 and
-// no separate solve is needed.  Padding rows (D <= b < Dp) are identity.  Returns false,
-// leaving *flag = 1, if a pivot is not above `floor`; L_ii stays on the diagonal.
+// Right-looking in steps of NB = 32 columns (8 tile columns):
+//   (1) one warp factors the 32 x 32 diagonal block in registers (lane i holds row i; the
+//       column of L each step needs comes by shuffles) and writes L_kk densely at the head
+//       of the panel buffer, with 1 / L_jj in column NB;
+//   (2) one thread per row below the block, and one for each right-hand side, solves
+//       x = a L_kk^-T with the row in registers (L_kk read as shared-memory broadcasts) and
+//       writes it to the panel buffer, rows ordered (row within tile, tile) so that the
+//       float4 reads of neighbouring tiles in (3) fall on distinct banks;
+//   (3) the trailing tiles take A_IK -= X_I X_K^T and the right-hand sides y -= x_b X^T,
+//       reading X from the panel buffer.
+// The right-hand sides behave as two extra rows appended below the matrix, so on return
+// y1 = L^-1 r1 and y2 = L^-1 r2 and no separate solve is needed.  Pivots use rsqrt (1/L_jj
+// directly).  Padding rows (D <= b < Dp) are identity.  Returns false, leaving *flag = 1, if
+// a pivot is not above `floor`; L_jj is left on A's diagonal.
 constexpr int NB = 32;
+constexpr int PP = 36;  // panel pitch (16-byte aligned rows)
+constexpr int LP = 33;  // pitch of the dense diagonal block at the head of the panel buffer
 
 template <typename T>
-__device__ bool cholesky_bordered(T* A, const Geo& g, T floor, int* flag, T* y1, T* y2, T* invd) {
-    const int ntl = g.ntl, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+__host__ __device__ inline size_t pan_bytes(int Dp) {
+    return ((size_t)(Dp + NB + 2) * PP * sizeof(T) + 255) & ~(size_t)255;
+}
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
+__device__ __forceinline__ void ld4(const float* p, float (&o)[4]) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&o)[4]) {
+    const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+
+template <typename T>
+__device__ bool cholesky_bordered(T* A, const Geo& g, T floor, int* flag, T* y1, T* y2, T* pan) {
+    const int ntl = g.ntl;
     if (threadIdx.x == 0) *flag = 0;
     for (int b = g.D + threadIdx.x; b < g.Dp; b += FB_THREADS) el(A, ntl, b, b) = T(1);
     __syncthreads();
     for (int c0 = 0; c0 < g.Dp; c0 += NB) {
         const int nb = min(NB, g.Dp - c0);  // a multiple of 4
-        // (1) diagonal block
-        if (warp == 0) {
+        const int r0 = c0 + nb, nrows = g.Dp - r0, mI = nrows / 4;
+        T* X = pan + NB * PP;              // trailing rows: row r0 + 4 i + rr at X[(rr mI + i) PP]
+        T* Yr = X + (size_t)nrows * PP;    // the two right-hand sides
+        // (1) diagonal block: warp 0, lane i holding row i in registers, the column of L each
+        // step needs taken by shuffles
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
             T a[NB];
 #pragma unroll
             for (int c = 0; c < NB; ++c)
@@ -396,8 +426,8 @@ __device__ bool cholesky_bordered(T* A, const Geo& g, T floor, int* flag, T* y1,
                     if (!(d > floor)) ok = false;
                 }
                 if (j < nb && ok) {
-                    const T l = Num<T>::sqrt_(d), inv = T(1) / l;
-                    if (lane == j) { a[j] = l; invd[j] = inv; }
+                    const T inv = rsqrt_t(d);
+                    if (lane == j) { a[j] = d * inv; pan[j * LP + NB] = inv; }
                     else if (lane > j) a[j] *= inv;
                     const T lij = a[j];
 #pragma unroll
@@ -410,15 +440,17 @@ __device__ bool cholesky_bordered(T* A, const Geo& g, T floor, int* flag, T* y1,
             if (ok) {
 #pragma unroll
                 for (int c = 0; c < NB; ++c)
-                    if (lane < nb && c <= lane) el(A, ntl, c0 + lane, c0 + c) = a[c];
+                    if (lane < nb && c <= lane) {
+                        el(A, ntl, c0 + lane, c0 + c) = a[c];
+                        pan[lane * LP + c] = a[c];
+                    }
             } else if (lane == 0) {
                 *flag = 1;
             }
         }
         __syncthreads();
         if (*flag) return false;
-        // (2) panel rows and the two right-hand sides
-        const int r0 = c0 + nb, nrows = g.Dp - r0;
+        // (2) panel rows and the two right-hand sides, one thread per row in registers
         for (int t = threadIdx.x; t < nrows + 2; t += FB_THREADS) {
             T x[NB];
             T* yv = t == nrows ? y1 : y2;
@@ -430,59 +462,66 @@ __device__ bool cholesky_bordered(T* A, const Geo& g, T floor, int* flag, T* y1,
                 if (c < nb) {
                     T v = x[c];
 #pragma unroll
-                    for (int k = 0; k < c; ++k) v -= x[k] * el(A, ntl, c0 + c, c0 + k);
-                    x[c] = v * invd[c];
+                    for (int k = 0; k < c; ++k) v -= x[k] * pan[c * LP + k];
+                    x[c] = v * pan[c * LP + NB];
                 }
             }
+            T* dst = t < nrows ? X + (size_t)((t & 3) * mI + (t >> 2)) * PP : Yr + (size_t)(t - nrows) * PP;
 #pragma unroll
             for (int c = 0; c < NB; ++c)
                 if (c < nb) {
-                    if (t < nrows) el(A, ntl, r0 + t, c0 + c) = x[c];
-                    else yv[c0 + c] = x[c];
+                    dst[c] = x[c];
+                    if (t >= nrows) yv[c0 + c] = x[c];
                 }
         }
         __syncthreads();
         // (3) trailing tiles and right-hand sides
-        const int T0 = r0 / 4, m = g.nt - T0, J0 = c0 / 4, nJ = nb / 4;
-        const int ntri = ntiles_of(m);
-        for (int u = threadIdx.x; u < ntri + 2 * m; u += FB_THREADS) {
+        const int T0 = r0 / 4;
+        const int ntri = ntiles_of(mI);
+        for (int u = threadIdx.x; u < ntri + 2 * mI; u += FB_THREADS) {
             if (u < ntri) {
                 int i2, k2;
                 tri_rc(u, i2, k2);
-                const int I = T0 + i2, K = T0 + k2, uc = tile_idx(I, K);
+                const int uc = tile_idx(T0 + i2, T0 + k2);
                 T acc[16];
                 tile_load(A, ntl, uc, acc);
-                for (int J = J0; J < J0 + nJ; ++J) {
-                    T av[16], bv[16];
-                    tile_load(A, ntl, tile_idx(I, J), av);
-                    tile_load(A, ntl, tile_idx(K, J), bv);
+                for (int s4 = 0; s4 < nb; s4 += 4) {
+                    T xi[4][4], xk[4][4];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        ld4(X + (size_t)(r * mI + i2) * PP + s4, xi[r]);
+                        ld4(X + (size_t)(r * mI + k2) * PP + s4, xk[r]);
+                    }
 #pragma unroll
                     for (int rr = 0; rr < 4; ++rr)
 #pragma unroll
                         for (int cc = 0; cc < 4; ++cc) {
                             T v = acc[rr * 4 + cc];
 #pragma unroll
-                            for (int k = 0; k < 4; ++k) v -= av[rr * 4 + k] * bv[cc * 4 + k];
+                            for (int k = 0; k < 4; ++k) v -= xi[rr][k] * xk[cc][k];
                             acc[rr * 4 + cc] = v;
                         }
                 }
                 tile_store(A, ntl, uc, acc);
             } else {
-                const int v0 = u - ntri, K = T0 + v0 % m;
-                T* yv = v0 < m ? y1 : y2;
+                const int v0 = u - ntri, k2 = v0 % mI;
+                T* yv = v0 < mI ? y1 : y2;
+                const T* yr = Yr + (size_t)(v0 < mI ? 0 : 1) * PP;
                 T acc[4];
 #pragma unroll
-                for (int cc = 0; cc < 4; ++cc) acc[cc] = yv[4 * K + cc];
-                for (int J = J0; J < J0 + nJ; ++J) {
-                    T bv[16];
-                    tile_load(A, ntl, tile_idx(K, J), bv);
+                for (int cc = 0; cc < 4; ++cc) acc[cc] = yv[4 * (T0 + k2) + cc];
+                for (int s4 = 0; s4 < nb; s4 += 4) {
+                    T yb[4], xk[4][4];
+                    ld4(yr + s4, yb);
+#pragma unroll
+                    for (int cc = 0; cc < 4; ++cc) ld4(X + (size_t)(cc * mI + k2) * PP + s4, xk[cc]);
 #pragma unroll
                     for (int cc = 0; cc < 4; ++cc)
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) acc[cc] -= yv[4 * J + k] * bv[cc * 4 + k];
+                        for (int k = 0; k < 4; ++k) acc[cc] -= yb[k] * xk[cc][k];
                 }
 #pragma unroll
-                for (int cc = 0; cc < 4; ++cc) yv[4 * K + cc] = acc[cc];
+                for (int cc = 0; cc < 4; ++cc) yv[4 * (T0 + k2) + cc] = acc[cc];
             }
         }
         __syncthreads();
@@ -802,7 +841,7 @@ __device__ unsigned process_pixel(const FullArgs& a, const Geo& g, Smem<T>& m, S
         const T delta = (T)a.loading * tr / (T)D;
         for (int b = threadIdx.x; b < D; b += FB_THREADS) el(m.A, g.ntl, b, b) += delta;
         __syncthreads();
-        bool ok = cholesky_bordered(m.A, g, T(16) * Num<T>::eps * (dmax + delta), m.flag, m.r1, m.r2, m.v);
+        bool ok = cholesky_bordered(m.A, g, T(16) * Num<T>::eps * (dmax + delta), m.flag, m.r1, m.r2, m.pan);
         if (ok && gate) {
             // kappa estimate from the factor's diagonal: (max L_ii / min L_ii)^2
             T lmax = T(0), lmin = T(3e38);
@@ -986,11 +1025,16 @@ __global__ void __launch_bounds__(FB_THREADS, 1) fullband_kernel(FullArgs a, Geo
     // slab: [matrix unless in shared memory][eigen scratch][FP64 re-solve area (mixed)]
     char* q = slab;
     if (!g.a_in_smem) { m.A = reinterpret_cast<T*>(q); q += ((sizeof(T) * (size_t)g.ntl * 16 + 255) & ~(size_t)255); }
+    if (g.pan_in_tc) m.pan = reinterpret_cast<T*>(st.buf[0]);
+    else if (g.pan_in_smem) m.pan = reinterpret_cast<T*>(sp_end);
+    else { m.pan = reinterpret_cast<T*>(q); q += pan_bytes<T>(g.Dp); }
     carve_scratch<T>(q, g, sc, &q);
     Smem<double> m64;
     Scratch<double> sc64;
     if (g.tc) {
         carve<double>(q, g64, m64, sc64, true, &q);
+        m64.pan = reinterpret_cast<double*>(q);
+        q += pan_bytes<double>(g64.Dp);
         carve_scratch<double>(q, g64, sc64, &q);
     }
     if (g.tc) {
@@ -1142,6 +1186,8 @@ Geo make_geo_only(const FullArgs& a) {
     g.mcap = std::min(g.Dp, a.inner * a.inner + 16);
     g.tc = false;
     g.a_in_smem = false;
+    g.pan_in_tc = false;
+    g.pan_in_smem = false;
     return g;
 }
 
@@ -1153,12 +1199,18 @@ Geo make_geo(const FullArgs& a, bool* smem_ok, size_t* smem_bytes, size_t* slab,
     g.tc = (sizeof(T) == 4) && a.precision == WDAD_PREC_MIXED && a.D <= 256;
     const size_t tcb = g.tc ? kTcBufBytes : 0;
     g.a_in_smem = (sizeof(T) == 4) && (amat + vecs + tcb <= 210 * 1024);
-    *smem_bytes = vecs + tcb + (g.a_in_smem ? amat : 0) + 1024;  // + alignment slack
+    const size_t panb = pan_bytes<T>(g.Dp);
+    size_t sm = vecs + tcb + (g.a_in_smem ? amat : 0);
+    g.pan_in_tc = g.tc && panb <= kTcBufBytes;
+    g.pan_in_smem = !g.pan_in_tc && sm + panb <= 210 * 1024;
+    if (g.pan_in_smem) sm += panb;
+    *smem_bytes = sm + 1024;  // + alignment slack
     *smem_ok = *smem_bytes <= 227 * 1024;
-    size_t sl = (g.a_in_smem ? 0 : ((amat + 255) & ~(size_t)255)) + scratch_bytes<T>(g);
+    size_t sl = (g.a_in_smem ? 0 : ((amat + 255) & ~(size_t)255)) + (g.pan_in_tc || g.pan_in_smem ? 0 : panb) +
+                scratch_bytes<T>(g);
     Geo g64 = make_geo_only<double>(a);
     if (g.tc) sl += ((sizeof(double) * (size_t)g64.ntl * 16 + 255) & ~(size_t)255) + vec_bytes<double>(g64) +
-                    scratch_bytes<double>(g64);
+                    pan_bytes<double>(g64.Dp) + scratch_bytes<double>(g64);
     *slab = (sl + 255) & ~(size_t)255;
     if (g64_out) *g64_out = g64;
     return g;
