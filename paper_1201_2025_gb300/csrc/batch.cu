@@ -20,22 +20,45 @@
 
 #include "batch.h"
 #include "dwt_dev.cuh"
+#include "tc.cuh"
 #include "reduced_dev.cuh"
 
 namespace wdad {
 
 constexpr int BATCH_THREADS = 512;
 constexpr int kGroupsPerDwtItem = 512;  // 4-pixel groups: 2048 pixels per DWT item
+constexpr int kChunkPx = 32;            // pixels per staged chunk of a DWT item
+constexpr int kStages = 3;              // chunks in flight per CTA
+constexpr int kStageFloats = kChunkPx * 256;  // stage stride (L <= 256)
+constexpr uint32_t kStageWait = 1u << 24;     // polls before a staged chunk counts as lost
+
+// Staged-chunk copy of DWT item chunk q (pixels [p0 + q kChunkPx, ...)) into stage s.
+__device__ __forceinline__ void issue_chunk(const BatchJob& j, int64_t p0, int64_t npx_total, int q, int s,
+                                            float* stages, uint64_t* full) {
+    const int64_t first = p0 + (int64_t)q * kChunkPx;
+    const int64_t n = min((int64_t)kChunkPx, npx_total - (int64_t)q * kChunkPx);
+    const uint32_t bytes = (uint32_t)(n * j.L * (int64_t)sizeof(float));
+    tc::mbar_arrive_expect_tx(&full[s], bytes);
+    tc::bulk_g2s(stages + (size_t)s * kStageFloats, j.cube + first * j.L, bytes, &full[s]);
+}
 
 __global__ void __launch_bounds__(BATCH_THREADS, 2)
     batch_kernel(const BatchJob* __restrict__ jobs, const BatchItem* __restrict__ items, int nitems, int* counter,
                  int* done, int* status, uint32_t spin_limit) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ int s_item;
     __shared__ int s_ready;
+    __shared__ int s_ok;
+    __shared__ __align__(8) uint64_t s_full[kStages];
     // the tile's arguments live in shared memory (a kernel parameter in the standalone
     // kernel), which keeps them out of the 64 registers a thread has at two CTAs per SM
     __shared__ DetectArgs s_args;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) tc::mbar_init(&s_full[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    uint32_t gchunk = 0;  // staged chunks this CTA has consumed (stage = g % kStages, parity = g / kStages)
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
         __syncthreads();
@@ -45,21 +68,67 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2)
         const BatchItem bi = items[it];
         const BatchJob& j = jobs[bi.job];
         if (bi.kind == 0) {
+            // DWT item: its pixels stream through kStages shared-memory stages by bulk copies
+            // (one thread issues, mbarriers count the bytes); the lanes keep their slice of the
+            // DWT matrix in registers
+            const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5, lane = threadIdx.x & 31;
             const int64_t P = (int64_t)j.H * j.W;
-            const int64_t warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-            // the job's K x L DWT matrix into shared memory, rows of LS floats, zero-padded
-            float* A_s = reinterpret_cast<float*>(smem_raw);
-            const int LS = j.variant == 0 ? 128 : 256;
-            for (int i = threadIdx.x; i < 4 * LS; i += blockDim.x) {
-                const int k = i / LS, c = i % LS;
-                A_s[i] = (k < j.K && c < j.L) ? j.A[(size_t)k * j.L + c] : 0.0f;
+            const int64_t p0 = 4 * (int64_t)bi.a, p1 = min(P, 4 * (int64_t)bi.b);
+            const int64_t npx_total = p1 - p0;
+            const int nchunk = (int)((npx_total + kChunkPx - 1) / kChunkPx);
+            float* stages = reinterpret_cast<float*>(smem_raw);
+            const int LV = j.L / 4;
+            float a[2][4][4];
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int c = lane + 32 * i;
+                        a[i][k][e] = (c < LV && k < j.K) ? __ldg(j.A + (size_t)k * j.L + c * 4 + e) : 0.0f;
+                    }
+            if (threadIdx.x == 0) {
+                tc::fence_proxy_async_smem();  // earlier generic accesses of the stages come first
+                for (int q = 0; q < min(kStages, nchunk); ++q)
+                    issue_chunk(j, p0, npx_total, q, (int)((gchunk + q) % kStages), stages, s_full);
             }
-            __syncthreads();
-            if (j.variant == 0)
-                dwt_groups_sA<1>(j.cube, P, j.L, A_s, j.K, j.approx, bi.a, bi.b, warp, nw);
-            else
-                dwt_groups_sA<2>(j.cube, P, j.L, A_s, j.K, j.approx, bi.a, bi.b, warp, nw);
-            __syncthreads();
+            int ok = 1;
+            int q = 0;
+            for (; q < nchunk; ++q) {
+                const uint32_t g = gchunk + (uint32_t)q;
+                const int s = (int)(g % kStages);
+                if (threadIdx.x == 0) s_ok = tc::mbar_wait_bounded(&s_full[s], (g / kStages) & 1u, kStageWait) ? 1 : 0;
+                __syncthreads();
+                ok = s_ok;
+                if (!ok) break;
+                const int npx = (int)min((int64_t)kChunkPx, npx_total - (int64_t)q * kChunkPx);
+                float* out = j.approx + (size_t)(p0 + (int64_t)q * kChunkPx) * j.K;
+                if (j.variant == 0) {
+                    const float(&a1)[1][4][4] = *reinterpret_cast<const float(*)[1][4][4]>(&a[0]);
+                    dwt_staged_pairs<1>(stages + (size_t)s * kStageFloats, npx, j.L, a1, j.K, out, warp, nw);
+                } else {
+                    dwt_staged_pairs<2>(stages + (size_t)s * kStageFloats, npx, j.L, a, j.K, out, warp, nw);
+                }
+                __syncthreads();  // the stage is free again
+                if (threadIdx.x == 0 && q + kStages < nchunk) {
+                    tc::fence_proxy_async_smem();
+                    issue_chunk(j, p0, npx_total, q + kStages, s, stages, s_full);
+                }
+            }
+            if (!ok) {
+                // a staged chunk never arrived: report it, let the copies in flight land, stop
+                if (threadIdx.x == 0) {
+                    atomicExch(&status[0], (int)WDAD_ERR_TIMEOUT);
+                    for (int r = q + 1; r < min(nchunk, q + kStages); ++r) {
+                        const uint32_t g = gchunk + (uint32_t)r;
+                        tc::mbar_wait_bounded(&s_full[g % kStages], (g / kStages) & 1u, kStageWait);
+                    }
+                }
+                __syncthreads();
+                return;
+            }
+            gchunk += (uint32_t)nchunk;
             if (threadIdx.x == 0) {
                 __threadfence();
                 atomicAdd(&done[bi.job], 1);
@@ -105,7 +174,10 @@ bool batch_job_supported(int L, int K) { return L % 4 == 0 && L <= 256 && K >= 1
 
 int batch_variant(int L) { return L <= 128 ? 0 : 1; }
 
-size_t batch_dwt_smem(int L) { return sizeof(float) * 4 * (size_t)(batch_variant(L) == 0 ? 128 : 256); }
+size_t batch_dwt_smem(int L) {
+    (void)L;
+    return sizeof(float) * (size_t)kStages * kStageFloats;
+}
 
 void batch_build_items(const std::vector<BatchJob>& jobs, std::vector<BatchItem>& items, std::vector<int>& dwt_items,
                        int drop_job, int lag) {

@@ -27,15 +27,17 @@ __device__ __forceinline__ float butterfly32(float (&v)[32], int lane) {
     return v[0];
 }
 
-// Reduce-scatter of 16 per-lane values over the 32 lanes: afterwards lanes l and l ^ 16 both
-// hold the sum over all lanes of v[l & 15].  The summation tree (lane pairs over bit 4, then
-// bits 3, 2, 1, 0, each addition own + partner) is the one butterfly32 builds for its value
-// indices, so the two give bit-identical sums for the same per-lane inputs.
-__device__ __forceinline__ float butterfly16x2(float (&v)[16], int lane) {
+// Reduce-scatter of 8 per-lane values over the 32 lanes: afterwards lanes l, l^8, l^16 and
+// l^24 hold the sum over all lanes of v[l & 7].  Folds over lane bits 4 and 3, then the
+// butterfly over bits 2, 1, 0: the summation tree butterfly32 builds, so the sums are
+// bit-identical to it for the same per-lane inputs.
+__device__ __forceinline__ float butterfly8x4(float (&v)[8], int lane) {
 #pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] += __shfl_xor_sync(0xffffffffu, v[j], 16);
+    for (int j = 0; j < 8; ++j) v[j] += __shfl_xor_sync(0xffffffffu, v[j], 16);
 #pragma unroll
-    for (int off = 8; off >= 1; off >>= 1) {
+    for (int j = 0; j < 8; ++j) v[j] += __shfl_xor_sync(0xffffffffu, v[j], 8);
+#pragma unroll
+    for (int off = 4; off >= 1; off >>= 1) {
         const bool upper = (lane & off) != 0;
 #pragma unroll
         for (int j = 0; j < off; ++j) {
@@ -47,54 +49,41 @@ __device__ __forceinline__ float butterfly16x2(float (&v)[16], int lane) {
     return v[0];
 }
 
-// Variant of dwt_groups for the persistent batch kernel (16-byte chunks, K <= 4, 4 pixels per
-// warp step): the DWT matrix comes from shared memory, A_s[k * NCH*128 + c] (zero for c >= L
-// and k >= K), instead of registers, which keeps the kernel within 64 registers a thread.  The
-// per-lane sums take the same (chunk, element) order and butterfly16x2 builds the same lane
-// tree as dwt_groups' butterfly32, so the coefficients are bit-identical to dwt_apply_kernel's.
-// Groups are 4-pixel groups here.
+// DWT of npx pixel spectra staged in shared memory (xs: pixel p at xs + p L, L % 4 == 0,
+// K <= 4): warp w takes pixels 2w, 2w + 1, then every 2 nwarps-th pair; lane slice a of the
+// DWT matrix in registers (zero beyond L and K).  Per-lane sums in dwt_groups' (chunk,
+// element) order and butterfly8x4's lane tree give coefficients bit-identical to
+// dwt_apply_kernel's.
 template <int NCH>
-__device__ __forceinline__ void dwt_groups_sA(const float* __restrict__ cube, int64_t P, int L,
-                                              const float* __restrict__ A_s, int K, float* __restrict__ out,
-                                              int64_t g_begin, int64_t g_end, int64_t warp, int64_t nwarps) {
-    constexpr int PX = 4, KP = 4, LS = NCH * 128;
+__device__ __forceinline__ void dwt_staged_pairs(const float* __restrict__ xs, int npx, int L,
+                                                 const float (&a)[NCH][4][4], int K, float* __restrict__ out,
+                                                 int warp, int nwarps) {
     const int lane = threadIdx.x & 31;
     const int LV = L / 4;
-    for (int64_t g = g_begin + warp; g < g_end; g += nwarps) {
-        const int64_t p0 = g * PX;
-        float x[PX][NCH][4];
+    for (int p0 = 2 * warp; p0 < npx; p0 += 2 * nwarps) {
+        float v[8];
 #pragma unroll
-        for (int p = 0; p < PX; ++p)
+        for (int p = 0; p < 2; ++p) {
+            float s[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
             for (int i = 0; i < NCH; ++i) {
                 const int c = lane + 32 * i;
                 float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
-                if ((p0 + p < P) && (c < LV)) t = __ldcs(reinterpret_cast<const float4*>(cube + (p0 + p) * L) + c);
-                x[p][i][0] = t.x; x[p][i][1] = t.y; x[p][i][2] = t.z; x[p][i][3] = t.w;
-            }
-        float v[16];
+                if (p0 + p < npx && c < LV) t = reinterpret_cast<const float4*>(xs + (size_t)(p0 + p) * L)[c];
 #pragma unroll
-        for (int k = 0; k < KP; ++k) {
-            float s[PX];
-#pragma unroll
-            for (int p = 0; p < PX; ++p) s[p] = 0.0f;
-#pragma unroll
-            for (int i = 0; i < NCH; ++i) {
-                const float4 a4 = *reinterpret_cast<const float4*>(A_s + k * LS + (lane + 32 * i) * 4);
-#pragma unroll
-                for (int p = 0; p < PX; ++p) {
-                    s[p] = fmaf(x[p][i][0], a4.x, s[p]);
-                    s[p] = fmaf(x[p][i][1], a4.y, s[p]);
-                    s[p] = fmaf(x[p][i][2], a4.z, s[p]);
-                    s[p] = fmaf(x[p][i][3], a4.w, s[p]);
+                for (int k = 0; k < 4; ++k) {
+                    s[k] = fmaf(t.x, a[i][k][0], s[k]);
+                    s[k] = fmaf(t.y, a[i][k][1], s[k]);
+                    s[k] = fmaf(t.z, a[i][k][2], s[k]);
+                    s[k] = fmaf(t.w, a[i][k][3], s[k]);
                 }
             }
 #pragma unroll
-            for (int p = 0; p < PX; ++p) v[p * KP + k] = s[p];
+            for (int k = 0; k < 4; ++k) v[p * 4 + k] = s[k];
         }
-        const float r = butterfly16x2(v, lane);
-        const int t = lane & 15, p = t / KP, k = t % KP;
-        if (lane < 16 && k < K && p0 + p < P) out[(p0 + p) * K + k] = r;
+        const float r = butterfly8x4(v, lane);
+        const int t = lane & 7, p = t >> 2, k = t & 3;
+        if (lane < 8 && k < K && p0 + p < npx) out[(size_t)(p0 + p) * K + k] = r;
     }
 }
 
