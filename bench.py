@@ -178,14 +178,14 @@ def _timer(stream):
     return _time
 
 
-def bench_batching(dev, stream, peak):
-    """64 cubes of uneven size (side U{128..1024}), band count (128/188/224), window and
+def bench_batching(dev, stream, peak, side_lo=128, side_hi=1024):
+    """64 cubes of uneven size (side U{side_lo..side_hi}), band count (128/188/224), window and
     detector in one persistent graph-captured launch, against the same jobs run one after
     another through the single-cube entry points (DWT + detector each)."""
     import torch
     from paper_1201_2025_gb300 import synth, wdad
     _time = _timer(stream)
-    specs = synth.batch_specs(64, seed=0)
+    specs = synth.batch_specs(64, seed=0, side_lo=side_lo, side_hi=side_hi)
     jobs, nbytes, npx = [], 0, 0
     for sp in specs:
         Hh, Ww, Ll = sp["H"], sp["W"], sp["L"]
@@ -198,7 +198,7 @@ def bench_batching(dev, stream, peak):
         nbytes += Hh * Ww * (4 * Ll + 4 * K + 4 * K + 4)  # DWT read + write, detector read + score write
     torch.cuda.synchronize()
     res = {"jobs": len(jobs), "pixels": npx, "cube_GB": sum(j["cube"].numel() * 4 for j in jobs) / 1e9,
-           "workload": "64 cubes, side U{128..1024}, L in {128,188,224}, windows (3,9)/(5,15)/(7,21), "
+           "workload": f"64 cubes, side U{{{side_lo}..{side_hi}}}, L in {{128,188,224}}, windows (3,9)/(5,15)/(7,21), "
                        "one detector each (LRX/DWRX/DWEST), f32, device-generated (same recipe)"}
     for name, tuned in (("default_plans", False), ("autotuned", True)):
         b = wdad.wdad_batch(jobs, autotune=tuned, use_graph=True)
@@ -443,7 +443,10 @@ def run_ours(args):
                 ent[f"{dn}_max_rel_err_vs_fp64"] = float(np.max(rel))
             mixed[name] = ent
         mixed["workload"] = "64x64x224 AR(1) rho=0.98 scene, 10 targets, windows 3/11, loading 1e-3"
-    batching = bench_batching(dev, stream, peak) if not args.no_batch else None
+    batching = None
+    if not args.no_batch:
+        batching = bench_batching(dev, stream, peak)
+        batching["small_cubes"] = bench_batching(dev, stream, peak, side_lo=32, side_hi=160)
     screening = bench_screening(dev, stream, args.screen_train_cubes, args.screen_train_steps) \
         if not args.no_screen else None
     step_bytes = H * W * (BYTES_DWT_PER_PX + 3 * 3 * 4)

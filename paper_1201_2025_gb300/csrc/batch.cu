@@ -57,8 +57,8 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2)
         for (int s = 0; s < kStages; ++s) tc::mbar_init(&s_full[s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    __syncthreads();
     uint32_t gchunk = 0;  // staged chunks this CTA has consumed (stage = g % kStages, parity = g / kStages)
+    int ready_job = -1;   // job whose DWT this CTA has seen finished and whose arguments s_args holds
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
         __syncthreads();
@@ -134,29 +134,34 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2)
                 atomicAdd(&done[bi.job], 1);
             }
         } else {
-            if (threadIdx.x == 0) {
-                uint32_t n = 0;
-                int ok = 1;
-                while (atomicAdd(&done[bi.job], 0) < j.dwt_items) {
-                    if (atomicAdd(&status[1 + bi.job], 0) != 0 || ++n > spin_limit) {
-                        ok = 0;
-                        atomicExch(&status[1 + bi.job], 1);
-                        atomicExch(&status[0], (int)WDAD_ERR_TIMEOUT);
-                        break;
+            // the first tile of a job this CTA meets waits (bounded) for the job's DWT items and
+            // loads the job's arguments; later tiles of the same job reuse both
+            if (bi.job != ready_job) {
+                if (threadIdx.x == 0) {
+                    uint32_t n = 0;
+                    int ok = 1;
+                    while (atomicAdd(&done[bi.job], 0) < j.dwt_items) {
+                        if (atomicAdd(&status[1 + bi.job], 0) != 0 || ++n > spin_limit) {
+                            ok = 0;
+                            atomicExch(&status[1 + bi.job], 1);
+                            atomicExch(&status[0], (int)WDAD_ERR_TIMEOUT);
+                            break;
+                        }
+                        __nanosleep(256);
                     }
-                    __nanosleep(256);
+                    __threadfence();
+                    s_ready = ok;
+                    DetectArgs& a = s_args;
+                    a.x = j.approx; a.H = j.H; a.W = j.W; a.D = j.K;
+                    a.inner = j.inner; a.outer = j.outer; a.loading = j.loading; a.border = j.border;
+                    a.dwest_mode = j.dwest_mode; a.dwest_tau = j.tau;
+                    for (int t = 0; t < 3; ++t) a.out[t] = j.out[t];
+                    a.flags = j.flags;
                 }
-                __threadfence();
-                s_ready = ok;
-                DetectArgs& a = s_args;
-                a.x = j.approx; a.H = j.H; a.W = j.W; a.D = j.K;
-                a.inner = j.inner; a.outer = j.outer; a.loading = j.loading; a.border = j.border;
-                a.dwest_mode = j.dwest_mode; a.dwest_tau = j.tau;
-                for (int t = 0; t < 3; ++t) a.out[t] = j.out[t];
-                a.flags = j.flags;
+                __syncthreads();
+                ready_job = s_ready ? bi.job : -1;
             }
-            __syncthreads();
-            if (s_ready) {
+            if (ready_job == bi.job) {
                 const int th = j.th;
                 switch (s_args.D) {
                     case 1: detect_tile<1>(s_args, th, bi.a, bi.b, smem_raw); break;

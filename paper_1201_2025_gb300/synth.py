@@ -151,13 +151,13 @@ def scene_ar1(H: int = 1024, W: int = 1024, L: int = 224, seed: int = 0, rho: fl
                       abundance=(0.1, 0.5), margin=10, ar_rho=rho)
 
 
-def batch_specs(n: int = 64, seed: int = 0):
-    """Uneven batch: side U{128..1024}, L in {128,188,224}, windows and detectors mixed."""
+def batch_specs(n: int = 64, seed: int = 0, side_lo: int = 128, side_hi: int = 1024):
+    """Uneven batch: side U{side_lo..side_hi}, L in {128,188,224}, windows and detectors mixed."""
     rng = np.random.default_rng(seed)
     wins = [(3, 9), (5, 15), (7, 21)]
     out = []
     for i in range(n):
-        side = int(rng.integers(128, 1025))
+        side = int(rng.integers(side_lo, side_hi + 1))
         L = int(rng.choice([128, 188, 224]))
         w = wins[int(rng.integers(0, 3))]
         det = int(rng.integers(0, 3))
