@@ -61,6 +61,9 @@ def lib():
                                         i64p, ctypes.c_int64, dp, dp, ctypes.c_int]
         L.or_auc.argtypes = [dp, u8p, ctypes.c_int64]
         L.or_scene_whiten.argtypes = [ctypes.c_int, dp, ctypes.c_long, dp, dp]
+        L.or_cnn_forward_bf16act.argtypes = [ctypes.c_int, dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp]
+        L.or_bf16_round.argtypes = [ctypes.c_double]
+        L.or_bf16_round.restype = ctypes.c_double
         L.or_cnn_nparam.argtypes = [ctypes.c_int]
         L.or_cnn_nparam.restype = ctypes.c_long
         L.or_cnn_forward.argtypes = [ctypes.c_int, dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp]
@@ -209,6 +212,22 @@ def cnn_forward(params: np.ndarray, x: np.ndarray) -> np.ndarray:
     out = np.zeros((B, H, W))
     lib().or_cnn_forward(K, _ptr(p, ctypes.c_double), _ptr(xx, ctypes.c_double), B, H, W, _ptr(out, ctypes.c_double))
     return out
+
+
+def cnn_forward_bf16act(params: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """Screening CNN forward (FP64) with the inputs of the two 32 -> 32 layers rounded to
+    bfloat16 (the tensor-core inference form)."""
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    xx = np.ascontiguousarray(x, dtype=np.float64)
+    B, H, W, K = xx.shape
+    out = np.zeros((B, H, W))
+    lib().or_cnn_forward_bf16act(K, _ptr(p, ctypes.c_double), _ptr(xx, ctypes.c_double), B, H, W,
+                                 _ptr(out, ctypes.c_double))
+    return out
+
+
+def bf16_round(v: float) -> float:
+    return float(lib().or_bf16_round(float(v)))
 
 
 def cnn_grad(params: np.ndarray, x: np.ndarray, t: np.ndarray, edge: int = 7):

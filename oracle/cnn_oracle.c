@@ -87,7 +87,31 @@ static void conv_back(const double* in, const double* dz, int B, int H, int W, i
             }
 }
 
+/* v rounded to float32 (nearest) and then to bfloat16 (nearest, ties to even): the value a
+   float32 activation takes when a tensor-core layer reads it as bfloat16 (finite inputs) */
+double or_bf16_round(double v) {
+    float f = (float)v;
+    unsigned int u;
+    memcpy(&u, &f, sizeof u);
+    u = (u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u;
+    memcpy(&f, &u, sizeof f);
+    return (double)f;
+}
+
+static int forward_impl(int K, const double* params, const double* x, int B, int H, int W, int bf16_act, double* pred);
+
 int or_cnn_forward(int K, const double* params, const double* x, int B, int H, int W, double* pred) {
+    return forward_impl(K, params, x, B, H, W, 0, pred);
+}
+
+/* The same network with the inputs of the two 32 -> 32 layers (the ReLU outputs of layers 1
+   and 2) rounded to bfloat16: the inference form whose 32 -> 32 convolutions run on the
+   tensor cores with bfloat16 operands and float accumulation. */
+int or_cnn_forward_bf16act(int K, const double* params, const double* x, int B, int H, int W, double* pred) {
+    return forward_impl(K, params, x, B, H, W, 1, pred);
+}
+
+static int forward_impl(int K, const double* params, const double* x, int B, int H, int W, int bf16_act, double* pred) {
     long px = (long)B * H * W;
     double* a = (double*)malloc(sizeof(double) * px * 32);
     double* c = (double*)malloc(sizeof(double) * px * 32);
@@ -103,6 +127,8 @@ int or_cnn_forward(int K, const double* params, const double* x, int B, int H, i
         conv(in, B, H, W, ci, w, bias, co, k, out);
         if (l < 3)
             for (long i = 0; i < px * co; ++i) out[i] = out[i] > 0.0 ? out[i] : 0.0;
+        if (bf16_act && (l == 0 || l == 1))
+            for (long i = 0; i < px * co; ++i) out[i] = or_bf16_round(out[i]);
         in = out;
     }
     free(a); free(c);

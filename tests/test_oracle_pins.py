@@ -398,3 +398,38 @@ def test_scene_whitening_degenerate_inputs_stay_finite():
     assert np.isfinite(M).all()
     mu, M = oracle.scene_whiten(np.array([[1.0, 2.0]]))  # one pixel
     np.testing.assert_array_equal(M, np.eye(2))
+
+
+def test_bf16_rounding_closed_forms():
+    # bfloat16 keeps 8 significant bits: spacing 2^-7 on [1, 2); halfway cases go to the even
+    # neighbour
+    assert oracle.bf16_round(1.0) == 1.0
+    assert oracle.bf16_round(1.0 + 2.0 ** -8) == 1.0                      # tie -> even (1.0)
+    assert oracle.bf16_round(1.0 + 3 * 2.0 ** -8) == 1.0 + 2.0 ** -6       # tie -> even
+    assert oracle.bf16_round(1.0 + 2.0 ** -8 + 2.0 ** -12) == 1.0 + 2.0 ** -7  # above the tie
+    assert oracle.bf16_round(3.0) == 3.0 and oracle.bf16_round(0.0) == 0.0
+    assert oracle.bf16_round(-1.0 - 3 * 2.0 ** -8) == -(1.0 + 2.0 ** -6)
+    assert oracle.bf16_round(2.0 ** -130) == 0.0 or abs(oracle.bf16_round(2.0 ** -130)) < 2.0 ** -126
+
+
+def test_cnn_bf16_activation_forward_bounds():
+    K = 4
+    n = oracle.cnn_nparam(K)
+    rng = np.random.default_rng(35)
+    params = rng.standard_normal(n) * 0.05
+    x = rng.standard_normal((1, 12, 13, K))
+    exact = oracle.cnn_forward(params, x)
+    q = oracle.cnn_forward_bf16act(params, x)
+    # rounding perturbs each rounded activation by at most 2^-8 relative; the output moves by
+    # far less than the output scale, but does move
+    assert 0 < np.abs(q - exact).max() <= 2.0 ** -6 * np.abs(exact).max()
+    # identity when every rounded activation is already a bfloat16 value: all hidden weights
+    # of layers 1 and 2 zero and bfloat16-exact biases
+    p2 = params.copy()
+    w1 = 4 * 25 * 32
+    p2[:w1] = 0.0
+    p2[w1:w1 + 32] = 0.25                                  # layer-1 biases (bfloat16-exact)
+    o2 = w1 + 32
+    p2[o2:o2 + 32 * 25 * 32] = 0.0
+    p2[o2 + 32 * 25 * 32:o2 + 32 * 25 * 32 + 32] = 0.5    # layer-2 biases
+    np.testing.assert_array_equal(oracle.cnn_forward_bf16act(p2, x), oracle.cnn_forward(p2, x))
