@@ -1,6 +1,8 @@
 // C ABI of libwdad (declared in include/wdad.h): argument checking, the handle's
 // workspace and plan caches, and dispatch to the kernels.  No exception leaves
 // this file; every entry point returns a wdad_status.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <cstdarg>
 #include <cmath>
@@ -297,6 +299,7 @@ void cnn_free(wdad_cnn_ctx* c) {
     auto& n = c->net;
     cudaFree(n.w); cudaFree(n.wf); cudaFree(n.m); cudaFree(n.v); cudaFree(n.grad); cudaFree(n.wt);
     cudaFree(n.norm); cudaFree(n.stat); cudaFree(n.act); cudaFree(n.loss); cudaFree(n.cx); cudaFree(n.ct);
+    cudaFree(n.wpk); cudaFree(n.tcerr);
     delete c;
 }
 
@@ -714,6 +717,9 @@ wdad_status wdad_cnn_create(wdad_handle h, int K, int bf16_weights, uint64_t see
         if (e == cudaSuccess) e = cudaMalloc(&n.loss, sizeof(float));
         if (e == cudaSuccess) e = cudaMalloc(&n.cx, sizeof(float) * (size_t)max_batch_pixels * K);
         if (e == cudaSuccess) e = cudaMalloc(&n.ct, sizeof(float) * (size_t)max_batch_pixels);
+        if (e == cudaSuccess) e = cudaMalloc(&n.wpk, sizeof(__nv_bfloat16) * 2 * 25 * 32 * 32);
+        if (e == cudaSuccess) e = cudaMalloc(&n.tcerr, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(n.tcerr, 0, sizeof(int));
         if (e != cudaSuccess) { cnn_free(c); return cuda_fail(h, e, "cnn allocation"); }
         std::vector<float> norm((size_t)(K + K * K), 0.f);  // mu = 0, M = I until a scene sets it
         for (int k = 0; k < K; ++k) norm[K + k * K + k] = 1.f;
@@ -802,7 +808,7 @@ wdad_status wdad_cnn_forward(wdad_cnn c, const float* x, int B, int H, int W, fl
     if (c->net.norm_mode == 0) e = wdad::cnn::scene_whitening(x, px, c->net.K, c->net.stat, c->net.norm, (cudaStream_t)stream);
     if (e == cudaSuccess)
         e = wdad::cnn::net_forward(c->net, x, B, H, W, c->net.norm, a0, a0 + px * 32, a0 + px * 64, pred,
-                                   (cudaStream_t)stream);
+                                   (cudaStream_t)stream, c->net.bf16 != 0, h->num_sms);
     return e == cudaSuccess ? WDAD_OK : cuda_fail(h, e, "cnn forward");
 }
 
@@ -968,7 +974,8 @@ wdad_status wdad_screen_run(wdad_handle h, wdad_cnn c, const float* cube, int H,
             float* a1 = a0 + npx * 32;
             float* a2 = a1 + npx * 32;
             float* o = a2 + npx * 32;
-            e = wdad::cnn::net_forward(n, approx + (size_t)h0 * W * K, 1, hr, W, n.norm, a0, a1, a2, o, s);
+            e = wdad::cnn::net_forward(n, approx + (size_t)h0 * W * K, 1, hr, W, n.norm, a0, a1, a2, o, s,
+                                       n.bf16 != 0, h->num_sms);
             if (e == cudaSuccess)
                 e = cudaMemcpyAsync(pred + (size_t)r0 * W, o + (size_t)(r0 - h0) * W, sizeof(float) * (size_t)(r1 - r0) * W,
                                     cudaMemcpyDeviceToDevice, s);
@@ -990,6 +997,15 @@ wdad_status wdad_screen_run(wdad_handle h, wdad_cnn c, const float* cube, int H,
         if (e == cudaSuccess) e = cudaMemcpyAsync(&nsel, cnt, sizeof nsel, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_fail(h, e, "screen selection");
+        if (n.bf16) {
+            int tcerr = 0;
+            e = cudaMemcpy(&tcerr, n.tcerr, sizeof tcerr, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return cuda_fail(h, e, "screen status");
+            if (tcerr) {
+                cudaMemset(n.tcerr, 0, sizeof(int));
+                return fail(h, WDAD_ERR_TIMEOUT, "screen: a tensor-core convolution gave up waiting");
+            }
+        }
         if (n_selected) *n_selected = (int64_t)nsel;
         // unevaluated pixels score -inf; the exact detector fills the selected ones
         e = wdad::cnn::fill(score, P, -INFINITY, s);

@@ -440,11 +440,20 @@ static cudaError_t conv_bwd_weight(const float* in, const float* dz, int B, int 
 // Forward of the whole net on x [B][H][W][K] (already normalised unless norm != null);
 // activations a[0..2] (32 ch) and the prediction out [B][H][W].
 cudaError_t net_forward(const Net& n, const float* x, int B, int H, int W, const float* norm, float* a0, float* a1,
-                        float* a2, float* out, cudaStream_t s) {
+                        float* a2, float* out, cudaStream_t s, bool tc, int num_sms) {
     const float* wf = n.wf;
     cudaError_t e = conv_fwd(x, B, H, W, n.K, wf + n.woff[0], wf + n.boff[0], 32, 5, 1, norm, a0, s);
-    if (e == cudaSuccess) e = conv_fwd(a0, B, H, W, 32, wf + n.woff[1], wf + n.boff[1], 32, 5, 1, nullptr, a1, s);
-    if (e == cudaSuccess) e = conv_fwd(a1, B, H, W, 32, wf + n.woff[2], wf + n.boff[2], 32, 5, 1, nullptr, a2, s);
+    if (tc) {
+        __nv_bfloat16* p1 = n.wpk;
+        __nv_bfloat16* p2 = n.wpk + 25 * 32 * 32;
+        if (e == cudaSuccess) e = pack_w5(wf + n.woff[1], p1, s);
+        if (e == cudaSuccess) e = pack_w5(wf + n.woff[2], p2, s);
+        if (e == cudaSuccess) e = conv5_tc(a0, B, H, W, p1, wf + n.boff[1], 1, a1, n.tcerr, num_sms, s);
+        if (e == cudaSuccess) e = conv5_tc(a1, B, H, W, p2, wf + n.boff[2], 1, a2, n.tcerr, num_sms, s);
+    } else {
+        if (e == cudaSuccess) e = conv_fwd(a0, B, H, W, 32, wf + n.woff[1], wf + n.boff[1], 32, 5, 1, nullptr, a1, s);
+        if (e == cudaSuccess) e = conv_fwd(a1, B, H, W, 32, wf + n.woff[2], wf + n.boff[2], 32, 5, 1, nullptr, a2, s);
+    }
     if (e == cudaSuccess) e = conv_fwd(a2, B, H, W, 32, wf + n.woff[3], wf + n.boff[3], 1, 3, 0, nullptr, out, s);
     return e;
 }

@@ -1,5 +1,7 @@
 // Host-side declarations of the CNN screener (A9); kernels in cnn.cu.
 #pragma once
+#include <cuda_bf16.h>
+
 #include "internal.h"
 
 namespace wdad {
@@ -22,6 +24,8 @@ struct Net {
     float* act = nullptr;  // activations and gradients of one training batch
     float* loss = nullptr; // device scalar
     float *cx = nullptr, *ct = nullptr;  // crop buffers
+    __nv_bfloat16* wpk = nullptr;  // the two 32 -> 32 layers' weights packed for the tensor cores
+    int* tcerr = nullptr;          // set by a tensor-core convolution that gave up waiting
 };
 
 void layer_dims(int K, int l, int* cin, int* cout, int* k);
@@ -30,8 +34,13 @@ inline size_t act_floats(int64_t px) { return (size_t)px * (32 * 5 + 2); }
 
 cudaError_t conv_fwd(const float* in, int B, int H, int W, int Cin, const float* w, const float* bias, int Cout, int k,
                      int relu, const float* norm, float* out, cudaStream_t s);
+// tc: the 32 -> 32 layers on the tensor cores (bfloat16 activations; inference of networks
+// with bfloat16 weights); otherwise all layers in float32 SIMT
 cudaError_t net_forward(const Net& n, const float* x, int B, int H, int W, const float* norm, float* a0, float* a1,
-                        float* a2, float* out, cudaStream_t s);
+                        float* a2, float* out, cudaStream_t s, bool tc = false, int num_sms = 0);
+cudaError_t pack_w5(const float* w, __nv_bfloat16* packed, cudaStream_t s);
+cudaError_t conv5_tc(const float* in, int B, int H, int W, const __nv_bfloat16* wpk, const float* bias, int relu,
+                     float* out, int* err, int num_sms, cudaStream_t s);
 cudaError_t net_grad(Net& n, const float* x, const float* t, int B, int H, int W, cudaStream_t s);
 cudaError_t net_adam(Net& n, float lr, cudaStream_t s);
 cudaError_t net_init(Net& n, uint64_t seed, cudaStream_t s);

@@ -79,6 +79,13 @@ def test_whitening_rejects_empty_input(wd):
         wd.wdad_scene_whitening(torch.zeros((0, 4), device="cuda"))
 
 
+# Networks with bfloat16 weights infer with their 32 -> 32 layers on the tensor cores
+# (bfloat16 activations, float32 sums); the oracle's bfloat16-activation forward is their
+# definition.  Bar: float32 summation order, and the rare activation whose float32 and
+# float64 values round to different bfloat16 neighbours.
+TOL_TC = 1e-3
+
+
 def test_per_scene_forward_matches_oracle(wd):
     # default mode: the forward whitens its input with the input's own statistics
     net = wd.wdad_cnn(K=4, bf16_weights=True, seed=5)
@@ -88,8 +95,29 @@ def test_per_scene_forward_matches_oracle(wd):
     got = net.forward(torch.from_numpy(x).cuda()).cpu().numpy()
     mu, M = oracle.scene_whiten(x.astype(np.float64))
     z = (x.astype(np.float64) - mu) @ M.T
-    want = oracle.cnn_forward(bf16_round(net.params()).astype(np.float64), z)
-    assert np.abs(got - want).max() <= 1e-4 * np.abs(want).max()
+    want = oracle.cnn_forward_bf16act(bf16_round(net.params()).astype(np.float64), z)
+    assert np.abs(got - want).max() <= TOL_TC * np.abs(want).max()
+    net.close()
+
+
+@pytest.mark.parametrize("B,H,W", [(2, 20, 33), (1, 16, 8), (1, 17, 9), (3, 5, 70)])
+def test_tensor_core_forward_matches_oracle(wd, B, H, W):
+    """The tensor-core 32 -> 32 layers over ragged tiles (16 x 8 output tiles), several images,
+    with a fixed input map; against the oracle's bfloat16-activation forward, and off the
+    float32 forward by no more than the bfloat16 activation rounding allows."""
+    net = wd.wdad_cnn(K=4, bf16_weights=True, seed=B * 100 + H)
+    rng = np.random.default_rng(H * W)
+    mu = np.array([0.1, -0.2, 0.3, 0.0], np.float32)
+    M = np.tril(rng.uniform(0.5, 1.5, (4, 4))).astype(np.float32)
+    net.set_norm(np.concatenate([mu, M.ravel()]))
+    x = rng.standard_normal((B, H, W, 4)).astype(np.float32)
+    got = net.forward(torch.from_numpy(x).cuda()).cpu().numpy()
+    z = (x.astype(np.float64) - mu) @ M.astype(np.float64).T
+    p = bf16_round(net.params()).astype(np.float64)
+    want = oracle.cnn_forward_bf16act(p, z)
+    assert np.abs(got - want).max() <= TOL_TC * np.abs(want).max()
+    full = oracle.cnn_forward(p, z)
+    assert np.abs(got - full).max() <= 2.0 ** -6 * np.abs(full).max()
     net.close()
 
 
@@ -104,9 +132,9 @@ def test_screen_predictions_match_oracle_chain(wd):
                                             seed=1, tile_rows=16, exact_reduce=True, inner=5, outer=15)
     ap = oracle.dwt_approx(sc.cube)
     mu, M = oracle.scene_whiten(ap)
-    want = oracle.cnn_forward(bf16_round(net.params()).astype(np.float64), ((ap - mu) @ M.T)[None])[0]
+    want = oracle.cnn_forward_bf16act(bf16_round(net.params()).astype(np.float64), ((ap - mu) @ M.T)[None])[0]
     got = pred.cpu().numpy()
-    assert np.abs(got - want).max() <= 1e-4 * np.abs(want).max()
+    assert np.abs(got - want).max() <= TOL_TC * np.abs(want).max()
     # with no audit the selection is exactly the predictions at or above the k-th largest
     k = int(np.ceil(0.1 * got.size))
     thr = np.sort(got.ravel())[-k]
