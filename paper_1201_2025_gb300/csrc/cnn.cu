@@ -46,9 +46,9 @@ __global__ void __launch_bounds__(CT * CT) conv_fwd_kernel(const float* __restri
                                                            int k, int relu, const float* __restrict__ norm,
                                                            float* __restrict__ out) {
     extern __shared__ __align__(16) float sm[];
-    const int p = k / 2, T = CT + k - 1, taps = k * k;
+    const int p = k / 2, T = CT + k - 1, taps = k * k, XP = Cin + 1;
     float* ws = sm;                              // [Cin][taps][COUT]
-    float* xs = sm + (size_t)Cin * taps * COUT;  // [Cin][T][T]
+    float* xs = sm + (size_t)Cin * taps * COUT;  // [T][T][Cin + 1]: pixel-major, channel pitch padded
     const int tiles_x = (W + CT - 1) / CT, tiles_y = (H + CT - 1) / CT;
     const int b = blockIdx.x / (tiles_x * tiles_y);
     const int t = blockIdx.x % (tiles_x * tiles_y);
@@ -67,14 +67,15 @@ __global__ void __launch_bounds__(CT * CT) conv_fwd_kernel(const float* __restri
 #pragma unroll
                 for (int j = 0; j < 8; ++j)
                     if (j < Cin) z = fmaf(norm[Cin + ci * Cin + j], xv[j], z);
-                xs[(size_t)ci * T * T + i] = z;
+                xs[(size_t)i * XP + ci] = z;
             }
         }
     } else {
+        // channel fastest: a warp reads whole NHWC pixel records (coalesced)
         for (int i = threadIdx.x; i < Cin * T * T; i += blockDim.x) {
-            const int ci = i / (T * T), r = (i / T) % T, c = i % T;
-            const int y = y0 + r - p, x = x0 + c - p;
-            xs[i] = (y >= 0 && y < H && x >= 0 && x < W) ? in[(((size_t)b * H + y) * W + x) * Cin + ci] : 0.f;
+            const int pix = i / Cin, ci = i - pix * Cin;
+            const int y = y0 + pix / T - p, x = x0 + pix % T - p;
+            xs[(size_t)pix * XP + ci] = (y >= 0 && y < H && x >= 0 && x < W) ? in[(((size_t)b * H + y) * W + x) * Cin + ci] : 0.f;
         }
     }
     __syncthreads();
@@ -84,11 +85,11 @@ __global__ void __launch_bounds__(CT * CT) conv_fwd_kernel(const float* __restri
 #pragma unroll
     for (int co = 0; co < COUT; ++co) acc[co] = bias ? bias[co] : 0.f;
     for (int ci = 0; ci < Cin; ++ci) {
-        const float* xr = xs + (size_t)ci * T * T;
+        const float* xr = xs + ci;
         const float* wr = ws + (size_t)ci * taps * COUT;
         for (int ky = 0; ky < k; ++ky)
             for (int kx = 0; kx < k; ++kx) {
-                const float a = xr[(ty + ky) * T + tx + kx];
+                const float a = xr[(size_t)((ty + ky) * T + tx + kx) * XP];
                 const float* wt = wr + (ky * k + kx) * COUT;
 #pragma unroll
                 for (int co = 0; co < COUT; ++co) acc[co] = fmaf(a, wt[co], acc[co]);
@@ -407,7 +408,7 @@ static inline int grid_for(int64_t n, int threads, int cap = 4096) {
 
 cudaError_t conv_fwd(const float* in, int B, int H, int W, int Cin, const float* w, const float* bias, int Cout, int k,
                      int relu, const float* norm, float* out, cudaStream_t s) {
-    const size_t smem = sizeof(float) * ((size_t)Cin * k * k * Cout + (size_t)Cin * (CT + k - 1) * (CT + k - 1));
+    const size_t smem = sizeof(float) * ((size_t)Cin * k * k * Cout + (size_t)(Cin + 1) * (CT + k - 1) * (CT + k - 1));
     const int tiles = ((W + CT - 1) / CT) * ((H + CT - 1) / CT) * B;
     cudaError_t e;
     if (Cout == 32) {
