@@ -354,12 +354,20 @@ __device__ __forceinline__ uint32_t fkey(float f) {
     return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
-__global__ void hist_kernel(const float* __restrict__ v, int64_t n, uint32_t prefix, int shift, uint32_t mask_hi,
-                            unsigned int* __restrict__ hist) {
+// 256-bin histogram of key byte (key >> shift) & 0xFF among the keys whose higher bytes equal
+// prefix: per-block counts in shared memory, then one global add per non-empty bin
+__global__ void __launch_bounds__(256) hist_kernel(const float* __restrict__ v, int64_t n, uint32_t prefix, int shift,
+                                                   uint32_t mask_hi, unsigned int* __restrict__ hist) {
+    __shared__ unsigned int sh[256];
+    sh[threadIdx.x] = 0u;
+    __syncthreads();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t kk = fkey(v[i]);
-        if ((kk & mask_hi) == prefix) atomicAdd(&hist[(kk >> shift) & 0xFFFFu], 1u);
+        if ((kk & mask_hi) == prefix) atomicAdd(&sh[(kk >> shift) & 0xFFu], 1u);
     }
+    __syncthreads();
+    const unsigned int c = sh[threadIdx.x];
+    if (c) atomicAdd(&hist[threadIdx.x], c);
 }
 
 // selection: key >= thr (top fraction) or an audit draw below audit_frac; compacted list
@@ -377,6 +385,42 @@ __global__ void select_kernel(const float* __restrict__ v, int64_t n, uint32_t t
 __global__ void fill_kernel(float* __restrict__ v, int64_t n, float val) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         v[i] = val;
+}
+
+// Output layer of inference (32 -> 1, 3x3, no ReLU): one thread per output pixel reads the
+// nine neighbouring 32-channel records (float4, coalesced per record) and its weights from
+// shared memory ([tap][ci]).
+__global__ void __launch_bounds__(256) conv3_to1_kernel(const float* __restrict__ in, int B, int H, int W,
+                                                        const float* __restrict__ w, const float* __restrict__ bias,
+                                                        float* __restrict__ out) {
+    __shared__ __align__(16) float ws[9 * 32];
+    for (int i = threadIdx.x; i < 9 * 32; i += blockDim.x) {
+        const int tap = i / 32, ci = i % 32;
+        ws[i] = w[ci * 9 + tap];
+    }
+    __syncthreads();
+    const int64_t n = (int64_t)B * H * W;
+    const float b0 = bias[0];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % W), y = (int)((i / W) % H);
+        const int64_t b = i / ((int64_t)H * W);
+        float acc = b0;
+        for (int tap = 0; tap < 9; ++tap) {
+            const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
+            if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+            const float4* a = reinterpret_cast<const float4*>(in + ((b * H + yy) * W + xx) * 32);
+            const float4* wt = reinterpret_cast<const float4*>(ws + tap * 32);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const float4 u = __ldg(a + q), c = wt[q];
+                acc = fmaf(u.x, c.x, acc);
+                acc = fmaf(u.y, c.y, acc);
+                acc = fmaf(u.z, c.z, acc);
+                acc = fmaf(u.w, c.w, acc);
+            }
+        }
+        out[i] = acc;
+    }
 }
 
 // ---------------------------------------------------------------- host side
@@ -451,6 +495,12 @@ cudaError_t net_forward(const Net& n, const float* x, int B, int H, int W, const
         if (e == cudaSuccess) e = pack_w5(wf + n.woff[2], p2, s);
         if (e == cudaSuccess) e = conv5_tc(a0, B, H, W, p1, wf + n.boff[1], 1, a1, n.tcerr, num_sms, s);
         if (e == cudaSuccess) e = conv5_tc(a1, B, H, W, p2, wf + n.boff[2], 1, a2, n.tcerr, num_sms, s);
+        if (e == cudaSuccess) {
+            conv3_to1_kernel<<<grid_for((int64_t)B * H * W, 256), 256, 0, s>>>(a2, B, H, W, wf + n.woff[3],
+                                                                              wf + n.boff[3], out);
+            e = cudaGetLastError();
+        }
+        return e;
     } else {
         if (e == cudaSuccess) e = conv_fwd(a0, B, H, W, 32, wf + n.woff[1], wf + n.boff[1], 32, 5, 1, nullptr, a1, s);
         if (e == cudaSuccess) e = conv_fwd(a1, B, H, W, 32, wf + n.woff[2], wf + n.boff[2], 32, 5, 1, nullptr, a2, s);
@@ -557,25 +607,27 @@ cudaError_t sample_crops(const Net& n, const float* approx, const float* score, 
 }
 
 // k-th largest key threshold of v (two 16-bit radix passes over histograms)
+// k-th largest key (four 8-bit radix passes over 256-bin histograms); the key itself, so
+// every value at or above the k-th largest is selected
 cudaError_t top_threshold(const float* v, int64_t n, int64_t kth, unsigned int* hist, uint32_t* thr, cudaStream_t s) {
     uint32_t prefix = 0, mask = 0;
     int64_t need = kth;  // rank from the top, 1-based
-    unsigned int h[65536];
-    for (int pass = 0; pass < 2; ++pass) {
-        const int shift = pass == 0 ? 16 : 0;
-        cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(unsigned int) * 65536, s);
+    unsigned int h[256];
+    for (int pass = 0; pass < 4; ++pass) {
+        const int shift = 24 - 8 * pass;
+        cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(unsigned int) * 256, s);
         if (e != cudaSuccess) return e;
-        hist_kernel<<<grid_for(n, 256), 256, 0, s>>>(v, n, prefix, shift, mask, hist);
+        hist_kernel<<<grid_for(n, 256, 1024), 256, 0, s>>>(v, n, prefix, shift, mask, hist);
         e = cudaMemcpyAsync(h, hist, sizeof(h), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return e;
-        int bin = 65535;
+        int bin = 255;
         for (; bin > 0; --bin) {
             if ((int64_t)h[bin] >= need) break;
             need -= h[bin];
         }
         prefix |= (uint32_t)bin << shift;
-        mask |= 0xFFFFu << shift;
+        mask |= 0xFFu << shift;
     }
     *thr = prefix;
     return cudaSuccess;
