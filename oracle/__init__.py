@@ -60,6 +60,8 @@ def lib():
         L.or_window_moments.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         i64p, ctypes.c_int64, dp, dp, ctypes.c_int]
         L.or_auc.argtypes = [dp, u8p, ctypes.c_int64]
+        L.or_adaptive_threshold.argtypes = [dp, ctypes.c_int64, ctypes.c_double, dp, dp, dp, u8p]
+        L.or_adaptive_threshold.restype = ctypes.c_int64
         L.or_scene_whiten.argtypes = [ctypes.c_int, dp, ctypes.c_long, dp, dp]
         L.or_cnn_forward_bf16act.argtypes = [ctypes.c_int, dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp]
         L.or_bf16_round.argtypes = [ctypes.c_double]
@@ -241,6 +243,16 @@ def cnn_grad(params: np.ndarray, x: np.ndarray, t: np.ndarray, edge: int = 7):
     lib().or_cnn_grad(K, _ptr(p, ctypes.c_double), _ptr(xx, ctypes.c_double), _ptr(tt, ctypes.c_double), B, H, W, edge,
                       _ptr(g, ctypes.c_double), ctypes.byref(loss))
     return loss.value, g
+
+
+def adaptive_threshold(score: np.ndarray, z: float):
+    """Eq. 12 cut-off: (mu_d, sigma_d, tau, mask) over the finite entries of a score map."""
+    s = np.ascontiguousarray(score, dtype=np.float64)
+    mask = np.zeros(s.shape, dtype=np.uint8)
+    mu, sd, tau = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    lib().or_adaptive_threshold(_ptr(s, ctypes.c_double), s.size, float(z), ctypes.byref(mu), ctypes.byref(sd),
+                                ctypes.byref(tau), _ptr(mask, ctypes.c_uint8))
+    return mu.value, sd.value, tau.value, mask
 
 
 def auc(score: np.ndarray, mask: np.ndarray) -> float:

@@ -597,3 +597,29 @@ int or_num_threads(void) {
     return 1;
 #endif
 }
+
+/*
+ * Adaptive cut-off of Eq. 12: tau = mu_d + z * sigma_d, with mu_d and sigma_d the mean and the
+ * (population, 1/n) standard deviation of the anomaly matrix over its finite entries; a
+ * pixel is declared anomalous when its score exceeds tau (NaN scores never are).  Two
+ * passes.  Returns the number of finite scores; mask may be NULL.
+ */
+int64_t or_adaptive_threshold(const double* score, int64_t n, double z, double* mu, double* sigma, double* tau,
+                              uint8_t* mask) {
+    int64_t m = 0;
+    double s = 0.0;
+    for (int64_t i = 0; i < n; ++i)
+        if (isfinite(score[i])) { s += score[i]; ++m; }
+    const double mean = m > 0 ? s / (double)m : NAN;
+    double ss = 0.0;
+    for (int64_t i = 0; i < n; ++i)
+        if (isfinite(score[i])) ss += (score[i] - mean) * (score[i] - mean);
+    const double sd = m > 0 ? sqrt(ss / (double)m) : NAN;
+    const double t = mean + z * sd;
+    if (mu) *mu = mean;
+    if (sigma) *sigma = sd;
+    if (tau) *tau = t;
+    if (mask)
+        for (int64_t i = 0; i < n; ++i) mask[i] = (uint8_t)(isfinite(score[i]) && score[i] > t);
+    return m;
+}

@@ -433,3 +433,29 @@ def test_cnn_bf16_activation_forward_bounds():
     p2[o2:o2 + 32 * 25 * 32] = 0.0
     p2[o2 + 32 * 25 * 32:o2 + 32 * 25 * 32 + 32] = 0.5    # layer-2 biases
     np.testing.assert_array_equal(oracle.cnn_forward_bf16act(p2, x), oracle.cnn_forward(p2, x))
+
+
+# ---------------------------------------------------------------- adaptive threshold (Eq. 12)
+def test_adaptive_threshold_worked_example():
+    # scores 1..4: mean 2.5, population variance 1.25; z = 1 -> tau = 2.5 + sqrt(1.25)
+    mu, sd, tau, mask = oracle.adaptive_threshold(np.array([1.0, 2.0, 3.0, 4.0]), 1.0)
+    assert mu == 2.5 and abs(sd - np.sqrt(1.25)) < 1e-15 and abs(tau - (2.5 + np.sqrt(1.25))) < 1e-15
+    assert mask.tolist() == [0, 0, 0, 1]
+    # z = 0: the mean itself; equal scores are not above it
+    _, _, tau0, mask0 = oracle.adaptive_threshold(np.array([1.0, 2.0, 2.5, 4.0, 3.0]), 0.0)
+    assert tau0 == 2.5 and mask0.tolist() == [0, 0, 0, 1, 1]
+    # NaN entries neither count nor get declared
+    mu, sd, _, mask = oracle.adaptive_threshold(np.array([1.0, np.nan, 3.0]), 0.5)
+    assert mu == 2.0 and sd == 1.0 and mask.tolist() == [0, 0, 1]
+
+
+def test_adaptive_threshold_invariances_and_gaussian_rate():
+    rng = np.random.default_rng(36)
+    s = rng.standard_normal(200000)
+    _, _, _, m = oracle.adaptive_threshold(s, 2.0)
+    # shift and positive scale move tau with the scores: same decisions
+    _, _, _, m2 = oracle.adaptive_threshold(3.0 * s + 7.0, 2.0)
+    assert np.array_equal(m, m2)
+    # Gaussian scores: the declared fraction is the upper tail 1 - Phi(z) (0.02275 at z = 2)
+    from scipy.stats import norm
+    assert abs(m.mean() - norm.sf(2.0)) < 4 * np.sqrt(norm.sf(2.0) / len(s))
