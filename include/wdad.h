@@ -254,6 +254,17 @@ wdad_status wdad_screen_run(wdad_handle h, wdad_cnn c, const float* cube, int H,
                             float top_frac, float audit_frac, uint64_t seed, int tile_rows, int exact_reduce,
                             float* score, float* pred, uint8_t* selected, int64_t* n_selected, void* stream);
 
+/* Adaptive cut-off of Eq. 12 (Sec. 5.3.2): tau = mu_d + z_alpha * sigma_d, where mu_d and
+ * sigma_d are the mean and the population (1/n) standard deviation of the n finite entries of
+ * the anomaly matrix `score` (device, float32; NaN entries, e.g. border pixels, are left out);
+ * mask (device, n bytes, nullable) receives 1 where score > tau, else 0 (NaN -> 0).
+ * host_stats (host, 4 doubles, nullable) receives mu_d, sigma_d, tau, count, after the call
+ * synchronises `stream`; without it the call is asynchronous.  FP64 sums in a fixed order
+ * (the same on any GPU).  n == 0 gives NaN statistics and count 0.  Uses the handle's
+ * workspace; z_alpha must be finite (WDAD_ERR_ARG otherwise). */
+wdad_status wdad_adaptive_threshold(wdad_handle h, const float* score, int64_t n, double z_alpha, uint8_t* mask,
+                                    double* host_stats, void* stream);
+
 /* A10 — pixel-level ROC AUC of a score map against a truth mask (Sec. 5.3.1):
  * Mann-Whitney U with ties counted one half.  HOST pointers; NaN scores rank lowest.
  * Writes NaN when the mask has no positive or no negative pixel. */

@@ -1037,6 +1037,28 @@ wdad_status wdad_screen_run(wdad_handle h, wdad_cnn c, const float* cube, int H,
     }
 }
 
+wdad_status wdad_adaptive_threshold(wdad_handle h, const float* score, int64_t n, double z_alpha, uint8_t* mask,
+                                    double* host_stats, void* stream) {
+    if (!h) return WDAD_ERR_ARG;
+    if (n < 0 || (n > 0 && !score) || !std::isfinite(z_alpha))
+        return fail(h, WDAD_ERR_ARG, "threshold: n >= 0, score for n > 0, finite z");
+    try {
+        DeviceGuard g(h->device);
+        if (n == 0) {
+            if (host_stats) { host_stats[0] = host_stats[1] = host_stats[2] = NAN; host_stats[3] = 0.0; }
+            return WDAD_OK;
+        }
+        wdad_status st = ensure_ws(h, wdad::adaptive_threshold_workspace());
+        if (st != WDAD_OK) return st;
+        cudaStream_t s = (cudaStream_t)stream;
+        cudaError_t e = wdad::launch_adaptive_threshold(score, n, z_alpha, h->ws, mask, host_stats, h->num_sms, s);
+        if (e == cudaSuccess && host_stats) e = cudaStreamSynchronize(s);
+        return e == cudaSuccess ? WDAD_OK : cuda_fail(h, e, "adaptive threshold");
+    } catch (...) {
+        return fail(h, WDAD_ERR_NOMEM, "host exception");
+    }
+}
+
 wdad_status wdad_auc(const float* score, const uint8_t* mask, int64_t n, double* auc) {
     if (!auc || n < 0 || (n > 0 && (!score || !mask))) return WDAD_ERR_ARG;
     try {

@@ -387,39 +387,36 @@ __global__ void fill_kernel(float* __restrict__ v, int64_t n, float val) {
         v[i] = val;
 }
 
-// Output layer of inference (32 -> 1, 3x3, no ReLU): one thread per output pixel reads the
-// nine neighbouring 32-channel records (float4, coalesced per record) and its weights from
-// shared memory ([tap][ci]).
+// Output layer of inference (32 -> 1, 3x3, no ReLU): one warp per output pixel, lane = input
+// channel, so each neighbouring 32-channel record is one coalesced 128-byte load; the lanes'
+// products are summed over the taps and then across the warp (butterfly).
 __global__ void __launch_bounds__(256) conv3_to1_kernel(const float* __restrict__ in, int B, int H, int W,
                                                         const float* __restrict__ w, const float* __restrict__ bias,
                                                         float* __restrict__ out) {
-    __shared__ __align__(16) float ws[9 * 32];
-    for (int i = threadIdx.x; i < 9 * 32; i += blockDim.x) {
-        const int tap = i / 32, ci = i % 32;
-        ws[i] = w[ci * 9 + tap];
-    }
-    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    float wl[9];
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) wl[tap] = __ldg(w + lane * 9 + tap);
+    const float b0 = __ldg(bias);
     const int64_t n = (int64_t)B * H * W;
-    const float b0 = bias[0];
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int x = (int)(i % W), y = (int)((i / W) % H);
-        const int64_t b = i / ((int64_t)H * W);
-        float acc = b0;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t HW = (int64_t)H * W;
+    for (int64_t i = warp; i < n; i += nwarps) {
+        // one 64-bit division for the image; the rest in 32 bits (H * W < 2^31)
+        const int64_t b = B == 1 ? 0 : i / HW;
+        const int r = (int)(i - b * HW);
+        const int y = r / W, x = r - y * W;
+        float acc = 0.f;
+#pragma unroll
         for (int tap = 0; tap < 9; ++tap) {
             const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
-            if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
-            const float4* a = reinterpret_cast<const float4*>(in + ((b * H + yy) * W + xx) * 32);
-            const float4* wt = reinterpret_cast<const float4*>(ws + tap * 32);
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const float4 u = __ldg(a + q), c = wt[q];
-                acc = fmaf(u.x, c.x, acc);
-                acc = fmaf(u.y, c.y, acc);
-                acc = fmaf(u.z, c.z, acc);
-                acc = fmaf(u.w, c.w, acc);
-            }
+            if (yy >= 0 && yy < H && xx >= 0 && xx < W)
+                acc = fmaf(__ldg(in + ((b * H + yy) * W + xx) * 32 + lane), wl[tap], acc);
         }
-        out[i] = acc;
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) out[i] = acc + b0;
     }
 }
 
@@ -496,8 +493,8 @@ cudaError_t net_forward(const Net& n, const float* x, int B, int H, int W, const
         if (e == cudaSuccess) e = conv5_tc(a0, B, H, W, p1, wf + n.boff[1], 1, a1, n.tcerr, num_sms, s);
         if (e == cudaSuccess) e = conv5_tc(a1, B, H, W, p2, wf + n.boff[2], 1, a2, n.tcerr, num_sms, s);
         if (e == cudaSuccess) {
-            conv3_to1_kernel<<<grid_for((int64_t)B * H * W, 256), 256, 0, s>>>(a2, B, H, W, wf + n.woff[3],
-                                                                              wf + n.boff[3], out);
+            conv3_to1_kernel<<<grid_for((int64_t)B * H * W * 32, 256), 256, 0, s>>>(a2, B, H, W, wf + n.woff[3],
+                                                                                   wf + n.boff[3], out);
             e = cudaGetLastError();
         }
         return e;

@@ -57,6 +57,11 @@ cudaError_t launch_detect_small(const DetectArgs& a, int tile_h, cudaStream_t s)
 // exact tile height (the plan); default plan of a configuration
 cudaError_t launch_detect_small_th(const DetectArgs& a, int th, cudaStream_t s);
 int detect_small_default_th(int D, int inner, int outer);
+// Eq. 12 cut-off on a score map (ws: adaptive_threshold_workspace() bytes of device memory);
+// stats_out (host, nullable): mu, sigma, tau, count, copied asynchronously on st
+size_t adaptive_threshold_workspace();
+cudaError_t launch_adaptive_threshold(const float* s, int64_t n, double z, void* ws, uint8_t* mask, double* stats_out,
+                                      int num_sms, cudaStream_t st);
 // largest dynamic shared memory of a detector tile plan that still lets two CTAs share an SM
 size_t detect_small_two_per_sm_bytes();
 cudaError_t launch_window_census(int H, int W, int inner, int outer, int border, int64_t* out,

@@ -90,13 +90,14 @@ def lib() -> ctypes.CDLL:
     L.wdad_detect_all_noalloc.argtypes = [f32p, i32, i32, i32, pp, f32p, vp, vp]
     L.wdad_auc.argtypes = [vp, vp, i64, ctypes.POINTER(ctypes.c_double)]
     L.wdad_scene_whitening.argtypes = [vp, f32p, i64, i32, f32p, vp]
+    L.wdad_adaptive_threshold.argtypes = [vp, f32p, i64, ctypes.c_double, vp, vp, vp]
     for name in ("wdad_create", "wdad_destroy", "wdad_last_error_detail", "wdad_dwt_approx", "wdad_detect",
                  "wdad_detect_all", "wdad_detect_all_host", "wdad_window_census", "wdad_auc",
                  "wdad_detect_all_noalloc", "wdad_window_moments", "wdad_autotune", "wdad_batch_create",
                  "wdad_batch_launch", "wdad_batch_status", "wdad_batch_destroy", "wdad_batch_run",
                  "wdad_cnn_create", "wdad_cnn_destroy", "wdad_cnn_set_norm", "wdad_cnn_params",
                  "wdad_cnn_set_params", "wdad_cnn_forward", "wdad_cnn_grad", "wdad_cnn_train", "wdad_cnn_save",
-                 "wdad_cnn_load", "wdad_screen_run", "wdad_scene_whitening"):
+                 "wdad_cnn_load", "wdad_screen_run", "wdad_scene_whitening", "wdad_adaptive_threshold"):
         getattr(L, name).restype = i32
     L.wdad_query_K.restype = i32
     _lib = L
@@ -469,6 +470,21 @@ def wdad_window_census(H: int, W: int, params: wdad_params | None = None, device
     h = handle(device)
     _check(lib().wdad_window_census(h, H, W, ctypes.byref(p), out.data_ptr(), _stream(out)), h)
     return out
+
+
+def wdad_adaptive_threshold(score, z_alpha: float, mask=None, want_mask: bool = True):
+    """Eq. 12 cut-off of a CUDA score map: (mu_d, sigma_d, tau, count, mask uint8 or None)."""
+    import torch
+    score = score.contiguous()
+    n = score.numel()
+    if want_mask and mask is None:
+        mask = torch.empty(score.shape, device=score.device, dtype=torch.uint8)
+    stats = np.zeros(4, dtype=np.float64)
+    h = handle(score.device.index or 0)
+    _check(lib().wdad_adaptive_threshold(h, score.data_ptr() if n else None, n, float(z_alpha),
+                                         mask.data_ptr() if (mask is not None and n) else None, stats.ctypes.data,
+                                         _stream(score)), h)
+    return float(stats[0]), float(stats[1]), float(stats[2]), int(stats[3]), mask
 
 
 def wdad_auc(score, mask) -> float:
