@@ -30,7 +30,7 @@ def _check(wd, s, z):
 @pytest.mark.parametrize("n", [1, 7, 1000, 512 * 512, 1024 * 1024 + 13])
 @pytest.mark.parametrize("z", [0.0, 1.5, 2.33, -1.0])
 def test_threshold_matches_oracle(wd, n, z):
-    rng = np.random.default_rng(n + int(100 * z))
+    rng = np.random.default_rng(7 * n + int(100 * (z + 2)))
     s = (rng.chisquare(4, n) * rng.uniform(0.5, 2.0)).astype(np.float32)
     s[rng.random(n) < 0.01] = np.nan  # border-style NaN entries
     _check(wd, s, z)
