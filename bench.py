@@ -398,6 +398,17 @@ def run_ours(args):
             ms = _time(lambda: wdad.wdad_detect(approx, det, reduce=False, params=p, out=one))
             dwt_plus = dwt_ms + ms
             per_det[f"{name}@{wi}/{wo}"] = {"detector_ms": ms, "Mpixel_s_with_dwt": H * W / (dwt_plus * 1e-3) / 1e6}
+    # adaptive cut-off of Eq. 12 (z = 2.33, alpha = 0.01) on the three maps of window (5,15)
+    thr = {}
+    maps5 = out[WINDOWS.index((5, 15))]
+    for d, dn in enumerate(("lrx", "dwrx", "dwest")):
+        mk = torch.empty((H, W), dtype=torch.uint8, device=dev)
+        ms = _time(lambda: wdad.wdad_adaptive_threshold(maps5[d], 2.33, mask=mk), n=10)
+        mu_d, sd_d, tau, cnt, mk = wdad.wdad_adaptive_threshold(maps5[d], 2.33, mask=mk)
+        m = mk.cpu().numpy() > 0
+        thr[dn] = {"us_per_map": ms * 1e3, "tau": tau, "declared_fraction": float(m.mean()),
+                   "implanted_recall": float((m & (sc.mask > 0)).sum() / max(1, (sc.mask > 0).sum()))}
+    thr["workload"] = "DWT-reduced maps of the 512x512x224 cube at window (5,15), z_alpha = 2.33"
     full = {}
     if not args.no_full:
         rows = args.full_rows
@@ -453,7 +464,8 @@ def run_ours(args):
     breakdown = {"dwt_ms": dwt_ms, "detect_ms": dict(zip([f"{a}/{b}" for a, b in WINDOWS], det_ms)),
                  "step_algorithmic_GBps": step_bytes / (ms_step * 1e-3) / 1e9,
                  "step_frac_of_hbm": step_bytes / (ms_step * 1e-3) / 1e9 / peak, "per_detector": per_det,
-                 "fullband_fp32": full, "mixed_precision": mixed, "batching": batching, "screening": screening}
+                 "adaptive_threshold": thr, "fullband_fp32": full, "mixed_precision": mixed, "batching": batching,
+                 "screening": screening}
 
     # end to end through the host-buffer entry point: H2D cube, DWT, 3 windows, D2H 9 maps
     hc = torch.from_numpy(sc.cube).pin_memory()

@@ -64,12 +64,34 @@ def _noise(rng: np.random.Generator, shape, sigma: float, ar_rho: float) -> np.n
     return out
 
 
+def adjacency_fraction(frac: np.ndarray, w: float) -> np.ndarray:
+    """Eq. 11: background pixels within one pixel of a target (the 8-neighbourhood ring) take
+    the target spectrum with weight exp(-rho^2 / w^2) f, rho their distance to the target pixel
+    and f its abundance (the largest such weight over neighbouring target pixels).  Returns the
+    effective fraction map: frac on targets, that weight on the ring, 0 elsewhere."""
+    H, W = frac.shape
+    g = np.zeros_like(frac)
+    for dy in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            if dy == 0 and dx == 0:
+                continue
+            sh = np.zeros_like(frac)
+            ys, yd = (slice(max(dy, 0), H + min(dy, 0)), slice(max(-dy, 0), H + min(-dy, 0)))
+            xs, xd = (slice(max(dx, 0), W + min(dx, 0)), slice(max(-dx, 0), W + min(-dx, 0)))
+            sh[yd, xd] = frac[ys, xs]  # abundance of the target pixel at offset (dy, dx)
+            g = np.maximum(g, np.exp(-(dy * dy + dx * dx) / (w * w)) * sh)
+    return np.where(frac > 0, frac, g)
+
+
 def make_scene(H: int, W: int, L: int, seed: int = 0, *, n_anom: int = 10,
                anom_side=(2, 2), abundance=(0.3, 0.3), margin: int = 6,
-               sigma: float = 0.005, ar_rho: float = 0.0,
+               sigma: float = 0.005, ar_rho: float = 0.0, adjacency_w: float | None = None,
                row_block: int = 256) -> Scene:
     """Draw one scene.  anom_side=(a, b) draws square targets of side U{a..b};
-    abundance=(lo, hi) draws f ~ U(lo, hi) per target (lo == hi: fixed)."""
+    abundance=(lo, hi) draws f ~ U(lo, hi) per target (lo == hi: fixed); adjacency_w > 0 adds
+    the adjacency effect of Eq. 11 with that width on the ring around the targets (the truth
+    mask stays the target pixels).  No random numbers are drawn for the adjacency effect, so a
+    seed gives the same targets and background with and without it."""
     rng = np.random.default_rng(seed)
     E = endmember_spectra(rng, L, 6)
     frac = np.zeros((H, W), dtype=np.float64)
@@ -81,6 +103,7 @@ def make_scene(H: int, W: int, L: int, seed: int = 0, *, n_anom: int = 10,
         y0 = int(rng.integers(lo_y, hi_y + 1))
         x0 = int(rng.integers(lo_x, hi_x + 1))
         frac[y0:y0 + side, x0:x0 + side] = f
+    eff = adjacency_fraction(frac, adjacency_w) if adjacency_w else frac
     cube = np.empty((H, W, L), dtype=np.float32)
     # rows are drawn block by block so large cubes never need a float64 copy
     for r0 in range(0, H, row_block):
@@ -89,8 +112,8 @@ def make_scene(H: int, W: int, L: int, seed: int = 0, *, n_anom: int = 10,
         b = np.zeros((r1 - r0, W, L), dtype=np.float64)
         for k in range(5):
             b += ab[..., k:k + 1] * E[k][None, None, :]
-        f = frac[r0:r1, :, None]
-        z = f * E[5][None, None, :] + (1.0 - f) * b  # Eq. 10 (identity where f == 0)
+        f = eff[r0:r1, :, None]
+        z = f * E[5][None, None, :] + (1.0 - f) * b  # Eq. 10 / Eq. 11 (identity where f == 0)
         z += _noise(rng, (r1 - r0, W, L), sigma, ar_rho)
         cube[r0:r1] = z.astype(np.float32)
     return Scene(cube=cube, mask=(frac > 0).astype(np.uint8), endmembers=E, abundance=frac)
