@@ -109,13 +109,16 @@ wdad_status wdad_detect_all(wdad_handle h, const float* cube, int H, int W, int 
                             float* scores, uint8_t* flags, void* stream);
 
 /* The same pass from HOST memory, for callers whose cube lives on the host: the
- * cube is copied to the handle's workspace on `stream`, reduced once (reduce = 1),
- * all three detectors run for each of the nwin parameter sets params[0..nwin-1]
- * (same wavelet and level), and the score maps are copied back to host_scores,
- * laid out [nwin][3][H][W] (LRX, DWRX, DWEST).  host_cube and host_scores are
- * HOST pointers; page-locked memory makes the copies asynchronous, pageable
- * memory makes them synchronous.  The caller synchronises `stream` before
- * reading host_scores. */
+ * cube is reduced once (reduce = 1), all three detectors run for each of the nwin
+ * parameter sets params[0..nwin-1] (same wavelet and level), and the score maps are
+ * copied back to host_scores, laid out [nwin][3][H][W] (LRX, DWRX, DWEST).
+ * host_cube and host_scores are HOST pointers.  With reduce = 1 and a page-locked
+ * host_cube (cudaMallocHost / cudaHostRegister, device-mapped), the DWT reads the
+ * cube in place over the host link (each spectrum once, no staging copy); otherwise
+ * the cube is first copied to the handle's workspace on `stream`.  Page-locked memory
+ * makes the copies asynchronous, pageable memory makes them synchronous.  The caller
+ * synchronises `stream` before reading host_scores, and keeps host_cube unchanged until
+ * then. */
 wdad_status wdad_detect_all_host(wdad_handle h, const float* host_cube, int H, int W, int L, int reduce,
                                  int nwin, const wdad_params* params, float* host_scores, void* stream);
 

@@ -461,7 +461,18 @@ wdad_status wdad_detect_all_host(wdad_handle h, const float* host_cube, int H, i
             if (st != WDAD_OK) return st;
             full = std::max(full, need);
         }
-        const size_t b_cube = align256(sizeof(float) * (size_t)P * L);
+        // A page-locked, device-mapped cube is read by the DWT in place (over the host link):
+        // the reduced path reads every spectrum once, so a staging copy would only add a pass.
+        const float* mapped = nullptr;
+        if (reduce) {
+            cudaPointerAttributes at{};
+            if (cudaPointerGetAttributes(&at, host_cube) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+                at.devicePointer)
+                mapped = static_cast<const float*>(at.devicePointer);
+            else
+                cudaGetLastError();  // not registered with CUDA: staged below
+        }
+        const size_t b_cube = mapped ? 0 : align256(sizeof(float) * (size_t)P * L);
         const size_t b_red = reduce ? align256(sizeof(float) * (size_t)P * D) : 0;
         const size_t b_out = align256(sizeof(float) * (size_t)P * 3 * nwin);
         wdad_status st = ensure_ws(h, b_cube + b_red + b_out + full);
@@ -471,15 +482,18 @@ wdad_status wdad_detect_all_host(wdad_handle h, const float* host_cube, int H, i
         float* d_red = (float*)(base + b_cube);
         float* d_out = (float*)(base + b_cube + b_red);
         void* scratch = base + b_cube + b_red + b_out;
-        cudaError_t e = cudaMemcpyAsync(d_cube, host_cube, sizeof(float) * (size_t)P * L, cudaMemcpyHostToDevice, s);
-        if (e != cudaSuccess) return cuda_fail(h, e, "copy cube to device");
-        const float* x = d_cube;
+        cudaError_t e = cudaSuccess;
+        if (!mapped) {
+            e = cudaMemcpyAsync(d_cube, host_cube, sizeof(float) * (size_t)P * L, cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) return cuda_fail(h, e, "copy cube to device");
+        }
+        const float* x = mapped ? mapped : d_cube;
         if (reduce) {
             const float* A = nullptr;
             int k2 = 0;
             st = get_dwt_plan(h, L, params[0].wavelet_taps, params[0].level, &A, &k2, s);
             if (st != WDAD_OK) return st;
-            e = wdad::launch_dwt_approx(d_cube, P, L, A, D, d_red, h->num_sms, s);
+            e = wdad::launch_dwt_approx(x, P, L, A, D, d_red, h->num_sms, s);
             if (e != cudaSuccess) return cuda_fail(h, e, "dwt_approx launch");
             x = d_red;
         }

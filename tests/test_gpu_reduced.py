@@ -214,8 +214,12 @@ def test_reduced_detectors_512_sampled(wd, scene512, win):
     assert dwest_relerr(got[2].ravel()[pix], want, aux)[ok].max() <= TOL_SCORE
 
 
-def test_host_entry_point_matches_device_path(wd, scene48):
-    hc = torch.from_numpy(scene48.cube).pin_memory()
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_entry_point_matches_device_path(wd, scene48, pinned):
+    # pinned: the DWT reads the host cube in place; pageable: staged by a copy
+    hc = torch.from_numpy(scene48.cube.copy())
+    if pinned:
+        hc = hc.pin_memory()
     wins = [(3, 9), (5, 15)]
     params = [wd.wdad_default_params(inner=a, outer=b) for a, b in wins]
     out = wd.wdad_detect_all_host(hc, params=params)
