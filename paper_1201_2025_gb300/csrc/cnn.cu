@@ -14,7 +14,9 @@
 // a forward convolution of the output gradient), ReLU masks, MSE loss on the interior of
 // each crop, Adam, crop sampling, the scene whitening of the input (the network sees
 // z = M (x - mu), with mu and M = L^{-1}, C = L L^T, the mean and covariance of the scene's
-// approximation matrix), and for screening a radix threshold and an audit draw.
+// approximation matrix), the output layer of inference (conv3_to1), and for screening a
+// radix threshold and an audit draw.  At inference, networks with BF16 weights run their
+// two 32-channel layers on the tensor cores (cnn_tc.cu).
 // Random numbers come from splitmix64 (Steele, Lea, Flood 2014) on (seed, counter).
 #include <cuda_bf16.h>
 
@@ -603,7 +605,6 @@ cudaError_t sample_crops(const Net& n, const float* approx, const float* score, 
     return cudaGetLastError();
 }
 
-// k-th largest key threshold of v (two 16-bit radix passes over histograms)
 // k-th largest key (four 8-bit radix passes over 256-bin histograms); the key itself, so
 // every value at or above the k-th largest is selected
 cudaError_t top_threshold(const float* v, int64_t n, int64_t kth, unsigned int* hist, uint32_t* thr, cudaStream_t s) {
