@@ -49,7 +49,8 @@ typedef enum { WDAD_LRX = 0, WDAD_DWRX = 1, WDAD_DWEST = 2 } wdad_detector;
 
 typedef enum {
     WDAD_PREC_FP32 = 0,   /* FP32 statistics and solves */
-    WDAD_PREC_MIXED = 1,  /* full band: BF16 tensor-core Gram, FP32 solve, FP64 re-solve above cond_gate */
+    WDAD_PREC_MIXED = 1,  /* full band: BF16 tensor-core Gram (FP32 sample Gram for LRX/DWRX when N < L),
+                             FP32 solve, FP64 re-solve above cond_gate */
     WDAD_PREC_FP64 = 2    /* full band: FP64 statistics and solves for every pixel */
 } wdad_precision;
 
@@ -94,7 +95,11 @@ wdad_status wdad_dwt_approx(wdad_handle h, const float* cube, int H, int W, int 
 /* A2-A6 — one detector on every pixel (Sec. 2, Eq. 1-5).
  * reduce = 1: DWT-reduced path (A1 into the handle's workspace, then the detector
  * on K bands — "DWT-LRX/DWRX/DWEST" of Sec. 5.2); reduce = 0: the detector on
- * the L-band cube as given.  score: [H][W] float32.
+ * the L-band cube as given.  score: [H][W] float32.  On the full band, LRX and DWRX
+ * with fewer background samples than bands (N = outer^2 - inner^2 < L, loading > 0) are
+ * solved at dimension N: with Xt = (X - mu_o) / sqrt(N) (L x N), C_o = Xt Xt^T and
+ * d^T (C_o + delta I)^-1 d = (d^T d - |L_M^-1 Xt^T d|^2) / delta, L_M L_M^T = Xt^T Xt + delta I
+ * (Woodbury identity); the result is the same quantity as the L x L solve.
  * flags (nullable): [H][W] uint8 per pixel; bit 0 = re-solved in FP64 (MIXED),
  * bit 1 = covariance not positive definite (score NaN), bit 2 = outside the
  * valid region (border = 1). */

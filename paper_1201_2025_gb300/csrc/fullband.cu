@@ -67,6 +67,16 @@ __device__ __forceinline__ void tri_rc(int u, int& r, int& c) {
     c = u - r * (r + 1) / 2;
 }
 
+// four consecutive values from a 16-byte aligned shared-memory address
+__device__ __forceinline__ void ld4(const float* p, float (&o)[4]) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&o)[4]) {
+    const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+
 // ---- window sample offsets in row-major order (background = outer square minus inner)
 __device__ __forceinline__ void bg_offset(int s, int ro, int ri, int& dy, int& dx) {
     const int wo = 2 * ro + 1, wi = 2 * ri + 1, side = ro - ri;
@@ -137,6 +147,8 @@ struct Smem {
 
 struct Geo {
     int D, Dp, nt, ntl, S, mcap;
+    int N, Np;         // background samples (outer^2 - inner^2), padded to 4
+    bool wood;         // LRX / DWRX through the N x N sample Gram (Woodbury), N < D
     bool a_in_smem;
     bool tc;           // window Gram on the tensor cores (mixed precision, D <= 256)
     bool pan_in_tc;    // Cholesky panel buffer inside the (then idle) tensor-core chunk buffers
@@ -154,7 +166,7 @@ constexpr size_t kTcBufBytes = 2 * 256 * 64 * 2;  // two BF16 chunk buffers (TC_
 // ---- statistics ---------------------------------------------------------------
 // mean over a sample list (kind 0 = background, 1 = inner) into out[0..Dp).  The samples
 // are split into G interleaved groups (G threads per band, G <= S so that the partial sums
-// fit the sample-chunk buffer `part`); each thread keeps four loads in flight, and the G
+// fit the sample-chunk buffer `part`); each thread keeps eight loads in flight, and the G
 // partial sums of a band are added in group order.  Ends with a barrier.
 template <typename T>
 __device__ void sample_mean(const float* __restrict__ x, int H, int W, const Geo& g, int py, int px, int kind,
@@ -167,17 +179,17 @@ __device__ void sample_mean(const float* __restrict__ x, int H, int W, const Geo
         T acc[4] = {T(0), T(0), T(0), T(0)};
         if (b < D) {
             int s = grp;
-            for (; s + 3 * G < n; s += 4 * G) {
-                float v[4];
+            for (; s + 7 * G < n; s += 8 * G) {
+                float v[8];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < 8; ++u) {
                     int dy, dx;
                     if (kind == 0) bg_offset(s + u * G, ro, ri, dy, dx); else in_offset(s + u * G, ri, dy, dx);
                     const size_t q = (size_t)reflect101(py + dy, H) * W + reflect101(px + dx, W);
                     v[u] = __ldg(x + q * D + b);
                 }
 #pragma unroll
-                for (int u = 0; u < 4; ++u) acc[u] += (T)v[u];
+                for (int u = 0; u < 8; ++u) acc[u & 3] += (T)v[u];
             }
             for (; s < n; s += G) {
                 int dy, dx;
@@ -227,8 +239,8 @@ __device__ void gram_accumulate(const float* __restrict__ x, int H, int W, const
             for (int s = 0; s < ns; ++s) {
                 const T* row = xs + (size_t)s * g.Dp;
                 T ai[4], bk[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) { ai[e] = row[4 * I + e]; bk[e] = row[4 * K + e]; }
+                ld4(row + 4 * I, ai);
+                ld4(row + 4 * K, bk);
 #pragma unroll
                 for (int rr = 0; rr < 4; ++rr)
 #pragma unroll
@@ -351,6 +363,76 @@ __device__ void gram_tc(const float* __restrict__ x, int H, int W, const Geo& g,
     __syncthreads();
 }
 
+// Sample Gram of the background window for the Woodbury form of LRX / DWRX (N < D):
+// G = Xt^T Xt (N x N, tile-packed with gw's geometry) and b_k = Xt^T d_k, Xt = sc (X - mu)
+// with the N background samples as columns, accumulated over chunks of BC bands.  A chunk
+// is staged band-major (xs[b * SP + s], SP = Np + 4): the tile products read four samples
+// as one float4.  Staging: thread (bb, s0) loads band c0 + bb of samples s0, s0 + SL, ...
+// (coalesced along the bands, eight loads in flight); the samples' pixel offsets are
+// computed once into qoff.
+template <typename T>
+__device__ void gram_samples(const float* __restrict__ x, int H, int W, const Geo& g, const Geo& gw, int py, int px,
+                             int ro, int ri, const T* mu, T sc, T* A, T* xs, const T* d1, const T* d2, T* b1, T* b2,
+                             int* qoff) {
+    const int SP = gw.Dp + 4;
+    const int BC = max(4, min(64, (g.S * g.Dp / SP) & ~3));
+    const int SL = FB_THREADS / BC;
+    const int bb = threadIdx.x % BC, s0 = threadIdx.x / BC;
+    for (int smp = threadIdx.x; smp < g.N; smp += FB_THREADS) {
+        int dy, dx;
+        bg_offset(smp, ro, ri, dy, dx);
+        qoff[smp] = reflect101(py + dy, H) * W + reflect101(px + dx, W);
+    }
+    for (int c0 = 0; c0 < g.Dp; c0 += BC) {
+        __syncthreads();
+        if (s0 < SL) {
+            const int band = c0 + bb;
+            const bool inb = band < g.D;
+            const T mub = inb ? mu[band] : T(0);
+            for (int smp = s0; smp < gw.Dp; smp += 8 * SL) {
+                float v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int sm = smp + u * SL;
+                    v[u] = (inb && sm < g.N) ? __ldg(x + (size_t)qoff[sm] * g.D + band) : 0.f;
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int sm = smp + u * SL;
+                    if (sm < gw.Dp) xs[(size_t)bb * SP + sm] = (inb && sm < g.N) ? ((T)v[u] - mub) * sc : T(0);
+                }
+            }
+        }
+        __syncthreads();
+        const int nbb = min(BC, g.Dp - c0);
+        for (int u = threadIdx.x; u < gw.ntl; u += FB_THREADS) {
+            int I, K;
+            tri_rc(u, I, K);
+            T acc[16];
+            tile_load(A, gw.ntl, u, acc);
+            for (int k = 0; k < nbb; ++k) {
+                const T* row = xs + (size_t)k * SP;
+                T ai[4], bk[4];
+                ld4(row + 4 * I, ai);
+                ld4(row + 4 * K, bk);
+#pragma unroll
+                for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+                    for (int cc = 0; cc < 4; ++cc) acc[rr * 4 + cc] += ai[rr] * bk[cc];
+            }
+            tile_store(A, gw.ntl, u, acc);
+        }
+        for (int t = threadIdx.x; t < 2 * gw.Dp; t += FB_THREADS) {
+            const int smp = t % gw.Dp;
+            const T* d = t < gw.Dp ? d1 : d2;
+            T acc = T(0);
+            for (int k = 0; k < nbb; ++k) acc += xs[(size_t)k * SP + smp] * d[c0 + k];
+            (t < gw.Dp ? b1 : b2)[smp] += acc;
+        }
+    }
+    __syncthreads();
+}
+
 template <typename T>
 __device__ void mat_zero(T* A, const Geo& g) {
     const int n = ntiles_of(g.nt) * 16;
@@ -366,8 +448,9 @@ __device__ void mat_scale(T* A, const Geo& g, T s) {
 }
 
 // ---- blocked Cholesky of the tile-packed matrix, bordered by the two right-hand sides.
-// Right-looking in steps of NB = 32 columns (8 tile columns):
-//   (1) one warp factors the 32 x 32 diagonal block in registers (lane i holds row i; the
+// Right-looking in steps of NB = 16 columns (4 tile columns; the per-panel critical paths
+// of (1) and (2) grow with NB, and 16 beat 32 at every size measured):
+//   (1) one warp factors the 16 x 16 diagonal block in registers (lane i holds row i; the
 //       column of L each step needs comes by shuffles) and writes L_kk densely at the head
 //       of the panel buffer, with 1 / L_jj in column NB;
 //   (2) one thread per row below the block, and one for each right-hand side, solves
@@ -380,9 +463,9 @@ __device__ void mat_scale(T* A, const Geo& g, T s) {
 // y1 = L^-1 r1 and y2 = L^-1 r2 and no separate solve is needed.  Pivots use rsqrt (1/L_jj
 // directly).  Padding rows (D <= b < Dp) are identity.  Returns false, leaving *flag = 1, if
 // a pivot is not above `floor`; L_jj is left on A's diagonal.
-constexpr int NB = 32;
-constexpr int PP = 36;  // panel pitch (16-byte aligned rows)
-constexpr int LP = 33;  // pitch of the dense diagonal block at the head of the panel buffer
+constexpr int NB = 16;
+constexpr int PP = 20;  // panel pitch (16-byte aligned rows; 20 words apart, float4 reads of 8 rows hit distinct banks)
+constexpr int LP = 17;  // pitch of the dense diagonal block at the head of the panel buffer
 
 template <typename T>
 __host__ __device__ inline size_t pan_bytes(int Dp) {
@@ -390,14 +473,6 @@ __host__ __device__ inline size_t pan_bytes(int Dp) {
 }
 __device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
-__device__ __forceinline__ void ld4(const float* p, float (&o)[4]) {
-    const float4 v = *reinterpret_cast<const float4*>(p);
-    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
-}
-__device__ __forceinline__ void ld4(const double* p, double (&o)[4]) {
-    const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
-    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
-}
 
 template <typename T>
 __device__ bool cholesky_bordered(T* A, const Geo& g, T floor, int* flag, T* y1, T* y2, T* pan) {
@@ -823,53 +898,115 @@ __device__ unsigned process_pixel(const FullArgs& a, const Geo& g, Smem<T>& m, S
             m.r1[b] = b < D ? c - m.mu_o[b] : T(0);
             m.r2[b] = b < D ? m.mu_i[b] - m.mu_o[b] : T(0);
         }
-        mat_zero(m.A, g);
-        if constexpr (sizeof(T) == 4) {
-            if (g.tc) gram_tc(a.x, a.H, a.W, g, py, px, 0, N, ro, ri, m.mu_o, 1.f / (float)N, m.A, *st);
-        }
-        if (!g.tc) {
-            gram_accumulate<T>(a.x, a.H, a.W, g, py, px, 0, N, ro, ri, m.mu_o, T(1), m.A, m.xs);
-            mat_scale(m.A, g, T(1) / (T)N);
-        }
-        T tr = T(0), dmax = T(0);
-        for (int b = threadIdx.x; b < D; b += FB_THREADS) {
-            tr += el(m.A, g.ntl, b, b);
-            dmax = max(dmax, el(m.A, g.ntl, b, b));
-        }
-        tr = block_sum(tr, m.red);
-        dmax = block_max(dmax, m.red);
-        const T delta = (T)a.loading * tr / (T)D;
-        for (int b = threadIdx.x; b < D; b += FB_THREADS) el(m.A, g.ntl, b, b) += delta;
-        __syncthreads();
-        bool ok = cholesky_bordered(m.A, g, T(16) * Num<T>::eps * (dmax + delta), m.flag, m.r1, m.r2, m.pan);
-        if (ok && gate) {
-            // kappa estimate from the factor's diagonal: (max L_ii / min L_ii)^2
-            T lmax = T(0), lmin = T(3e38);
-            for (int b = threadIdx.x; b < D; b += FB_THREADS) {
-                const T l = el(m.A, g.ntl, b, b);
-                lmax = max(lmax, l);
-                lmin = min(lmin, l);
+        if (g.wood) {
+            // Fewer samples than bands: C = Xt Xt^T (Xt = (X - mu_o) / sqrt(N), D x N) has rank
+            // below D, and by the Woodbury identity
+            //   d^T (C + delta I)^-1 d = (d^T d - |L^-1 Xt^T d|^2) / delta,  L L^T = Xt^T Xt + delta I,
+            // so the factorisation runs at dimension N instead of D.  In mixed precision this
+            // FP32 form replaces the BF16 Gram: it is both cheaper and more accurate here.
+            Geo gw = g;
+            gw.D = g.N;
+            gw.Dp = g.Np;
+            gw.nt = g.Np / 4;
+            gw.ntl = ntiles_of(gw.nt);
+            for (int b = threadIdx.x; b < gw.Dp; b += FB_THREADS) { m.v[b] = T(0); m.p[b] = T(0); }
+            mat_zero(m.A, gw);
+            gram_samples<T>(a.x, a.H, a.W, g, gw, py, px, ro, ri, m.mu_o, T(1) / Num<T>::sqrt_((T)N), m.A, m.xs,
+                            m.r1, m.r2, m.v, m.p, reinterpret_cast<int*>(m.dd));
+            T tr = T(0), dmax = T(0), d1 = T(0), d2 = T(0), fro = T(0);
+            for (int b = threadIdx.x; b < N; b += FB_THREADS) {
+                tr += el(m.A, gw.ntl, b, b);
+                dmax = max(dmax, el(m.A, gw.ntl, b, b));
             }
-            lmax = block_max(lmax, m.red);
-            lmin = -block_max(-lmin, m.red);
-            const T kap = (lmax / lmin) * (lmax / lmin);
-            if (!(kap <= (T)a.cond_gate)) redo |= want & 3u;
-        }
-        if (!ok && gate) redo |= want & 3u;
-        if (ok) {
-            T q1 = T(0), q2 = T(0);
-            for (int b = threadIdx.x; b < D; b += FB_THREADS) { q1 += m.r1[b] * m.r1[b]; q2 += m.r2[b] * m.r2[b]; }
-            q1 = block_sum(q1, m.red);
-            q2 = block_sum(q2, m.red);
-            if (threadIdx.x == 0) {
-                if ((want & 1u) && a.out[0]) a.out[0][pix] = (float)q1;
-                if ((want & 2u) && a.out[1]) a.out[1][pix] = (float)fabs(q2);
+            if (gate) {  // |G|_F^2: off-diagonal tiles stand for both triangles
+                for (int u = threadIdx.x; u < gw.ntl; u += FB_THREADS) {
+                    int I, K;
+                    tri_rc(u, I, K);
+                    T q = T(0);
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) q += m.A[e * gw.ntl + u] * m.A[e * gw.ntl + u];
+                    fro += I == K ? q : T(2) * q;
+                }
+                fro = block_sum(fro, m.red);
+            }
+            for (int b = threadIdx.x; b < D; b += FB_THREADS) { d1 += m.r1[b] * m.r1[b]; d2 += m.r2[b] * m.r2[b]; }
+            tr = block_sum(tr, m.red);
+            dmax = block_max(dmax, m.red);
+            d1 = block_sum(d1, m.red);
+            d2 = block_sum(d2, m.red);
+            const T delta = (T)a.loading * tr / (T)D;
+            for (int b = threadIdx.x; b < N; b += FB_THREADS) el(m.A, gw.ntl, b, b) += delta;
+            __syncthreads();
+            const bool ok = cholesky_bordered(m.A, gw, T(16) * Num<T>::eps * (dmax + delta), m.flag, m.v, m.p, m.pan);
+            // kappa(C + delta I) bound: its smallest eigenvalue is delta exactly (C has rank below
+            // D), its largest (that of G + delta I) at most |G|_F + delta
+            if (ok && gate && !((Num<T>::sqrt_(fro) + delta) / delta <= (T)a.cond_gate)) redo |= want & 3u;
+            if (!ok && gate) redo |= want & 3u;
+            if (ok) {
+                T q1 = T(0), q2 = T(0);
+                for (int b = threadIdx.x; b < N; b += FB_THREADS) { q1 += m.v[b] * m.v[b]; q2 += m.p[b] * m.p[b]; }
+                q1 = block_sum(q1, m.red);
+                q2 = block_sum(q2, m.red);
+                if (threadIdx.x == 0) {
+                    if ((want & 1u) && a.out[0]) a.out[0][pix] = (float)((d1 - q1) / delta);
+                    if ((want & 2u) && a.out[1]) a.out[1][pix] = (float)fabs((d2 - q2) / delta);
+                }
+            } else {
+                flag |= 2;
+                if (threadIdx.x == 0) {
+                    if ((want & 1u) && a.out[0]) a.out[0][pix] = fnan;
+                    if ((want & 2u) && a.out[1]) a.out[1][pix] = fnan;
+                }
             }
         } else {
-            flag |= 2;
-            if (threadIdx.x == 0) {
-                if ((want & 1u) && a.out[0]) a.out[0][pix] = fnan;
-                if ((want & 2u) && a.out[1]) a.out[1][pix] = fnan;
+            mat_zero(m.A, g);
+            if constexpr (sizeof(T) == 4) {
+                if (g.tc) gram_tc(a.x, a.H, a.W, g, py, px, 0, N, ro, ri, m.mu_o, 1.f / (float)N, m.A, *st);
+            }
+            if (!g.tc) {
+                gram_accumulate<T>(a.x, a.H, a.W, g, py, px, 0, N, ro, ri, m.mu_o, T(1), m.A, m.xs);
+                mat_scale(m.A, g, T(1) / (T)N);
+            }
+            T tr = T(0), dmax = T(0);
+            for (int b = threadIdx.x; b < D; b += FB_THREADS) {
+                tr += el(m.A, g.ntl, b, b);
+                dmax = max(dmax, el(m.A, g.ntl, b, b));
+            }
+            tr = block_sum(tr, m.red);
+            dmax = block_max(dmax, m.red);
+            const T delta = (T)a.loading * tr / (T)D;
+            for (int b = threadIdx.x; b < D; b += FB_THREADS) el(m.A, g.ntl, b, b) += delta;
+            __syncthreads();
+            bool ok = cholesky_bordered(m.A, g, T(16) * Num<T>::eps * (dmax + delta), m.flag, m.r1, m.r2, m.pan);
+            if (ok && gate) {
+                // kappa estimate from the factor's diagonal: (max L_ii / min L_ii)^2
+                T lmax = T(0), lmin = T(3e38);
+                for (int b = threadIdx.x; b < D; b += FB_THREADS) {
+                    const T l = el(m.A, g.ntl, b, b);
+                    lmax = max(lmax, l);
+                    lmin = min(lmin, l);
+                }
+                lmax = block_max(lmax, m.red);
+                lmin = -block_max(-lmin, m.red);
+                const T kap = (lmax / lmin) * (lmax / lmin);
+                if (!(kap <= (T)a.cond_gate)) redo |= want & 3u;
+            }
+            if (!ok && gate) redo |= want & 3u;
+            if (ok) {
+                T q1 = T(0), q2 = T(0);
+                for (int b = threadIdx.x; b < D; b += FB_THREADS) { q1 += m.r1[b] * m.r1[b]; q2 += m.r2[b] * m.r2[b]; }
+                q1 = block_sum(q1, m.red);
+                q2 = block_sum(q2, m.red);
+                if (threadIdx.x == 0) {
+                    if ((want & 1u) && a.out[0]) a.out[0][pix] = (float)q1;
+                    if ((want & 2u) && a.out[1]) a.out[1][pix] = (float)fabs(q2);
+                }
+            } else {
+                flag |= 2;
+                if (threadIdx.x == 0) {
+                    if ((want & 1u) && a.out[0]) a.out[0][pix] = fnan;
+                    if ((want & 2u) && a.out[1]) a.out[1][pix] = fnan;
+                }
             }
         }
     }
@@ -1184,6 +1321,9 @@ Geo make_geo_only(const FullArgs& a) {
     g.ntl = ntiles_of(g.nt);
     g.S = fb_chunk(sizeof(T));
     g.mcap = std::min(g.Dp, a.inner * a.inner + 16);
+    g.N = a.outer * a.outer - a.inner * a.inner;
+    g.Np = (g.N + 3) & ~3;
+    g.wood = g.N < g.D && a.loading > 0.0 && (int64_t)a.H * a.W < (int64_t)INT32_MAX;
     g.tc = false;
     g.a_in_smem = false;
     g.pan_in_tc = false;

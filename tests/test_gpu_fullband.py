@@ -127,3 +127,25 @@ def test_reduce_to_more_than_eight_coefficients_is_unsupported(wd, scene48):
     with pytest.raises(wd.WdadError) as ei:
         wd.wdad_detect_all(x, reduce=True, level=1, inner=3, outer=7)
     assert ei.value.status == wd.WDAD_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("D,win", [(37, (1, 3)), (61, (3, 7)), (130, (5, 11)), (224, (5, 15))])
+@pytest.mark.parametrize("prec", [2, 0])
+def test_fullband_fewer_samples_than_bands(wd, D, win, prec):
+    # N = outer^2 - inner^2 < D: LRX and DWRX are solved at dimension N through the sample
+    # Gram (Woodbury identity); the scores must match the oracle's D x D solve
+    rng = np.random.default_rng(D + win[1])
+    mix = np.eye(D) + 0.1 * rng.standard_normal((D, D))
+    cube = (0.2 * rng.standard_normal((19, 23, D)) @ mix + 1.0).astype(np.float32)
+    cube[9, 11] += 0.5 * rng.standard_normal(D).astype(np.float32)  # one outlier pixel
+    got = wd.wdad_detect_all(_gpu(cube), reduce=False, inner=win[0], outer=win[1], precision=prec).cpu().numpy()
+    c64 = cube.astype(np.float64)
+    pix = _sample(19, 23, np.zeros((19, 23), bool), n=60, seed=D)
+    for det in (0, 1):
+        want = oracle.detect(c64, det, win[0], win[1], pixels=pix)
+        e = relerr(got[det].ravel()[pix], want)
+        tol = 1e-6 if prec == 2 else _fp32_rx_tol(c64, det, win, pix)
+        assert np.all(e <= tol), (det, e.max(), np.max(e / tol))
+    want, aux = oracle.detect(c64, 2, win[0], win[1], pixels=pix, want_aux=True)
+    e = dwest_relerr(got[2].ravel()[pix], want, aux)
+    assert e.max() <= (1e-6 if prec == 2 else TOL_SCORE), e.max()
