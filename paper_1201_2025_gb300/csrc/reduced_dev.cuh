@@ -305,8 +305,8 @@ __host__ __device__ constexpr int rr_second(int E, int r, int k) {
 // Each rotation zeroes a_pq and moves a_pp, a_qq by -/+ t a_pq; the blocks between
 // two pairs transform as R_i^T B R_j.  A is first scaled to unit Frobenius norm, so every
 // rotation's operands stay normal whatever the data's scale.  Entries at or below the FP32
-// rounding level (2^-22 of the norm) are left alone; sweeps end with the first sweep that
-// rotates nothing.  On return A's diagonal holds the eigenvalues divided by ||A||_F (their
+// rounding level (2^-22 of the norm) are left alone; sweeps end when no off-diagonal entry
+// is above that level.  On return A's diagonal holds the eigenvalues divided by ||A||_F (their
 // signs and ratios, which is all the DWEST selection uses), V's columns the eigenvectors.
 template <int D>
 __device__ __forceinline__ void jacobi_inplace(float (&A)[D][D], float (&V)[D][D]) {
@@ -331,7 +331,14 @@ __device__ __forceinline__ void jacobi_inplace(float (&A)[D][D], float (&V)[D][D
     const float tol = 2.384185791e-7f;  // 2^-22 of the (unit) norm
     constexpr int kSweeps = (D <= 4) ? 8 : 12;
     for (int sweep = 0; sweep < kSweeps; ++sweep) {
-        bool rotated = false;
+        // a sweep rotates nothing exactly when no off-diagonal entry is above tol at its start
+        // (nothing rotated leaves A unchanged), so that sweep is replaced by this check
+        bool live = false;
+#pragma unroll
+        for (int p = 0; p < D; ++p)
+#pragma unroll
+            for (int q = p + 1; q < D; ++q) live |= fabsf(A[p][q]) > tol;
+        if (!live) break;
 #pragma unroll
         for (int r = 0; r < E - 1; ++r) {
             float c[M], sn[M];
@@ -344,7 +351,6 @@ __device__ __forceinline__ void jacobi_inplace(float (&A)[D][D], float (&V)[D][D
                 if (q >= D) continue;
                 const float apq = A[p][q];
                 if (!(fabsf(apq) > tol)) continue;
-                rotated = true;
                 // t = sgn(theta) / (|theta| + sqrt(theta^2 + 1)) with theta = dq / h, dq = a_qq - a_pp,
                 // h = 2 a_pq, written as sgn(dq) h / (|dq| + sqrt(dq^2 + h^2)): one rsqrtf and one
                 // approximate division.  c^2 + s^2 = 1 holds to the rsqrtf error, and an inexact
@@ -407,7 +413,6 @@ __device__ __forceinline__ void jacobi_inplace(float (&A)[D][D], float (&V)[D][D
                 }
             }
         }
-        if (!rotated) break;
     }
 }
 

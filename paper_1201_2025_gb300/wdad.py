@@ -472,8 +472,9 @@ def wdad_window_census(H: int, W: int, params: wdad_params | None = None, device
     return out
 
 
-def wdad_adaptive_threshold(score, z_alpha: float, mask=None, want_mask: bool = True):
-    """Eq. 12 cut-off of a CUDA score map: (mu_d, sigma_d, tau, count, mask uint8 or None)."""
+def wdad_adaptive_threshold(score, z_alpha: float, mask=None, want_mask: bool = True, want_stats: bool = True):
+    """Eq. 12 cut-off of a CUDA score map: (mu_d, sigma_d, tau, count, mask uint8 or None).
+    want_stats=False leaves the call asynchronous (no host statistics; the four are NaN, -1)."""
     import torch
     score = score.contiguous()
     n = score.numel()
@@ -482,8 +483,10 @@ def wdad_adaptive_threshold(score, z_alpha: float, mask=None, want_mask: bool = 
     stats = np.zeros(4, dtype=np.float64)
     h = handle(score.device.index or 0)
     _check(lib().wdad_adaptive_threshold(h, score.data_ptr() if n else None, n, float(z_alpha),
-                                         mask.data_ptr() if (mask is not None and n) else None, stats.ctypes.data,
-                                         _stream(score)), h)
+                                         mask.data_ptr() if (mask is not None and n) else None,
+                                         stats.ctypes.data if want_stats else None, _stream(score)), h)
+    if not want_stats:
+        return float("nan"), float("nan"), float("nan"), -1, mask
     return float(stats[0]), float(stats[1]), float(stats[2]), int(stats[3]), mask
 
 

@@ -55,3 +55,13 @@ def test_threshold_edge_cases(wd):
     assert mu == 3.0 and sd == 0.0 and tau == 3.0 and int(mask.sum()) == 0
     with pytest.raises(RuntimeError):
         wd.wdad_adaptive_threshold(torch.ones(10, device="cuda"), float("nan"))
+
+
+def test_threshold_without_host_stats_gives_the_same_mask(wd):
+    rng = np.random.default_rng(11)
+    s = torch.from_numpy(rng.chisquare(4, 300001).astype(np.float32)).cuda()
+    *_, m_sync = wd.wdad_adaptive_threshold(s, 2.33)
+    mu, sd, tau, n, m_async = wd.wdad_adaptive_threshold(s, 2.33, want_stats=False)
+    torch.cuda.synchronize()
+    assert n == -1 and np.isnan(tau)
+    assert torch.equal(m_sync, m_async)
