@@ -463,38 +463,43 @@ def run_ours(args):
                                   "lrx_Mpixel_s": rows * W / (ms_lrx * 1e-3) / 1e6,
                                   "reduced_speedup_all3": (ms_all / (rows * W)) / ((dwt_alone_ms + det_ms[WINDOWS.index((wi, wo))]) / (H * W))}
         full["sample"] = f"{rows} x {W} x {L} strip of the cube, FP32, all pixels of the strip"
-    # mixed precision (BF16 tensor-core Gram, FP32 solve, FP64 re-solve above cond_gate) against
-    # the FP32 and FP64 full-band forms on an ill-conditioned AR(1) scene
+    # mixed precision against the FP32 and FP64 full-band forms on an ill-conditioned AR(1) scene.
+    # Window 3/11 (N = 112 < L): LRX/DWRX take the FP32 sample-Gram (Woodbury) form in every
+    # precision, DWEST the BF16 tensor-core Gram in MIXED; window 7/21 (N = 392 >= L): all three
+    # detectors use the BF16 tensor-core Gram in MIXED.
     mixed = {}
     if not args.no_full:
         ar = synth.make_scene(64, 64, L, seed=7, n_anom=10, anom_side=(1, 3), abundance=(0.1, 0.5), margin=6,
                               ar_rho=0.98)
         xa = torch.from_numpy(ar.cube).to(dev)
-        res = {}
-        for name, prec, gate in (("fp64", 2, 1e6), ("fp32", 0, 1e6), ("mixed_gate1e6", 1, 1e6),
-                                 ("mixed_gate1e3", 1, 1e3)):
-            maps, ms_det, frac_det = [], [], []
-            for d in range(3):
-                fl = torch.zeros((64, 64), dtype=torch.uint8, device=dev)
-                pp = wdad.wdad_default_params(inner=3, outer=11, precision=prec, cond_gate=gate)
-                ms_det.append(_time(lambda: wdad.wdad_detect(xa, d, reduce=False, params=pp, flags=fl), n=1))
-                fl.zero_()
-                maps.append(wdad.wdad_detect(xa, d, reduce=False, params=pp, flags=fl).cpu().numpy())
-                frac_det.append(float((fl.cpu().numpy() & 1).mean()))
-            res[name] = (maps, ms_det, frac_det)
-        ref = res["fp64"][0]
-        for name, (maps, ms_det, frac_det) in res.items():
-            ent = {}
-            for d, dn in enumerate(("lrx", "dwrx", "dwest")):
-                ent[f"{dn}_Mpixel_s"] = 64 * 64 / (ms_det[d] * 1e-3) / 1e6
-                ent[f"{dn}_fp64_resolved_fraction"] = frac_det[d]
-                ent[f"{dn}_auc"] = wdad.wdad_auc(maps[d], ar.mask)
-                ent[f"{dn}_dauc_vs_fp64"] = ent[f"{dn}_auc"] - wdad.wdad_auc(ref[d], ar.mask)
-                rel = np.abs(maps[d] - ref[d]) / np.maximum(np.abs(ref[d]), 1e-6 * np.median(np.abs(ref[d])))
-                ent[f"{dn}_median_rel_err_vs_fp64"] = float(np.median(rel))
-                ent[f"{dn}_max_rel_err_vs_fp64"] = float(np.max(rel))
-            mixed[name] = ent
-        mixed["workload"] = "64x64x224 AR(1) rho=0.98 scene, 10 targets, windows 3/11, loading 1e-3"
+        for wi, wo in ((3, 11), (7, 21)):
+            res = {}
+            for name, prec, gate in (("fp64", 2, 1e6), ("fp32", 0, 1e6), ("mixed_gate1e6", 1, 1e6),
+                                     ("mixed_gate1e3", 1, 1e3)):
+                maps, ms_det, frac_det = [], [], []
+                for d in range(3):
+                    fl = torch.zeros((64, 64), dtype=torch.uint8, device=dev)
+                    pp = wdad.wdad_default_params(inner=wi, outer=wo, precision=prec, cond_gate=gate)
+                    ms_det.append(_time(lambda: wdad.wdad_detect(xa, d, reduce=False, params=pp, flags=fl), n=1))
+                    fl.zero_()
+                    maps.append(wdad.wdad_detect(xa, d, reduce=False, params=pp, flags=fl).cpu().numpy())
+                    frac_det.append(float((fl.cpu().numpy() & 1).mean()))
+                res[name] = (maps, ms_det, frac_det)
+            ref = res["fp64"][0]
+            mw = {}
+            for name, (maps, ms_det, frac_det) in res.items():
+                ent = {}
+                for d, dn in enumerate(("lrx", "dwrx", "dwest")):
+                    ent[f"{dn}_Mpixel_s"] = 64 * 64 / (ms_det[d] * 1e-3) / 1e6
+                    ent[f"{dn}_fp64_resolved_fraction"] = frac_det[d]
+                    ent[f"{dn}_auc"] = wdad.wdad_auc(maps[d], ar.mask)
+                    ent[f"{dn}_dauc_vs_fp64"] = ent[f"{dn}_auc"] - wdad.wdad_auc(ref[d], ar.mask)
+                    rel = np.abs(maps[d] - ref[d]) / np.maximum(np.abs(ref[d]), 1e-6 * np.median(np.abs(ref[d])))
+                    ent[f"{dn}_median_rel_err_vs_fp64"] = float(np.median(rel))
+                    ent[f"{dn}_max_rel_err_vs_fp64"] = float(np.max(rel))
+                mw[name] = ent
+            mixed[f"{wi}/{wo}"] = mw
+        mixed["workload"] = "64x64x224 AR(1) rho=0.98 scene, 10 targets, windows 3/11 and 7/21, loading 1e-3"
     batching = None
     if not args.no_batch:
         batching = bench_batching(dev, stream, peak)
@@ -562,7 +567,7 @@ def run_ours(args):
 def run_profile_case(case: str):
     """Small workloads for ncu captures of kernels outside the timed step (a few GB at most):
     batch (8 cubes, side <= 512), screen (1024x1024x224 screening pass), mixed (64x64x224 AR(1)
-    full-band LRX, MIXED then FP32).  Each runs its workload twice and exits."""
+    full-band LRX, MIXED at window 7/21 then FP32 at 3/11).  Each runs its workload twice and exits."""
     import torch
     from paper_1201_2025_gb300 import synth, wdad
     dev = torch.device("cuda", 0)
@@ -593,8 +598,8 @@ def run_profile_case(case: str):
         sc = synth.make_scene(64, 64, L, seed=7, n_anom=10, anom_side=(1, 3), abundance=(0.1, 0.5), margin=6,
                               ar_rho=0.98)
         x = torch.from_numpy(sc.cube).to(dev)
-        for _ in range(2):
-            wdad.wdad_detect(x, 0, reduce=False, inner=3, outer=11, precision=1, cond_gate=1e6)
+        for _ in range(2):  # MIXED at 7/21 (BF16 tensor-core Gram), FP32 at 3/11 (sample-Gram form)
+            wdad.wdad_detect(x, 0, reduce=False, inner=7, outer=21, precision=1, cond_gate=1e6)
             wdad.wdad_detect(x, 0, reduce=False, inner=3, outer=11, precision=0)
     torch.cuda.synchronize()
     print("profile case", case, "ok")

@@ -1,8 +1,8 @@
 // Adaptive cut-off of Eq. 12 on a score map: tau = mu_d + z sigma_d, with mu_d and sigma_d
 // the mean and the population standard deviation of the map's finite entries; a pixel is
 // declared anomalous when its score exceeds tau.  Three launches: FP64 partial sums (count,
-// sum, sum of squares) over THR_BLOCKS fixed pixel ranges, a one-thread combination in block
-// order (so the statistics are the same on any GPU), and the comparison that writes the
+// sum, sum of squares) over THR_BLOCKS fixed pixel ranges, their combination by a tree of
+// fixed shape (so the statistics are the same on any GPU), and the comparison that writes the
 // binary map.  The one-pass variance sum/n - mean^2 is taken in FP64; detector scores have
 // mean^2 / variance of order 1-10, so the cancellation costs a few units of 1e-16.
 #include "internal.h"
@@ -42,15 +42,23 @@ __global__ void __launch_bounds__(THR_THREADS) thr_partials_kernel(const float* 
     }
 }
 
-// stats = [mu, sigma, tau, count]
-__global__ void thr_finalize_kernel(const double* __restrict__ part, double z, double* __restrict__ stats) {
-    if (threadIdx.x != 0) return;
-    double c = 0.0, sum = 0.0, sq = 0.0;
-    for (int b = 0; b < THR_BLOCKS; ++b) {
-        c += part[3 * b];
-        sum += part[3 * b + 1];
-        sq += part[3 * b + 2];
+// stats = [mu, sigma, tau, count]; one block of THR_BLOCKS threads, pairwise halving
+__global__ void __launch_bounds__(THR_BLOCKS) thr_finalize_kernel(const double* __restrict__ part, double z,
+                                                                  double* __restrict__ stats) {
+    __shared__ double r[3][THR_BLOCKS];
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) r[k][t] = part[3 * t + k];
+    __syncthreads();
+    for (int h = THR_BLOCKS / 2; h >= 1; h >>= 1) {
+        if (t < h) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) r[k][t] += r[k][t + h];
+        }
+        __syncthreads();
     }
+    if (t != 0) return;
+    const double c = r[0][0], sum = r[1][0], sq = r[2][0];
     const double nan = __longlong_as_double(0x7ff8000000000000ll);
     const double mu = c > 0.0 ? sum / c : nan;
     const double var = c > 0.0 ? fmax(sq / c - mu * mu, 0.0) : nan;
@@ -77,7 +85,7 @@ cudaError_t launch_adaptive_threshold(const float* s, int64_t n, double z, void*
     double* part = reinterpret_cast<double*>(ws);
     double* stats = part + 3 * (size_t)THR_BLOCKS;
     thr_partials_kernel<<<THR_BLOCKS, THR_THREADS, 0, st>>>(s, n, part);
-    thr_finalize_kernel<<<1, 32, 0, st>>>(part, z, stats);
+    thr_finalize_kernel<<<1, THR_BLOCKS, 0, st>>>(part, z, stats);
     if (mask && n > 0) {
         int64_t g = (n + 255) / 256;
         const int64_t cap = (int64_t)num_sms * 8;
