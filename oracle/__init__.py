@@ -259,3 +259,24 @@ def auc(score: np.ndarray, mask: np.ndarray) -> float:
     s = np.ascontiguousarray(score, dtype=np.float64).ravel()
     m = np.ascontiguousarray(mask, dtype=np.uint8).ravel()
     return float(lib().or_auc(_ptr(s, ctypes.c_double), _ptr(m, ctypes.c_uint8), len(s)))
+
+
+def global_rx(cube: np.ndarray, loading: float = 1e-3, want_cond: bool = False):
+    """Global RX, Eq. 1 (Sec. 2.1): s(r) = (r - mu)^T (C + delta I)^-1 (r - mu), with mu and
+    C = (1/P) sum (x - mu)(x - mu)^T taken over all P pixels of the image (one background for
+    the whole scene) and delta = loading * trace(C) / L, the loading rule of the local
+    detectors.  cube [H][W][L] -> scores [H][W] float64; with want_cond also cond(C + delta I)."""
+    c = np.asarray(cube, dtype=np.float64)
+    L = c.shape[-1]
+    X = c.reshape(-1, L)
+    mu = X.mean(axis=0)
+    Xc = X - mu
+    C = Xc.T @ Xc / X.shape[0]
+    delta = loading * np.trace(C) / L
+    M = C + delta * np.eye(L)
+    Z = np.linalg.solve(M, Xc.T)          # M^-1 (x - mu) for every pixel
+    s = np.einsum("pl,lp->p", Xc, Z).reshape(c.shape[:-1])
+    if want_cond:
+        ev = np.linalg.eigvalsh(M)
+        return s, float(ev[-1] / ev[0])
+    return s

@@ -71,14 +71,14 @@ def test_odd_length_pads_last_sample():
 
 
 @pytest.mark.parametrize("L", [64, 128, 256, 224, 188, 189, 7, 5])
-@pytest.mark.parametrize("taps", [4, 8])
+@pytest.mark.parametrize("taps", [2, 4, 6, 8, 12, 20])
 def test_perfect_reconstruction(L, taps):
     x = np.random.default_rng(L + taps).standard_normal(L)
     c = oracle.dwt_full(x, taps)
     np.testing.assert_allclose(oracle.dwt_inverse(c, L, taps), x, atol=1e-12)
 
 
-@pytest.mark.parametrize("taps", [4, 8])
+@pytest.mark.parametrize("taps", [2, 4, 8, 12, 20])
 def test_full_dwt_is_orthogonal_for_power_of_two(taps):
     L = 128
     Wm = np.stack([oracle.dwt_full(e, taps) for e in np.eye(L)], axis=1)
@@ -459,3 +459,51 @@ def test_adaptive_threshold_invariances_and_gaussian_rate():
     # Gaussian scores: the declared fraction is the upper tail 1 - Phi(z) (0.02275 at z = 2)
     from scipy.stats import norm
     assert abs(m.mean() - norm.sf(2.0)) < 4 * np.sqrt(norm.sf(2.0) / len(s))
+
+
+# ---------------------------------------------------------------- global RX (Eq. 1)
+def test_global_rx_trace_identity():
+    # sum over the image of (x - mu)^T M^-1 (x - mu) = P tr(M^-1 C): P L without loading, and
+    # P sum lambda / (lambda + delta) over the eigenvalues of C with it
+    rng = np.random.default_rng(1)
+    cube = rng.standard_normal((20, 25, 6)) @ (np.eye(6) + 0.4 * rng.standard_normal((6, 6))) + 3.0
+    P = 500
+    assert abs(oracle.global_rx(cube, loading=0.0).sum() - P * 6) < 1e-9 * P * 6
+    X = cube.reshape(-1, 6)
+    C = np.cov(X.T, bias=True)
+    lam = np.linalg.eigvalsh(C)
+    delta = 0.05 * lam.sum() / 6
+    want = P * np.sum(lam / (lam + delta))
+    assert abs(oracle.global_rx(cube, loading=0.05).sum() - want) < 1e-9 * want
+
+
+def test_global_rx_affine_invariance():
+    # without loading the score is invariant under any invertible affine band transform
+    rng = np.random.default_rng(2)
+    cube = rng.standard_normal((9, 11, 5))
+    A = rng.standard_normal((5, 5)) + 3 * np.eye(5)
+    b = rng.standard_normal(5)
+    np.testing.assert_allclose(oracle.global_rx(cube @ A.T + b, loading=0.0), oracle.global_rx(cube, loading=0.0),
+                               rtol=1e-9)
+
+
+def test_global_rx_chi_square_on_gaussian_background():
+    # Gaussian pixels: the score follows chi-square with L degrees of freedom (Sec. 2.1), up to
+    # the O(1/P) effect of the estimated mean and covariance
+    from scipy import stats
+    rng = np.random.default_rng(3)
+    L, P = 5, 40000
+    Sig = np.eye(L) + 0.5 * np.ones((L, L))
+    X = rng.multivariate_normal(np.arange(L), Sig, size=P)
+    s = oracle.global_rx(X.reshape(200, 200, L), loading=0.0).ravel()
+    for q in (0.5, 0.9, 0.99):
+        assert abs(np.quantile(s, q) / stats.chi2.ppf(q, L) - 1) < 0.03, q
+    assert stats.kstest(s, "chi2", args=(L,)).statistic < 0.01
+
+
+def test_global_rx_single_outlier_ranks_first():
+    rng = np.random.default_rng(4)
+    cube = 0.1 * rng.standard_normal((16, 16, 8)) + 1.0
+    cube[5, 7] += 0.5 * rng.standard_normal(8)
+    s = oracle.global_rx(cube)
+    assert np.unravel_index(np.argmax(s), s.shape) == (5, 7)
