@@ -56,7 +56,8 @@ typedef enum {
 
 /* Detection parameters.  Fill with wdad_default_params() and override. */
 typedef struct {
-    int wavelet_taps;  /* 8 = db4, "Daubechies4" of Sec. 4 (default); 4 = D4 */
+    int wavelet_taps;  /* Daubechies filter length, even 2..20: 8 = db4, "Daubechies4" of Sec. 4
+                          (default); 4 = D4; taps/2 vanishing moments (Sec. 6 other filters) */
     int level;         /* -1 = smallest J whose approximation length is <= 4 (Sec. 4) */
     int inner, outer;  /* odd window sides, 1 <= inner < outer <= 63 (Sec. 2.2, Sec. 5.2) */
     float loading;     /* LRX/DWRX diagonal loading delta = loading * trace(C_o) / dim; default 1e-3 */
@@ -84,6 +85,24 @@ wdad_status wdad_last_error_detail(wdad_handle h, char* buf, int len);
 /* Number of approximation coefficients K for L bands and a level (-1 = auto, Sec. 4):
  * K = L halved (rounding up) J times.  Returns -1 for invalid input. */
 int wdad_query_K(int L, int taps, int level);
+
+/* Global RX, Eq. 1 (Sec. 2.1): score[p] = (r_p - mu)^T (C + delta I)^-1 (r_p - mu) with mu and
+ * C = (1/P) sum (r - mu)(r - mu)^T over all P = H*W pixels (one background for the whole
+ * image) and delta = p->loading * trace(C) / bands, the loading rule of the local detectors.
+ * reduce = 0: on the L bands of cube; reduce = 1: on the K DWT approximation coefficients
+ * (p->wavelet_taps, p->level), computed into the handle's workspace.  cube: device
+ * [H][W][L] float32; score: device [H][W] float32.  Bands (L or K) up to 1024, otherwise
+ * WDAD_ERR_UNSUPPORTED.  Mean and covariance: FP32 partial sums over fixed pixel ranges
+ * combined in FP64 in a fixed order; inverse: FP32 symmetric sweep in one block.  If the
+ * loaded covariance is not numerically positive definite every score is NaN.  Asynchronous
+ * on `stream`; uses the handle's workspace. */
+wdad_status wdad_global_rx(wdad_handle h, const float* cube, int H, int W, int L, int reduce, const wdad_params* p,
+                           float* score, void* stream);
+
+/* Host-only: the scaling filter h[0..taps-1] the DWT uses (Sec. 4; Daubechies' extremal-phase
+ * construction, taps/2 vanishing moments, sum h = sqrt(2)).  taps even, 2..20; h (host, taps
+ * doubles) is written on success.  WDAD_ERR_ARG for other taps or a NULL h.  No GPU needed. */
+wdad_status wdad_wavelet_filter(int taps, double* h);
 
 /* A1 — approximation matrix (Sec. 4; Eq. 9 cascaded J times, Fig. 1, details discarded).
  * cube: [H][W][L] float32; approx: [H][W][K] float32 (caller allocates H*W*K floats);

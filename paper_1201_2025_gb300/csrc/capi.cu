@@ -85,8 +85,9 @@ wdad_status cuda_fail(wdad_ctx* h, cudaError_t e, const char* where) {
 
 wdad_status check_params(wdad_ctx* h, const wdad_params* p) {
     if (!p) return fail(h, WDAD_ERR_ARG, "params is NULL");
-    if (p->wavelet_taps != 8 && p->wavelet_taps != 4)
-        return fail(h, WDAD_ERR_ARG, "wavelet_taps must be 8 (db4) or 4 (D4), got %d", p->wavelet_taps);
+    if (p->wavelet_taps < 2 || p->wavelet_taps > wdad::kMaxTaps || (p->wavelet_taps & 1))
+        return fail(h, WDAD_ERR_ARG, "wavelet_taps must be even, 2..%d (8 = db4), got %d", wdad::kMaxTaps,
+                    p->wavelet_taps);
     if (p->level < -1 || p->level > 30) return fail(h, WDAD_ERR_ARG, "level must be -1..30, got %d", p->level);
     if (p->inner < 1 || !(p->inner & 1) || p->outer <= p->inner || !(p->outer & 1) || p->outer > 63)
         return fail(h, WDAD_ERR_ARG, "windows must be odd with 1 <= inner < outer <= 63, got %d/%d", p->inner,
@@ -373,10 +374,56 @@ wdad_status wdad_last_error_detail(wdad_handle h, char* buf, int len) {
 }
 
 int wdad_query_K(int L, int taps, int level) {
-    if (L < 1 || (taps != 8 && taps != 4) || level < -1 || level > 30) return -1;
+    if (L < 1 || taps < 2 || taps > wdad::kMaxTaps || (taps & 1) || level < -1 || level > 30) return -1;
     int K = 0;
     wdad::dwt_levels(L, level, &K);
     return K;
+}
+
+wdad_status wdad_global_rx(wdad_handle h, const float* cube, int H, int W, int L, int reduce, const wdad_params* p,
+                           float* score, void* stream) {
+    if (!h) return WDAD_ERR_ARG;
+    try {
+        DeviceGuard g(h->device);
+        wdad_status st = check_params(h, p);
+        if (st != WDAD_OK) return st;
+        st = check_cube(h, cube, H, W, L);
+        if (st != WDAD_OK) return st;
+        if (reduce != 0 && reduce != 1) return fail(h, WDAD_ERR_ARG, "reduce must be 0 or 1");
+        const int64_t P = (int64_t)H * W;
+        if (P == 0) return WDAD_OK;
+        if (!score) return fail(h, WDAD_ERR_ARG, "score is NULL");
+        cudaStream_t s = (cudaStream_t)stream;
+        const int D = reduce ? wdad_query_K(L, p->wavelet_taps, p->level) : L;
+        if (D < 1 || D > wdad::kGlobalRxMaxBands)
+            return fail(h, WDAD_ERR_UNSUPPORTED, "global RX supports 1..%d bands, got %d", wdad::kGlobalRxMaxBands, D);
+        const size_t need = wdad::global_rx_workspace_bytes(P, D, h->num_sms);
+        if (need == 0) return fail(h, WDAD_ERR_UNSUPPORTED, "global RX workspace for %d bands", D);
+        const size_t off = reduce ? align256(sizeof(float) * (size_t)P * D) : 0;
+        st = ensure_ws(h, off + need);
+        if (st != WDAD_OK) return st;
+        const float* x = cube;
+        if (reduce) {
+            const float* A = nullptr;
+            int k2 = 0;
+            st = get_dwt_plan(h, L, p->wavelet_taps, p->level, &A, &k2, s);
+            if (st != WDAD_OK) return st;
+            float* xr = (float*)h->ws;
+            cudaError_t e = wdad::launch_dwt_approx(cube, P, L, A, D, xr, h->num_sms, s);
+            if (e != cudaSuccess) return cuda_fail(h, e, "dwt_approx launch");
+            x = xr;
+        }
+        cudaError_t e = wdad::launch_global_rx(x, P, D, p->loading, score, (char*)h->ws + off, h->ws_bytes - off,
+                                               h->num_sms, s);
+        return e == cudaSuccess ? WDAD_OK : cuda_fail(h, e, "global RX launch");
+    } catch (...) {
+        return fail(h, WDAD_ERR_NOMEM, "host exception");
+    }
+}
+
+wdad_status wdad_wavelet_filter(int taps, double* h) {
+    if (!h) return WDAD_ERR_ARG;
+    return wdad::filter_coeffs(taps, h) ? WDAD_OK : WDAD_ERR_ARG;
 }
 
 wdad_status wdad_dwt_approx(wdad_handle h, const float* cube, int H, int W, int L, const wdad_params* p,

@@ -10,28 +10,79 @@
 // butterfly leaves lane l with coefficient (pixel l / KP, k = l % KP), so the
 // PX*K results leave as one coalesced store.  The lane partial sums plus the tree
 // of shuffles keep the FP32 rounding error near sqrt(L) ulp instead of L ulp.
+#include <complex>
+#include <vector>
+
 #include "dwt_dev.cuh"
 
 namespace wdad {
 
-bool filter_coeffs(int taps, double* h) {
-    if (taps == 8) {
-        // Daubechies' 4-vanishing-moment scaling filter (Ten Lectures on Wavelets, Table 6.1)
-        static const double db4[8] = {0.2303778133088964,  0.7148465705529154,  0.6308807679298587,
-                                      -0.0279837694168599, -0.1870348117190931, 0.0308413818355607,
-                                      0.0328830116668852,  -0.0105974017850690};
-        for (int i = 0; i < 8; ++i) h[i] = db4[i];
-        return true;
+// ---- Daubechies scaling filters with taps / 2 vanishing moments, taps = 2 .. kMaxTaps.
+// Daubechies' construction (Ten Lectures on Wavelets, Sec. 6.1): with p = taps / 2,
+// |m0(w)|^2 = cos^2p(w/2) P(sin^2(w/2)), P(y) = sum_{k<p} C(p-1+k, k) y^k.  Each root y_j of
+// P gives the pair z, 1/z of z + 1/z = 2 - 4 y_j; keeping the root outside the unit circle
+// for every pair gives the extremal-phase filter, h(w) ~ (1 + w)^p prod_j (w - z_j), scaled
+// to sum(h) = sqrt(2) (db4 = taps 8, D4 = taps 4).  Roots of P: Laguerre's method with
+// deflation, each root then refined on the undeflated polynomial.
+using cplx = std::complex<double>;
+
+static cplx laguerre_root(const std::vector<cplx>& a, cplx z) {
+    const int n = (int)a.size() - 1;  // degree, a ascending
+    for (int it = 0; it < 100; ++it) {
+        cplx p = a[n], dp = 0.0, d2p = 0.0;
+        for (int k = n - 1; k >= 0; --k) {
+            d2p = d2p * z + dp;
+            dp = dp * z + p;
+            p = p * z + a[k];
+        }
+        d2p *= 2.0;
+        if (std::abs(p) == 0.0) break;
+        const cplx G = dp / p, Hs = G * G - d2p / p;
+        const cplx sq = std::sqrt((double)(n - 1) * ((double)n * Hs - G * G));
+        const cplx den = std::abs(G + sq) >= std::abs(G - sq) ? G + sq : G - sq;
+        const cplx step = std::abs(den) > 0.0 ? (double)n / den : cplx(1e-3 * (1.0 + std::abs(z)), 0.0);
+        z -= step;
+        if (std::abs(step) <= 4e-16 * std::abs(z)) break;
     }
-    if (taps == 4) {
-        const double s3 = sqrt(3.0), r = 4.0 * sqrt(2.0);
-        h[0] = (1.0 + s3) / r; h[1] = (3.0 + s3) / r; h[2] = (3.0 - s3) / r; h[3] = (1.0 - s3) / r;
-        return true;
-    }
-    return false;
+    return z;
 }
 
-struct Filter { double h[8]; int taps; };
+bool filter_coeffs(int taps, double* h) {
+    if (taps < 2 || taps > kMaxTaps || (taps & 1)) return false;
+    const int p = taps / 2, n = p - 1;
+    std::vector<cplx> P(n + 1), a;
+    double c = 1.0;
+    for (int k = 0; k <= n; ++k) {  // C(p-1+k, k)
+        P[k] = c;
+        c = c * (double)(p + k) / (double)(k + 1);
+    }
+    std::vector<cplx> w(1, cplx(1.0, 0.0));  // ascending coefficients of the filter polynomial
+    auto times = [&w](cplx root) {            // w <- w * (x - root)
+        w.push_back(0.0);
+        for (int i = (int)w.size() - 1; i >= 1; --i) w[i] = w[i - 1] - root * w[i];
+        w[0] = -root * w[0];
+    };
+    for (int k = 0; k < p; ++k) times(cplx(-1.0, 0.0));
+    a = P;
+    for (int d = n; d >= 1; --d) {
+        cplx y = laguerre_root(a, cplx(0.0, 0.0));
+        y = laguerre_root(P, y);
+        // deflate a by (x - y)
+        std::vector<cplx> b(d);
+        b[d - 1] = a[d];
+        for (int k = d - 1; k >= 1; --k) b[k - 1] = a[k] + y * b[k];
+        a.swap(b);
+        const cplx q = 2.0 - 4.0 * y, disc = std::sqrt(q * q - 4.0);
+        const cplx z1 = 0.5 * (q + disc), z2 = 0.5 * (q - disc);
+        times(std::abs(z1) >= std::abs(z2) ? z1 : z2);
+    }
+    double sum = 0.0;
+    for (int i = 0; i < taps; ++i) sum += w[i].real();
+    for (int i = 0; i < taps; ++i) h[i] = w[i].real() * std::sqrt(2.0) / sum;
+    return true;
+}
+
+struct Filter { double h[kMaxTaps]; int taps; };
 
 // One block per band l: cascade of Eq. 9 steps on the unit spectrum e_l.
 __global__ void dwt_matrix_kernel(int L, int J, int K, Filter f, float* __restrict__ A) {

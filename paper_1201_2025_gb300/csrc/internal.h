@@ -30,6 +30,7 @@ inline int dwt_levels(int L, int level, int* K) {
 }
 
 // Daubechies scaling filters (sum = sqrt 2): taps 8 = db4, taps 4 = D4.
+constexpr int kMaxTaps = 20;  // Daubechies filters db1 .. db10
 bool filter_coeffs(int taps, double* h);
 
 // ---- A1: DWT approximation ---------------------------------------------------
@@ -57,6 +58,13 @@ cudaError_t launch_detect_small(const DetectArgs& a, int tile_h, cudaStream_t s)
 // exact tile height (the plan); default plan of a configuration
 cudaError_t launch_detect_small_th(const DetectArgs& a, int th, cudaStream_t s);
 int detect_small_default_th(int D, int inner, int outer);
+// Global RX of Eq. 1 on a [P][L] cube (L <= kGlobalRxMaxBands), scores [P]; workspace from
+// global_rx_workspace_bytes (0 for unsupported sizes).
+constexpr int kGlobalRxMaxBands = 1024;
+size_t global_rx_workspace_bytes(int64_t P, int L, int num_sms);
+cudaError_t launch_global_rx(const float* x, int64_t P, int L, float loading, float* score, void* ws, size_t ws_bytes,
+                             int num_sms, cudaStream_t s);
+
 // Eq. 12 cut-off on a score map (ws: adaptive_threshold_workspace() bytes of device memory);
 // stats_out (host, nullable): mu, sigma, tau, count, copied asynchronously on st
 size_t adaptive_threshold_workspace();

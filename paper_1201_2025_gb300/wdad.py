@@ -91,13 +91,16 @@ def lib() -> ctypes.CDLL:
     L.wdad_auc.argtypes = [vp, vp, i64, ctypes.POINTER(ctypes.c_double)]
     L.wdad_scene_whitening.argtypes = [vp, f32p, i64, i32, f32p, vp]
     L.wdad_adaptive_threshold.argtypes = [vp, f32p, i64, ctypes.c_double, vp, vp, vp]
+    L.wdad_wavelet_filter.argtypes = [i32, vp]
+    L.wdad_global_rx.argtypes = [vp, f32p, i32, i32, i32, i32, pp, f32p, vp]
     for name in ("wdad_create", "wdad_destroy", "wdad_last_error_detail", "wdad_dwt_approx", "wdad_detect",
                  "wdad_detect_all", "wdad_detect_all_host", "wdad_window_census", "wdad_auc",
                  "wdad_detect_all_noalloc", "wdad_window_moments", "wdad_autotune", "wdad_batch_create",
                  "wdad_batch_launch", "wdad_batch_status", "wdad_batch_destroy", "wdad_batch_run",
                  "wdad_cnn_create", "wdad_cnn_destroy", "wdad_cnn_set_norm", "wdad_cnn_params",
                  "wdad_cnn_set_params", "wdad_cnn_forward", "wdad_cnn_grad", "wdad_cnn_train", "wdad_cnn_save",
-                 "wdad_cnn_load", "wdad_screen_run", "wdad_scene_whitening", "wdad_adaptive_threshold"):
+                 "wdad_cnn_load", "wdad_screen_run", "wdad_scene_whitening", "wdad_adaptive_threshold",
+                 "wdad_wavelet_filter", "wdad_global_rx"):
         getattr(L, name).restype = i32
     L.wdad_query_K.restype = i32
     _lib = L
@@ -162,6 +165,13 @@ def wdad_query_K(L: int, taps: int = 8, level: int = -1) -> int:
     return int(lib().wdad_query_K(L, taps, level))
 
 
+def wdad_wavelet_filter(taps: int = 8) -> np.ndarray:
+    """The DWT's scaling filter (host computation, no GPU): float64 [taps]."""
+    h = np.zeros(taps if taps > 0 else 1, dtype=np.float64)
+    _check(lib().wdad_wavelet_filter(int(taps), h.ctypes.data), None)
+    return h[:taps]
+
+
 def wdad_dwt_approx(cube, params: wdad_params | None = None, out=None, **over):
     """A1: approximation matrix [H, W, K] of a CUDA cube [H, W, L]."""
     import torch
@@ -192,6 +202,20 @@ def wdad_detect(cube, detector: int, reduce: bool = True, params: wdad_params | 
     h = handle(cube.device.index or 0)
     _check(lib().wdad_detect(h, cube.data_ptr(), H, W, L, int(detector), int(bool(reduce)), ctypes.byref(p),
                              out.data_ptr(), flags.data_ptr() if flags is not None else None, _stream(cube)), h)
+    return out
+
+
+def wdad_global_rx(cube, reduce: bool = True, params: wdad_params | None = None, out=None, **over):
+    """Global RX (Eq. 1, image-wide mean and covariance) on every pixel: [H, W] float32."""
+    import torch
+    cube = _cube(cube)
+    p = _params(params, over)
+    H, W, L = cube.shape
+    if out is None:
+        out = torch.empty((H, W), device=cube.device, dtype=torch.float32)
+    h = handle(cube.device.index or 0)
+    _check(lib().wdad_global_rx(h, cube.data_ptr(), H, W, L, int(bool(reduce)), ctypes.byref(p), out.data_ptr(),
+                                _stream(cube)), h)
     return out
 
 

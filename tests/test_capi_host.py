@@ -47,8 +47,30 @@ def test_query_K_matches_oracle_levels(wl, L, level):
 
 def test_query_K_rejects_bad_input(wl):
     assert wl.wdad_query_K(0, 8, -1) == -1
-    assert wl.wdad_query_K(224, 6, -1) == -1
+    assert wl.wdad_query_K(224, 7, -1) == -1   # odd filter length
+    assert wl.wdad_query_K(224, 22, -1) == -1  # beyond db10
+    assert wl.wdad_query_K(224, 0, -1) == -1
     assert wl.wdad_query_K(224, 8, -2) == -1
+    assert wl.wdad_query_K(224, 6, -1) == wl.wdad_query_K(224, 8, -1)  # K does not depend on the filter
+
+
+@pytest.mark.parametrize("taps", [2, 4, 6, 8, 10, 12, 14, 16, 18, 20])
+def test_wavelet_filter_matches_oracle(wl, taps):
+    # two independent constructions of Daubechies' filter (Laguerre here, Durand-Kerner in the
+    # oracle); the oracle's is pinned to the published db4 / D4 values and the filter identities
+    np.testing.assert_allclose(wl.wdad_wavelet_filter(taps), oracle.daub_filter(taps), rtol=0, atol=1e-12)
+
+
+def test_wavelet_filter_published_values(wl):
+    s3, r = np.sqrt(3.0), 4 * np.sqrt(2.0)
+    np.testing.assert_allclose(wl.wdad_wavelet_filter(4), [(1 + s3) / r, (3 + s3) / r, (3 - s3) / r, (1 - s3) / r],
+                               rtol=0, atol=1e-15)
+    db4 = [0.2303778133088964, 0.7148465705529154, 0.6308807679298587, -0.0279837694168599,
+           -0.1870348117190931, 0.0308413818355607, 0.0328830116668852, -0.0105974017850690]
+    np.testing.assert_allclose(wl.wdad_wavelet_filter(8), db4, rtol=0, atol=1e-15)
+    for bad in (0, 3, 22):
+        with pytest.raises(wl.WdadError):
+            wl.wdad_wavelet_filter(bad)
 
 
 def test_null_handle_is_an_argument_error(wl):

@@ -47,6 +47,23 @@ def test_dwt_parity(wd, synth, shape, taps):
     assert np.max(np.abs(got - want) / scale) <= TOL_DWT
 
 
+@pytest.mark.parametrize("shape", [(48, 48, 224), (5, 9, 189), (3, 5, 97), (2, 3, 4)])
+@pytest.mark.parametrize("taps", [2, 6, 10, 12, 16, 20])
+def test_dwt_parity_other_filters(wd, shape, taps):
+    # Daubechies filters beyond db4 / D4 (Sec. 6): the product builds its own filter and matrix
+    H, W, L = shape
+    rng = np.random.default_rng(H * 1000 + L + taps)
+    cube = (0.3 + 0.1 * rng.standard_normal(shape)).astype(np.float32)
+    for level in ((-1, 5) if L % 4 == 0 else (-1,)):  # K > 4 needs L % 4 == 0 beyond 128 bands
+        if wd.wdad_query_K(L, taps, level) > 8:
+            continue
+        got = wd.wdad_dwt_approx(_gpu(cube), wavelet_taps=taps, level=level).cpu().numpy()
+        want = oracle.dwt_approx(cube, taps=taps, level=level)
+        assert got.shape == want.shape
+        scale = np.maximum(np.abs(want), np.sqrt(np.mean(want ** 2)))
+        assert np.max(np.abs(got - want) / scale) <= TOL_DWT, (taps, level)
+
+
 @pytest.mark.parametrize("level", [0, 1, 2, 5])
 def test_dwt_explicit_level(wd, level):
     cube = (0.3 + 0.1 * np.random.default_rng(level).standard_normal((6, 10, 224))).astype(np.float32)
@@ -78,19 +95,26 @@ def test_window_census_bit_exact(wd, H, W, win, border):
 
 
 # ---------------------------------------------------------------- A3-A6 detectors on the reduced cube
-def _check_scene(wd, cube, win, loading=1e-3, dwest_mode=0, label=""):
+def _check_scene(wd, cube, win, loading=1e-3, dwest_mode=0, label="", taps=8):
     x = _gpu(cube)
     got = wd.wdad_detect_all(x, reduce=True, inner=win[0], outer=win[1], loading=loading,
-                             dwest_mode=dwest_mode).cpu().numpy()
-    a = oracle.dwt_approx(cube)
+                             dwest_mode=dwest_mode, wavelet_taps=taps).cpu().numpy()
+    a = oracle.dwt_approx(cube, taps=taps)
+    tol = TOL_SCORE
+    if taps != 8:
+        # filters other than db4 smooth the coefficients differently: the bar is the FP32 one of
+        # the arithmetic, max(1e-4, 32 u kappa) per pixel (the fixed 1e-4 is the db4 path's)
+        _, aux = oracle.detect(a, 0, win[0], win[1], loading=loading, want_aux=True, want_cond=True)
+        tol = np.maximum(TOL_SCORE, 32 * 2.0 ** -24 * aux[..., 1] / aux[..., 0])
     for det in (0, 1):
         want = oracle.detect(a, det, win[0], win[1], loading=loading)
         e = relerr(got[det], want)
-        assert e.max() <= TOL_SCORE, f"{label} det {det} win {win}: max rel err {e.max():.3g}"
+        assert np.all(e <= tol), f"{label} det {det} win {win}: max rel err {e.max():.3g}"
     want, aux = oracle.detect(a, 2, win[0], win[1], dwest_mode=dwest_mode, want_aux=True)
     ok = dwest_ok_mask(aux)
     e = dwest_relerr(got[2], want, aux)
-    assert ok.mean() > 0.9, f"{label}: only {ok.mean():.3f} of DWEST pixels are well determined"
+    # (other filters leave more pixels with an eigenvalue near the selection cut-off)
+    assert ok.mean() > (0.9 if taps == 8 else 0.5), f"{label}: only {ok.mean():.3f} of DWEST pixels are well determined"
     assert e[ok].max() <= TOL_SCORE, f"{label} DWEST win {win}: max rel err {e[ok].max():.3g} ({(~ok).sum()} excluded)"
     return got
 
@@ -98,6 +122,11 @@ def _check_scene(wd, cube, win, loading=1e-3, dwest_mode=0, label=""):
 @pytest.mark.parametrize("win", [(3, 11), (3, 9), (5, 15), (7, 21)])
 def test_reduced_detectors_scene48(wd, scene48, win):
     _check_scene(wd, scene48.cube, win, label="48x48")
+
+
+@pytest.mark.parametrize("taps", [2, 12, 20])
+def test_reduced_detectors_other_filters(wd, scene48, taps):
+    _check_scene(wd, scene48.cube, (3, 11), label=f"taps {taps}", taps=taps)
 
 
 def test_reduced_dwest_projection_norm(wd, scene48):
@@ -169,9 +198,10 @@ def test_empty_and_invalid_inputs(wd):
     with pytest.raises(wd.WdadError) as ei:
         wd.wdad_detect(x, 0, inner=9, outer=9)
     assert ei.value.status == wd.WDAD_ERR_ARG
-    with pytest.raises(wd.WdadError) as ei:
-        wd.wdad_detect(x, 0, wavelet_taps=6)
-    assert ei.value.status == wd.WDAD_ERR_ARG
+    for taps in (7, 22, 0):
+        with pytest.raises(wd.WdadError) as ei:
+            wd.wdad_detect(x, 0, wavelet_taps=taps)
+        assert ei.value.status == wd.WDAD_ERR_ARG
     with pytest.raises(wd.WdadError) as ei:
         wd.wdad_detect(x, 7)
     assert ei.value.status == wd.WDAD_ERR_ARG
