@@ -8,9 +8,11 @@
 //   (4) grx_gram_reduce: the range partials of every entry added in range order in FP64, / P;
 //   (5) grx_invert: one block turns C + delta I into its inverse with the symmetric sweep
 //       operator (Gauss-Jordan elimination that keeps the matrix symmetric, so only the lower
-//       triangle is stored and updated), FP32, in shared memory when it fits;
-//   (6) grx_score: per pixel y = B d, s = d^T y with d = x - mu; B is symmetric, so lane i
-//       reads row k of B at column i (coalesced), eight pixels per warp share every load.
+//       triangle is stored and updated), FP32: in registers (8 x 8 tiles, one per thread) up to
+//       248 bands, else in shared memory when it fits, else in global memory;
+//   (6) grx_score: per pixel s = d^T B d with d = x - mu, from the strict lower triangle and
+//       the diagonal of the symmetric B (about half the multiply-adds of y = B d); lane i reads
+//       row k of B at column i (coalesced), eight pixels per warp share every load.
 // A pivot at or below the floor (the matrix is not numerically positive definite) sets the
 // status word and every score becomes NaN.
 #include <float.h>
@@ -205,6 +207,135 @@ __global__ void __launch_bounds__(GRX_THREADS) grx_invert_kernel(float* __restri
     }
 }
 
+// column KC of a register tile to col[8 I ..], row KC to col[8 K ..]; the sweep's new values
+// of that column / row (compile-time register offsets, selected by a switch on k % 8)
+template <int KC>
+__device__ __forceinline__ void tile_col_out(const float (&a)[64], float* col, int I) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) col[8 * I + r] = a[r * 8 + KC];
+}
+template <int KC>
+__device__ __forceinline__ void tile_row_out(const float (&a)[64], float* col, int K) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) col[8 * K + c] = a[KC * 8 + c];
+}
+template <int KC>
+__device__ __forceinline__ void tile_col_set(float (&a)[64], const float (&ci)[8], int I, int k, float inv) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) a[r * 8 + KC] = 8 * I + r == k ? -inv : ci[r];
+}
+template <int KC>
+__device__ __forceinline__ void tile_row_set(float (&a)[64], const float (&cj)[8], int K, int k, float inv) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) a[KC * 8 + c] = 8 * K + c == k ? -inv : cj[c] * inv;
+}
+#define GRX_SWITCH8(kc, CALL) \
+    switch (kc) {                \
+        case 0: CALL(0); break;  \
+        case 1: CALL(1); break;  \
+        case 2: CALL(2); break;  \
+        case 3: CALL(3); break;  \
+        case 4: CALL(4); break;  \
+        case 5: CALL(5); break;  \
+        case 6: CALL(6); break;  \
+        default: CALL(7); break; \
+    }
+
+// (5') the same sweep with the matrix in registers, for L <= 8 * 31: thread u holds the 8 x 8
+// tile (I, K) of the lower triangle (diagonal tiles hold both triangles, padding is zero).
+// Step k: the owners of column k (and of row k left of the diagonal tile) publish it to col[],
+// every tile takes a_ij -= (a_ik / a_kk) a_kj, and the owners then set a_ik = a_ik / a_kk
+// and a_kk = -1 / a_kk.  Register arrays are indexed by compile-time offsets only.
+__global__ void __launch_bounds__(GRX_THREADS, 1) grx_invert_regs_kernel(const float* __restrict__ Mg,
+                                                                         const double* __restrict__ diag, int L,
+                                                                         float loading, float* __restrict__ B,
+                                                                         int* __restrict__ status) {
+    __shared__ __align__(16) float col[8 * 32];
+    __shared__ float s_floor, s_delta;
+    const int nst = (L + 7) / 8, nstl = ntri(nst);
+    const int u = threadIdx.x;
+    const bool own = u < nstl;
+    int I = 0, K = 0;
+    if (own) tri_decode(u, I, K);
+    if (threadIdx.x == 0) {
+        double tr = 0.0, dmax = 0.0;
+        for (int i = 0; i < L; ++i) { tr += diag[i]; dmax = fmax(dmax, diag[i]); }
+        s_delta = (float)((double)loading * tr / (double)L);
+        s_floor = 16.f * FLT_EPSILON * (float)(dmax + (double)s_delta);
+    }
+    for (int i = threadIdx.x; i < 8 * 32; i += GRX_THREADS) col[i] = 0.f;
+    __syncthreads();
+    float a[64];
+#pragma unroll
+    for (int e = 0; e < 64; ++e) {
+        const int i = 8 * I + (e >> 3), j = 8 * K + (e & 7);
+        float v = 0.f;
+        if (own && i < L && j < L) {
+            v = j <= i ? Mg[ntri(i) + j] : Mg[ntri(j) + i];
+            if (i == j) v += s_delta;
+        }
+        a[e] = v;
+    }
+    bool fail = false;
+    for (int k = 0; k < L; ++k) {
+        const int kt = k >> 3, kc = k & 7;
+        if (own && K == kt) {
+#define GRX_C(n) tile_col_out<n>(a, col, I)
+            GRX_SWITCH8(kc, GRX_C)
+#undef GRX_C
+        } else if (own && I == kt) {
+#define GRX_R(n) tile_row_out<n>(a, col, K)
+            GRX_SWITCH8(kc, GRX_R)
+#undef GRX_R
+        }
+        __syncthreads();
+        const float piv = col[k];
+        if (!(piv > s_floor)) { fail = true; break; }  // uniform
+        const float inv = 1.f / piv;
+        if (own) {
+            float ci[8], cj[8];
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const int i = 8 * I + r;
+                ci[r] = i == k ? 0.f : col[i] * inv;
+            }
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const int j = 8 * K + c;
+                cj[c] = j == k ? 0.f : col[j];
+            }
+#pragma unroll
+            for (int e = 0; e < 64; ++e) a[e] = fmaf(-ci[e >> 3], cj[e & 7], a[e]);
+            if (K == kt) {
+#define GRX_C(n) tile_col_set<n>(a, ci, I, k, inv)
+                GRX_SWITCH8(kc, GRX_C)
+#undef GRX_C
+            }
+            if (I == kt) {
+#define GRX_R(n) tile_row_set<n>(a, cj, K, k, inv)
+                GRX_SWITCH8(kc, GRX_R)
+#undef GRX_R
+            }
+        }
+        __syncthreads();
+    }
+    if (fail) {
+        if (threadIdx.x == 0) *status = 1;
+        return;
+    }
+    if (threadIdx.x == 0) *status = 0;
+    if (own) {
+#pragma unroll
+        for (int e = 0; e < 64; ++e) {
+            const int i = 8 * I + (e >> 3), j = 8 * K + (e & 7);
+            if (i < L && j < L) {
+                B[(size_t)i * L + j] = -a[e];
+                if (I != K) B[(size_t)j * L + i] = -a[e];
+            }
+        }
+    }
+}
+
 // (6) warp w: pixels p0 + w PW .. + PW - 1; lane l: rows i = l + 32 m, m < M
 template <int M, int PW>
 __global__ void __launch_bounds__(GRX_SCORE_THREADS) grx_score_kernel(const float* __restrict__ x, int64_t P, int L,
@@ -228,18 +359,23 @@ __global__ void __launch_bounds__(GRX_SCORE_THREADS) grx_score_kernel(const floa
     for (int q = 0; q < PW; ++q)
 #pragma unroll
         for (int m = 0; m < M; ++m) acc[q][m] = 0.f;
-    for (int k = 0; k < L; ++k) {
-        float bk[M];
+    // acc_i = sum over k < i of B_ik d_k (the strict lower triangle), k in segments of 32: in
+    // segment t only row blocks m >= t take part (compile-time bounds after unrolling t)
 #pragma unroll
-        for (int m = 0; m < M; ++m) {
-            const int i = lane + 32 * m;
-            bk[m] = i < L ? __ldg(B + (size_t)k * L + i) : 0.f;
-        }
+    for (int t = 0; t < M; ++t) {
+        const int k1 = L < 32 * t + 32 ? L : 32 * t + 32;
+#pragma unroll 2
+        for (int k = 32 * t; k < k1; ++k) {
+            float dk[PW];
 #pragma unroll
-        for (int q = 0; q < PW; ++q) {
-            const float dk = dw[q * L + k];
+            for (int q = 0; q < PW; ++q) dk[q] = dw[q * L + k];
 #pragma unroll
-            for (int m = 0; m < M; ++m) acc[q][m] = fmaf(bk[m], dk, acc[q][m]);
+            for (int m = t; m < M; ++m) {
+                const int i = lane + 32 * m;
+                const float bk = (i < L && k < i) ? __ldg(B + (size_t)k * L + i) : 0.f;
+#pragma unroll
+                for (int q = 0; q < PW; ++q) acc[q][m] = fmaf(bk, dk[q], acc[q][m]);
+            }
         }
     }
     const bool failed = *status != 0;
@@ -249,7 +385,10 @@ __global__ void __launch_bounds__(GRX_SCORE_THREADS) grx_score_kernel(const floa
 #pragma unroll
         for (int m = 0; m < M; ++m) {
             const int i = lane + 32 * m;
-            if (i < L) s = fmaf(dw[q * L + i], acc[q][m], s);
+            if (i < L) {  // s = sum_i d_i (B_ii d_i + 2 acc_i)
+                const float di = dw[q * L + i];
+                s = fmaf(di, fmaf(__ldg(B + (size_t)i * L + i), di, 2.f * acc[q][m]), s);
+            }
         }
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -341,11 +480,16 @@ cudaError_t launch_global_rx(const float* x, int64_t P, int L, float loading, fl
     grx_gram_kernel<<<dim3(g.nblk2, g.ngroups), GRX_THREADS, smem_g, s>>>(x, P, L, g.range, mu, g.S, part2);
     const int nent = g.nstl * 64;
     grx_gram_reduce_kernel<<<(nent + 255) / 256, 256, 0, s>>>(part2, g.nblk2, L, P, M, diag);
-    const int in_smem = ntri(L) + L + 4 <= GRX_INV_SMEM_FLOATS;
-    const size_t smem_i = sizeof(float) * (in_smem ? (size_t)(((L + 3) & ~3) + ntri(L)) : (size_t)((L + 3) & ~3));
-    e = cudaFuncSetAttribute(grx_invert_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_i);
-    if (e != cudaSuccess) return e;
-    grx_invert_kernel<<<1, GRX_THREADS, smem_i, s>>>(M, diag, L, loading, B, status, in_smem);
+    if (g.nstl <= GRX_THREADS) {
+        grx_invert_regs_kernel<<<1, GRX_THREADS, 0, s>>>(M, diag, L, loading, B, status);
+    } else {
+        const int in_smem = ntri(L) + L + 4 <= GRX_INV_SMEM_FLOATS;
+        const size_t smem_i =
+            sizeof(float) * (in_smem ? (size_t)(((L + 3) & ~3) + ntri(L)) : (size_t)((L + 3) & ~3));
+        e = cudaFuncSetAttribute(grx_invert_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_i);
+        if (e != cudaSuccess) return e;
+        grx_invert_kernel<<<1, GRX_THREADS, smem_i, s>>>(M, diag, L, loading, B, status, in_smem);
+    }
     const int mrows = (L + 31) / 32;
     if (mrows <= 1) e = launch_score<1, 8>(x, P, L, mu, B, status, score, s);
     else if (mrows <= 2) e = launch_score<2, 8>(x, P, L, mu, B, status, score, s);
