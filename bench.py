@@ -116,6 +116,23 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(v: float, ws: int, device=None) -> float:
+    """The largest of one float per rank (the slowest rank's time); v itself for one rank.
+    device: where the collective's tensor lives (the rank's GPU under NCCL, CPU under gloo)."""
+    if ws <= 1:
+        return float(v)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(ws: int, ms_per_step: float) -> float:
+    """Whole-job throughput: every rank processes its own cube, 3 windows per step."""
+    return ws * 3 * H * W / (ms_per_step * 1e-3) / 1e6
+
+
 def cpu_oracle_sample(cube: np.ndarray, rows: int, min_seconds: float = 0.0):
     """Time the FP64 oracle (as it stands) on the first `rows` rows of the cube: DWT
     plus the three detectors at the three windows, repeated until min_seconds have
@@ -361,14 +378,9 @@ def run_ours(args):
         t1.record(stream)
         torch.cuda.synchronize()
         barrier()
-    ms_total = t0.elapsed_time(t1)
-    if ws > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_total = float(tt.item())
+    ms_total = max_over_ranks(t0.elapsed_time(t1), ws, dev)
     ms_step = ms_total / nsteps
-    value = ws * 3 * H * W / (ms_step * 1e-3) / 1e6
+    value = job_value(ws, ms_step)
 
     # launch durations inside the timed region, on each kernel's own stream (they overlap)
     dwt_ms = sum(e[0].elapsed_time(e[1]) for e in ev) / nsteps
@@ -539,13 +551,8 @@ def run_ours(args):
         stream.synchronize()  # the host reads its scores each step
     s1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = s0.elapsed_time(s1) / e2e_steps
-    if ws > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
-    e2e = {"value": ws * 3 * H * W / (e2e_ms * 1e-3) / 1e6, "unit": UNIT,
+    e2e_ms = max_over_ranks(s0.elapsed_time(s1) / e2e_steps, ws, dev)
+    e2e = {"value": job_value(ws, e2e_ms), "unit": UNIT,
            "h2d_bytes_per_step": H * W * L * 4, "d2h_bytes_per_step": len(WINDOWS) * 3 * H * W * 4,
            "ms_per_step": e2e_ms}
 
