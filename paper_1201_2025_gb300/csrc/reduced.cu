@@ -58,7 +58,7 @@ static int spec_nc(int D) { return D + D * (D + 1) / 2; }
 static int spec_dp(int D) { return D <= 4 ? 4 : 8; }
 
 size_t detect_small_smem(int D, int inner, int outer, int tile_h) {
-    return smem_bytes(spec_dp(D), spec_nc(D), 4, inner, outer, tile_h) + sizeof(float) * (16 * 8 + 8);
+    return smem_bytes(spec_dp(D), spec_nc(D), 4, inner, outer, tile_h) + sizeof(float) * 8;  // + tile reference
 }
 
 // Tallest tile (<= want, >= 8 rows) that lets two CTAs share an SM; else the tallest that

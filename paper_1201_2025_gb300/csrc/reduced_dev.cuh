@@ -82,12 +82,9 @@ struct CensusPayload {                        // linear pixel index, int64
 
 // ---------------------------------------------------------------- stage 0: reflected halo load
 template <int D>
-__device__ __forceinline__ void load_halo_spec(const TileGeom& g, const float* __restrict__ x, float* xs,
-                                               float* part /* D per thread */) {
+__device__ __forceinline__ void load_halo_spec(const TileGeom& g, const float* __restrict__ x, float* xs) {
     using P = SpecPayload<D>;
     const int n = g.HR * g.WR;
-#pragma unroll
-    for (int k = 0; k < D; ++k) part[k] = 0.f;
     if constexpr (D == 4) {
         // eight 16-byte loads in flight per thread before any is stored
         constexpr int B = 8;
@@ -111,7 +108,6 @@ __device__ __forceinline__ void load_halo_spec(const TileGeom& g, const float* _
             for (int u = 0; u < B; ++u)
                 if (dsti[u] >= 0) {
                     *reinterpret_cast<float4*>(xs + (size_t)dsti[u] * P::DP) = v[u];
-                    part[0] += v[u].x; part[1] += v[u].y; part[2] += v[u].z; part[3] += v[u].w;
                 }
         }
     } else {
@@ -122,11 +118,7 @@ __device__ __forceinline__ void load_halo_spec(const TileGeom& g, const float* _
             const float* src = x + ((size_t)gy * g.W + gx) * D;
             float* dst = xs + ((size_t)r * g.XP + c) * P::DP;
 #pragma unroll
-            for (int k = 0; k < D; ++k) {
-                const float v = __ldg(src + k);
-                dst[k] = v;
-                part[k] += v;
-            }
+            for (int k = 0; k < D; ++k) dst[k] = __ldg(src + k);
         }
     }
 }
@@ -427,40 +419,33 @@ __device__ void detect_tile(const DetectArgs& a, int th, int tile_x, int tile_y,
     float* xs = reinterpret_cast<float*>(smem_raw);
     float* hso = xs + (size_t)g.HR * g.XP * P::DP;
     float* hsi = hso + (size_t)NC * g.HR * HP;
-    // tile-mean scratch after the inner sums (in the dynamic buffer, not static shared
-    // memory, so that a kernel holding several instantiations keeps its static size small)
-    float* red = hsi + (size_t)NC * g.nin * HP;  // [16][8]
-    float* cref = red + 16 * 8;                  // [8]
+    // tile reference after the inner sums (in the dynamic buffer, not static shared memory,
+    // so that a kernel holding several instantiations keeps its static size small)
+    float* cref = hsi + (size_t)NC * g.nin * HP;  // [8]
 
-    // stage 0 + tile reference: the mean of the halo region, as 16 fixed partial sums (halo
-    // rows r = v mod 16) combined in a fixed order, whatever the block size
-    float part[D];
-    load_halo_spec<D>(g, a.x, xs, part);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    // stage 0 + tile reference: the mean of the middle halo row (a tile row), summed by warp 0
+    // in a fixed order whatever the block size.  Any value near the tile's data serves: the
+    // shift only keeps the second-moment sums from cancelling.
+    load_halo_spec<D>(g, a.x, xs);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     __syncthreads();
-    for (int v = warp; v < 16; v += nw) {
+    if (warp == 0) {
         float acc[D];
 #pragma unroll
         for (int k = 0; k < D; ++k) acc[k] = 0.f;
-        for (int r = v; r < g.HR; r += 16)
-            for (int c = lane; c < g.WR; c += 32) {
-                const float* px = xs + ((size_t)r * g.XP + c) * P::DP;
+        const int r = g.HR / 2;
+        for (int c = lane; c < g.WR; c += 32) {
+            const float* px = xs + ((size_t)r * g.XP + c) * P::DP;
 #pragma unroll
-                for (int k = 0; k < D; ++k) acc[k] += px[k];
-            }
+            for (int k = 0; k < D; ++k) acc[k] += px[k];
+        }
 #pragma unroll
         for (int k = 0; k < D; ++k) {
             float t = acc[k];
 #pragma unroll
             for (int o = 16; o >= 1; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-            if (lane == 0) red[v * 8 + k] = t;
+            if (lane == 0) cref[k] = t / (float)g.WR;
         }
-    }
-    __syncthreads();
-    if (threadIdx.x < D) {
-        float t = 0.f;
-        for (int v = 0; v < 16; ++v) t += red[v * 8 + threadIdx.x];
-        cref[threadIdx.x] = t / (float)(g.HR * g.WR);
     }
     __syncthreads();
     // stage 1: shift in place
