@@ -206,8 +206,11 @@ wdad_status wdad_autotune(wdad_handle h, int D, int inner, int outer, int* tile_
 
 /* Prepare a batch of n jobs: DWT plans, tile plans (autotune != 0: the autotuner's, else
  * the defaults that wdad_detect uses), a device work list and per-job scratch owned by the
- * batch, and, when use_graph != 0, a CUDA graph of the whole launch (counter reset plus one
- * persistent kernel) captured on a private stream.  The jobs' pointers are baked in: later
+ * batch, and, when use_graph != 0, a CUDA graph of the whole launch captured on a private
+ * stream.  Jobs below 512 x 512 pixels share one persistent kernel (counter reset, then the
+ * kernel); a job of at least 512 x 512 pixels fills the GPU alone and runs as its own DWT and
+ * detector launches after it, in the same graph (running the two side by side on forked
+ * streams measured no faster).  The jobs' pointers are baked in: later
  * launches read and write the same buffers.  With default plans every job's scores are
  * bit-identical to wdad_detect / wdad_detect_all on the same job. */
 wdad_status wdad_batch_create(wdad_handle h, int n, const wdad_job* jobs, int autotune, int use_graph,

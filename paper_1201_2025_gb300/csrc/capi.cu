@@ -35,16 +35,30 @@ struct wdad_cnn_ctx {
     wdad::cnn::Net net;
 };
 
+// A job of at least kBatchDirectPixels pixels fills the GPU on its own: the batch runs it as
+// its own DWT and detector launches (in the same graph), the smaller jobs in the persistent
+// kernel.  Same kernels and plans as the single-cube entry points, so the same scores.
+constexpr int64_t kBatchDirectPixels = 512 * 512;
+
+struct BatchDirect {
+    const float* cube;
+    const float* A;
+    int64_t P;
+    int L, K, th;
+    wdad::DetectArgs args;  // args.x = the job's approximation matrix
+};
+
 struct wdad_batch_ctx {
     wdad_ctx* h = nullptr;
-    int n = 0;
+    int n = 0;  // jobs in the persistent kernel
     int nitems = 0;
     size_t smem = 0;
     wdad::BatchJob* d_jobs = nullptr;
     wdad::BatchItem* d_items = nullptr;
     int* d_counters = nullptr;
     float* d_approx = nullptr;
-    std::vector<int> th;
+    std::vector<int> th;  // every job's plan, in the caller's order
+    std::vector<BatchDirect> direct;
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -612,6 +626,20 @@ wdad_status wdad_autotune(wdad_handle h, int D, int inner, int outer, int* tile_
     }
 }
 
+// The batch's work on one stream: the persistent kernel for the small jobs, then each large
+// job's DWT and detector launches.
+static cudaError_t batch_issue(wdad_batch_ctx* b, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    if (b->n > 0)
+        e = wdad::batch_launch(b->d_jobs, b->d_items, b->nitems, b->d_counters, b->n, b->smem, b->h->num_sms, s);
+    for (const BatchDirect& d : b->direct) {
+        if (e != cudaSuccess) break;
+        e = wdad::launch_dwt_approx(d.cube, d.P, d.L, d.A, d.K, const_cast<float*>(d.args.x), b->h->num_sms, s);
+        if (e == cudaSuccess) e = wdad::launch_detect_small_th(d.args, d.th, s);
+    }
+    return e;
+}
+
 wdad_status wdad_batch_create(wdad_handle h, int n, const wdad_job* jobs, int autotune_plans, int use_graph,
                               wdad_batch* out, void* stream) {
     if (!h) return WDAD_ERR_ARG;
@@ -621,9 +649,11 @@ wdad_status wdad_batch_create(wdad_handle h, int n, const wdad_job* jobs, int au
     wdad_batch_ctx* b = nullptr;
     try {
         DeviceGuard g(h->device);
-        std::vector<wdad::BatchJob> hj((size_t)n);
+        std::vector<wdad::BatchJob> hj;
+        std::vector<BatchDirect> direct;
+        std::vector<int> th_all((size_t)n);
         size_t approx_floats = 0;
-        std::vector<size_t> aoff((size_t)n);
+        std::vector<size_t> aoff, doff;
         size_t smem = 0;
         for (int i = 0; i < n; ++i) {
             const wdad_job& j = jobs[i];
@@ -646,9 +676,27 @@ wdad_status wdad_batch_create(wdad_handle h, int n, const wdad_job* jobs, int au
                 if (st != WDAD_OK) return st;
             }
             if (th < 1) return fail(h, WDAD_ERR_UNSUPPORTED, "batch job %d: window too large", i);
+            th_all[(size_t)i] = th;
+            const size_t P = (size_t)j.H * j.W;
+            if ((int64_t)P >= kBatchDirectPixels) {
+                BatchDirect d{};
+                d.cube = j.cube; d.A = A; d.P = (int64_t)P; d.L = j.L; d.K = K; d.th = th;
+                wdad::DetectArgs& a = d.args;
+                a.H = j.H; a.W = j.W; a.D = K;
+                a.inner = j.params.inner; a.outer = j.params.outer; a.loading = j.params.loading;
+                a.border = j.params.border; a.dwest_mode = j.params.dwest_mode; a.dwest_tau = j.params.dwest_tau;
+                if (j.detector == 3) { a.out[0] = j.scores; a.out[1] = j.scores + P; a.out[2] = j.scores + 2 * P; }
+                else a.out[j.detector] = j.scores;
+                a.flags = j.flags;
+                direct.push_back(d);
+                doff.push_back(approx_floats);
+                approx_floats += ((P * K + 63) / 64) * 64;
+                continue;
+            }
             smem = std::max(smem, wdad::detect_small_smem(K, j.params.inner, j.params.outer, th));
             smem = std::max(smem, wdad::batch_dwt_smem(j.L));
-            wdad::BatchJob& bj = hj[(size_t)i];
+            hj.emplace_back();
+            wdad::BatchJob& bj = hj.back();
             bj = wdad::BatchJob{};
             bj.cube = j.cube; bj.A = A; bj.flags = j.flags;
             bj.H = j.H; bj.W = j.W; bj.L = j.L; bj.K = K;
@@ -656,34 +704,38 @@ wdad_status wdad_batch_create(wdad_handle h, int n, const wdad_job* jobs, int au
             bj.dwest_mode = j.params.dwest_mode; bj.loading = j.params.loading; bj.tau = j.params.dwest_tau;
             bj.th = th;
             bj.variant = wdad::batch_variant(j.L);
-            const size_t P = (size_t)j.H * j.W;
             if (j.detector == 3) { bj.out[0] = j.scores; bj.out[1] = j.scores + P; bj.out[2] = j.scores + 2 * P; }
             else bj.out[j.detector] = j.scores;
-            aoff[(size_t)i] = approx_floats;
+            aoff.push_back(approx_floats);
             approx_floats += ((P * K + 63) / 64) * 64;
         }
+        const int np = (int)hj.size();
         int drop = -1;
         if (const char* e = std::getenv("WDAD_FAULT_DROP_DWT_ITEM")) drop = std::atoi(e);
         std::vector<wdad::BatchItem> items;
         std::vector<int> dwt_items;
-        wdad::batch_build_items(hj, items, dwt_items, drop, 4 * 2 * h->num_sms);
+        if (np > 0) wdad::batch_build_items(hj, items, dwt_items, drop, 4 * 2 * h->num_sms);
         b = new wdad_batch_ctx();
         b->h = h;
-        b->n = n;
+        b->n = np;
         b->nitems = (int)items.size();
         b->smem = smem;
+        b->th = th_all;
         cudaError_t e = cudaMalloc(&b->d_approx, sizeof(float) * std::max<size_t>(approx_floats, 64));
-        if (e == cudaSuccess) e = cudaMalloc(&b->d_jobs, sizeof(wdad::BatchJob) * (size_t)n);
+        if (e == cudaSuccess) e = cudaMalloc(&b->d_jobs, sizeof(wdad::BatchJob) * (size_t)std::max(np, 1));
         if (e == cudaSuccess) e = cudaMalloc(&b->d_items, sizeof(wdad::BatchItem) * std::max<size_t>(items.size(), 1));
-        if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, sizeof(int) * (size_t)(2 + 2 * n));
+        if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, sizeof(int) * (size_t)(2 + 2 * std::max(np, 1)));
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->last, cudaEventDisableTiming);
         if (e != cudaSuccess) { batch_free(b); return cuda_fail(h, e, "batch allocation"); }
-        for (int i = 0; i < n; ++i) {
+        if (np == 0) e = cudaMemsetAsync(b->d_counters, 0, sizeof(int) * 4, s);  // status word stays 0
+        for (int i = 0; i < np; ++i) {
             hj[(size_t)i].approx = b->d_approx + aoff[(size_t)i];
             hj[(size_t)i].dwt_items = dwt_items[(size_t)i];
-            b->th.push_back(hj[(size_t)i].th);
         }
-        e = cudaMemcpyAsync(b->d_jobs, hj.data(), sizeof(wdad::BatchJob) * (size_t)n, cudaMemcpyHostToDevice, s);
+        for (size_t i = 0; i < direct.size(); ++i) direct[i].args.x = b->d_approx + doff[i];
+        b->direct = direct;
+        if (e == cudaSuccess && np > 0)
+            e = cudaMemcpyAsync(b->d_jobs, hj.data(), sizeof(wdad::BatchJob) * (size_t)np, cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess && !items.empty())
             e = cudaMemcpyAsync(b->d_items, items.data(), sizeof(wdad::BatchItem) * items.size(), cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -692,8 +744,7 @@ wdad_status wdad_batch_create(wdad_handle h, int n, const wdad_job* jobs, int au
             e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
             if (e == cudaSuccess) e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
             if (e == cudaSuccess) {
-                cudaError_t el = wdad::batch_launch(b->d_jobs, b->d_items, b->nitems, b->d_counters, n, smem,
-                                                    h->num_sms, b->cap_stream);
+                cudaError_t el = batch_issue(b, b->cap_stream);
                 e = cudaStreamEndCapture(b->cap_stream, &b->graph);
                 if (el != cudaSuccess) e = el;
             }
@@ -712,9 +763,7 @@ wdad_status wdad_batch_launch(wdad_batch b, void* stream) {
     if (!b) return WDAD_ERR_ARG;
     DeviceGuard g(b->h->device);
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = b->exec ? cudaGraphLaunch(b->exec, s)
-                            : wdad::batch_launch(b->d_jobs, b->d_items, b->nitems, b->d_counters, b->n, b->smem,
-                                                 b->h->num_sms, s);
+    cudaError_t e = b->exec ? cudaGraphLaunch(b->exec, s) : batch_issue(b, s);
     if (e == cudaSuccess) e = cudaEventRecord(b->last, s);
     if (e != cudaSuccess) return cuda_fail(b->h, e, "batch launch");
     return WDAD_OK;
@@ -724,7 +773,7 @@ wdad_status wdad_batch_status(wdad_batch b, int* tile_h_out) {
     if (!b) return WDAD_ERR_ARG;
     DeviceGuard g(b->h->device);
     if (tile_h_out)
-        for (int i = 0; i < b->n; ++i) tile_h_out[i] = b->th[(size_t)i];
+        for (size_t i = 0; i < b->th.size(); ++i) tile_h_out[i] = b->th[i];
     cudaError_t e = cudaEventSynchronize(b->last);
     int dev_status = 0;
     if (e == cudaSuccess) e = cudaMemcpy(&dev_status, b->d_counters + 1 + b->n, sizeof(int), cudaMemcpyDeviceToHost);

@@ -120,3 +120,31 @@ def test_batch_rejects_unsupported_band_count(wd):
     with pytest.raises(wd.WdadError) as ei:
         wd.wdad_batch([{"cube": x, "detector": 0, "scores": torch.empty((8, 8), device="cuda")}])
     assert ei.value.status == wd.WDAD_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_large_jobs_run_as_their_own_launches(wd, scenes, use_graph):
+    # jobs of 512 x 512 pixels or more leave the persistent kernel (they fill the GPU alone) and
+    # run as their own DWT and detector launches inside the batch: still the single-cube scores
+    from paper_1201_2025_gb300 import synth
+    jobs = _jobs(wd, scenes[:3])
+    for i, (H, W, L, det) in enumerate(((512, 520, 224, 3), (600, 440, 128, 0))):
+        sc = synth.make_scene(H, W, L, seed=300 + i, n_anom=10, margin=5)
+        jobs.append({"cube": torch.from_numpy(sc.cube).cuda(), "detector": det,
+                     "scores": torch.full((3, H, W) if det == 3 else (H, W), -1.0, device="cuda"),
+                     "over": {"inner": 5, "outer": 15}})
+    b = wd.wdad_batch(jobs, autotune=False, use_graph=use_graph)
+    for _ in range(2):
+        b.launch()
+        st, ths = b.status()
+        assert st == wd.WDAD_OK and len(ths) == len(jobs)
+        for job in jobs:
+            assert torch.equal(job["scores"], _alone(wd, job))
+    b.close()
+    only_large = jobs[3:]
+    b = wd.wdad_batch(only_large, autotune=False, use_graph=use_graph)  # no persistent part at all
+    b.launch()
+    assert b.status()[0] == wd.WDAD_OK
+    for job in only_large:
+        assert torch.equal(job["scores"], _alone(wd, job))
+    b.close()
