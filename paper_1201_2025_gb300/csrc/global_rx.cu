@@ -397,6 +397,88 @@ __global__ void __launch_bounds__(GRX_SCORE_THREADS) grx_score_kernel(const floa
     }
 }
 
+// (6') L % 4 == 0: lane l holds rows 128 g + 4 l .. + 3 (g < G), so one 16-byte load brings
+// four entries of row k of B, and four k steps of a pixel's d come in one 16-byte shared load.
+// Blocks of 128 x 128 below the diagonal count twice and those above it are skipped.
+template <int G, int PW>
+__global__ void __launch_bounds__(GRX_SCORE_THREADS, 2) grx_score4_kernel(const float* __restrict__ x, int64_t P, int L,
+                                                                       const float* __restrict__ mu,
+                                                                       const float* __restrict__ B,
+                                                                       const int* __restrict__ status,
+                                                                       float* __restrict__ score) {
+    extern __shared__ __align__(16) float ds[];  // [PX][L] centred pixels
+    constexpr int PX = PW * (GRX_SCORE_THREADS / 32);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t p0 = (int64_t)blockIdx.x * PX;
+    for (int e = threadIdx.x; e < PX * L; e += GRX_SCORE_THREADS) {
+        const int q = e / L, b = e - q * L;
+        const int64_t p = p0 + q;
+        ds[e] = p < P ? __ldg(x + p * L + b) - __ldg(mu + b) : 0.f;
+    }
+    __syncthreads();
+    const float* dw = ds + (size_t)warp * PW * L;
+    float acc[PW][G][4];
+#pragma unroll
+    for (int q = 0; q < PW; ++q)
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[q][g][j] = 0.f;
+    // s = sum over row groups g of d_g^T (B_gg d_g + 2 sum_{h<g} B_gh d_h): the columns k of
+    // group h feed row groups g >= h only, twice where g > h (compile-time after unrolling h)
+#pragma unroll
+    for (int h = 0; h < G; ++h) {
+        const int k1 = L < 128 * h + 128 ? L : 128 * h + 128;
+        for (int k = 128 * h; k < k1; k += 4) {
+            float4 d4[PW];
+#pragma unroll
+            for (int q = 0; q < PW; ++q) d4[q] = *reinterpret_cast<const float4*>(dw + q * L + k);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                float4 b4[G];
+#pragma unroll
+                for (int g = h; g < G; ++g) {
+                    const int i = 128 * g + 4 * lane;
+                    b4[g] = i < L ? __ldg(reinterpret_cast<const float4*>(B + (size_t)(k + kk) * L + i))
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int q = 0; q < PW; ++q) {
+                    const float dk = kk == 0 ? d4[q].x : kk == 1 ? d4[q].y : kk == 2 ? d4[q].z : d4[q].w;
+#pragma unroll
+                    for (int g = h; g < G; ++g) {
+                        const float w = g == h ? dk : 2.f * dk;
+                        acc[q][g][0] = fmaf(b4[g].x, w, acc[q][g][0]);
+                        acc[q][g][1] = fmaf(b4[g].y, w, acc[q][g][1]);
+                        acc[q][g][2] = fmaf(b4[g].z, w, acc[q][g][2]);
+                        acc[q][g][3] = fmaf(b4[g].w, w, acc[q][g][3]);
+                    }
+                }
+            }
+        }
+    }
+    const bool failed = *status != 0;
+#pragma unroll
+    for (int q = 0; q < PW; ++q) {
+        float s = 0.f;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const int i = 128 * g + 4 * lane;
+            if (i < L) {
+                const float4 di = *reinterpret_cast<const float4*>(dw + q * L + i);
+                s = fmaf(di.x, acc[q][g][0], s);
+                s = fmaf(di.y, acc[q][g][1], s);
+                s = fmaf(di.z, acc[q][g][2], s);
+                s = fmaf(di.w, acc[q][g][3], s);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        const int64_t p = p0 + warp * PW + q;
+        if (lane == 0 && p < P) score[p] = failed ? __int_as_float(0x7fc00000) : s;
+    }
+}
+
 struct GrxLayout {
     int64_t P;
     int L, nblk1, nblk2, nst, nstl, ngroups, S;
@@ -424,7 +506,7 @@ GrxLayout grx_layout(int64_t P, int L, int num_sms) {
     g.range = range;
     g.nblk2 = (int)((P + range - 1) / range);
     const int Lp8 = g.nst * 8;
-    g.S = Lp8 <= 256 ? 32 : Lp8 <= 512 ? 16 : 8;
+    g.S = Lp8 <= 256 ? 64 : Lp8 <= 512 ? 32 : 16;  // pixels staged per chunk (<= 64 KB)
     size_t o = 0;
     g.off_part1 = o; o = a256(o + sizeof(double) * (size_t)g.nblk1 * L);
     g.off_mu = o; o = a256(o + sizeof(float) * (size_t)L);
@@ -447,6 +529,19 @@ cudaError_t launch_score(const float* x, int64_t P, int L, const float* mu, cons
     if (e != cudaSuccess) return e;
     const int64_t grid = (P + PX - 1) / PX;
     grx_score_kernel<M, PW><<<(unsigned)grid, GRX_SCORE_THREADS, smem, s>>>(x, P, L, mu, B, status, score);
+    return cudaGetLastError();
+}
+
+template <int G, int PW>
+cudaError_t launch_score4(const float* x, int64_t P, int L, const float* mu, const float* B, const int* status,
+                          float* score, cudaStream_t s) {
+    constexpr int PX = PW * (GRX_SCORE_THREADS / 32);
+    const size_t smem = sizeof(float) * (size_t)PX * L;
+    cudaError_t e = cudaFuncSetAttribute(grx_score4_kernel<G, PW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t grid = (P + PX - 1) / PX;
+    grx_score4_kernel<G, PW><<<(unsigned)grid, GRX_SCORE_THREADS, smem, s>>>(x, P, L, mu, B, status, score);
     return cudaGetLastError();
 }
 
@@ -491,7 +586,13 @@ cudaError_t launch_global_rx(const float* x, int64_t P, int L, float loading, fl
         grx_invert_kernel<<<1, GRX_THREADS, smem_i, s>>>(M, diag, L, loading, B, status, in_smem);
     }
     const int mrows = (L + 31) / 32;
-    if (mrows <= 1) e = launch_score<1, 8>(x, P, L, mu, B, status, score, s);
+    if (L % 4 == 0 && L > 32) {
+        const int groups = (L + 127) / 128;
+        if (groups <= 1) e = launch_score4<1, 8>(x, P, L, mu, B, status, score, s);
+        else if (groups <= 2) e = launch_score4<2, 8>(x, P, L, mu, B, status, score, s);
+        else if (groups <= 4) e = launch_score4<4, 4>(x, P, L, mu, B, status, score, s);
+        else e = launch_score4<8, 2>(x, P, L, mu, B, status, score, s);
+    } else if (mrows <= 1) e = launch_score<1, 8>(x, P, L, mu, B, status, score, s);
     else if (mrows <= 2) e = launch_score<2, 8>(x, P, L, mu, B, status, score, s);
     else if (mrows <= 4) e = launch_score<4, 8>(x, P, L, mu, B, status, score, s);
     else if (mrows <= 8) e = launch_score<8, 8>(x, P, L, mu, B, status, score, s);
