@@ -404,14 +404,17 @@ def run_ours(args):
     dwt_alone_ms = _time_serial(lambda: wdad.wdad_dwt_approx(x, pdwt, out=approx))
     peak, peak_kind = _peaks()
     dwt_gbs = H * W * BYTES_DWT_PER_PX / (dwt_ms * 1e-3) / 1e9
-    traffic = None  # dram read + write bytes of one launch from the committed ncu summary
-    try:
-        with open(os.path.join(ROOT, "profiles", "dwt_apply_kernel_512x512x224.md")) as f:
-            for line in f:
-                if line.startswith("dram_bytes_per_launch:"):
-                    traffic = int(line.split(":")[1])
-    except Exception:
-        pass
+    def _traffic(name):  # dram read + write bytes of one launch, from the committed ncu summary
+        try:
+            with open(os.path.join(ROOT, "profiles", name)) as f:
+                for line in f:
+                    if line.startswith("dram_bytes_per_launch:"):
+                        return int(line.split(":")[1])
+        except Exception:
+            pass
+        return None
+
+    traffic = _traffic("dwt_apply_kernel_512x512x224.md")
     roofline_dwt = {"kernel": "dwt_apply_kernel", "bound": "hbm", "achieved": dwt_gbs, "peak": peak, "unit": "GB/s",
                     "frac": dwt_gbs / peak, "traffic": traffic, "peak_source": peak_kind,
                     "algorithmic_bytes_per_launch": H * W * BYTES_DWT_PER_PX}
@@ -421,7 +424,8 @@ def run_ours(args):
     det_tflops = H * W * FLOPS_DETECT_PER_PX / (det_avg_ms * 1e-3) / 1e12
     alu_peak = FP32_LANES * sm_mhz * 1e6 / 1e12
     roofline_det = {"kernel": "detect_small_kernel<4>", "bound": "alu", "achieved": det_tflops, "peak": alu_peak,
-                    "unit": "TFLOP/s", "frac": det_tflops / alu_peak, "traffic": None,
+                    "unit": "TFLOP/s", "frac": det_tflops / alu_peak,
+                    "traffic": _traffic("detect_small_kernel_512x512_K4.md"),
                     "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 at {sm_mhz:.0f} MHz",
                     "algorithmic_flops_per_launch": H * W * FLOPS_DETECT_PER_PX}
     # the dominant kernel of the step is the one with the larger share of the step time
