@@ -104,24 +104,29 @@ def test_mixed_without_gate_is_finite_and_unflagged(wd, scene48):
     assert bool(torch.all(flags & 1))
 
 
-@pytest.mark.parametrize("win,gate", [((3, 11), 1e6), ((5, 15), 1e6), ((3, 11), 3e4)])
-def test_mixed_fewer_samples_than_bands_matches_oracle(wd, scene48, win, gate):
+@pytest.mark.parametrize("win,gate,loading", [((3, 11), 1e6, 1e-3), ((5, 15), 1e6, 1e-3), ((3, 11), 3e4, 1e-3),
+                                              ((3, 11), 1e6, 1e-6)])
+def test_mixed_fewer_samples_than_bands_matches_oracle(wd, scene48, win, gate, loading):
     # N < L: mixed LRX/DWRX take the FP32 sample-Gram (Woodbury) solve; pixels below the gate
     # meet the FP32 bar max(1e-4, 32 u kappa), pixels above it are the FP64 re-solve (1e-6)
     from parity import TOL_SCORE, relerr
     cube = scene48.cube.astype(np.float64)
     x = _gpu(scene48.cube)
     pix = _pixels(48, 48, n=40, seed=win[1])
-    _, aux = oracle.detect(cube, 0, win[0], win[1], pixels=pix, want_aux=True, want_cond=True)
+    _, aux = oracle.detect(cube, 0, win[0], win[1], loading=loading, pixels=pix, want_aux=True, want_cond=True)
     kappa = aux[..., 1] / aux[..., 0]
     for det in (0, 1):  # one detector per call: the flags then tell which pixels were re-solved
         flags = torch.zeros((48, 48), dtype=torch.uint8, device="cuda")
         got = wd.wdad_detect(x, det, reduce=False, inner=win[0], outer=win[1], precision=1, cond_gate=gate,
-                             flags=flags).cpu().numpy()
+                             loading=loading, flags=flags).cpu().numpy()
         re = (flags.cpu().numpy().ravel()[pix] & 1).astype(bool)
         tol = np.where(re, 1e-6, np.maximum(TOL_SCORE, 32 * 2.0 ** -24 * kappa))
-        want = oracle.detect(cube, det, win[0], win[1], pixels=pix)
+        want = oracle.detect(cube, det, win[0], win[1], loading=loading, pixels=pix)
         e = relerr(got.ravel()[pix], want)
         assert np.all(e <= tol), (det, e.max(), np.max(e / tol))
-        # the gate bounds kappa from above (|G|_F + delta) / delta, and kappa here is ~1e5
-        assert re.all() if gate < 1e5 else not re.any()
+        # the gate bounds kappa from above by (|G|_F + delta) / delta: every pixel whose kappa is
+        # above the gate is re-solved; at loading 1e-3 kappa here is ~1e5 and the bound stays
+        # below 1 + 1e3 L, so a 1e6 gate re-solves nothing
+        assert re[kappa > gate].all()
+        if loading == 1e-3 and gate >= 1e6:
+            assert not re.any()
