@@ -87,3 +87,14 @@ def test_auc_matches_oracle(wl):
     m = (rng.uniform(size=s.size) < 0.05).astype(np.uint8)
     assert abs(wl.wdad_auc(s, m) - oracle.auc(s.astype(np.float64), m)) < 1e-12
     assert np.isnan(wl.wdad_auc(s, np.zeros_like(m)))
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch):
+    # no CPU fallback: without libwdad.so every call raises instead of computing elsewhere
+    from paper_1201_2025_gb300 import wdad
+    monkeypatch.setattr(wdad, "_lib", None)
+    monkeypatch.setattr(wdad, "_SO", os.path.join(ROOT, "no_such_dir", "libwdad.so"))
+    with pytest.raises(RuntimeError, match="missing"):
+        wdad.lib()
+    with pytest.raises(RuntimeError, match="missing"):
+        wdad.wdad_query_K(224)
