@@ -44,7 +44,7 @@ cudaError_t scratch_ptr(int dev, float** out) {
 
 bool params_ok(const wdad_params* p) {
     if (!p) return false;
-    if (p->wavelet_taps != 8 && p->wavelet_taps != 4) return false;
+    if (p->wavelet_taps < 2 || p->wavelet_taps > wdad::kMaxTaps || (p->wavelet_taps & 1)) return false;
     if (p->level < -1 || p->level > 30) return false;
     if (p->inner < 1 || !(p->inner & 1) || p->outer <= p->inner || !(p->outer & 1) || p->outer > 63) return false;
     if (!(p->loading >= 0.f) || !(p->loading < 3.0e38f)) return false;

@@ -45,6 +45,21 @@ def test_noalloc_matches_detect_all_on_two_calls_in_a_row(wd):
         assert _close(got, want)
 
 
+@pytest.mark.parametrize("taps", [4, 12])
+def test_noalloc_other_filters(wd, taps):
+    from paper_1201_2025_gb300 import synth
+    sc = synth.make_scene(40, 50, 224, seed=13, n_anom=4, margin=4)
+    x = torch.from_numpy(sc.cube).cuda()
+    got = wd.wdad_detect_all_noalloc(x, inner=3, outer=9, wavelet_taps=taps)
+    torch.cuda.synchronize()
+    want = wd.wdad_detect_all(x, reduce=True, inner=3, outer=9, wavelet_taps=taps)
+    torch.cuda.synchronize()
+    assert _close(got, want)
+    with pytest.raises(wd.WdadError) as ei:
+        wd.wdad_detect_all_noalloc(x, wavelet_taps=taps + 1)
+    assert ei.value.status == wd.WDAD_ERR_ARG
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch(wd):
     x = torch.zeros((1025, 1024, 16), device="cuda")  # K = 4: 4,198,400 coefficients > 4,194,304
     with pytest.raises(wd.WdadError) as ei:
