@@ -116,6 +116,13 @@ def _dist():
     return ws, rank, local
 
 
+def _config(ws: int) -> dict:
+    """The workload both arms report (the reference arm times a row sample of it, stated in its
+    cpu_baseline)."""
+    return {"workload": WORKLOAD, "H": H, "W": W, "L": L, "windows": WINDOWS, "path": "DWT-reduced",
+            "l2": "inputs larger than L2 (235 MB cube vs 129 MB L2)", "parallelism": f"replicas x{ws}"}
+
+
 def max_over_ranks(v: float, ws: int, device=None) -> float:
     """The largest of one float per rank (the slowest rank's time); v itself for one rank.
     device: where the collective's tensor lives (the rank's GPU under NCCL, CPU under gloo)."""
@@ -175,7 +182,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample_rows": rows},
+        "config": _config(1),
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -579,8 +586,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": nsteps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded AVIRIS-shaped linear-mixing cube)",
-        "config": {"workload": WORKLOAD, "H": H, "W": W, "L": L, "windows": WINDOWS, "path": "DWT-reduced",
-                   "l2": "inputs larger than L2 (235 MB cube vs 129 MB L2)", "parallelism": f"replicas x{ws}"},
+        "config": _config(ws),
         "roofline": roofline, "roofline_other_kernel": roofline_other, "breakdown": breakdown, "e2e": e2e,
         "cpu_baseline": cpu, "gpu_launches": nsteps * (1 + len(WINDOWS)), "clocks": clocks,
     }), flush=True)
