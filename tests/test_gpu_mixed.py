@@ -130,3 +130,27 @@ def test_mixed_fewer_samples_than_bands_matches_oracle(wd, scene48, win, gate, l
         assert re[kappa > gate].all()
         if loading == 1e-3 and gate >= 1e6:
             assert not re.any()
+
+
+def test_mixed_full_size_ar1_sampled(wd):
+    # the precision workload at full size: 1024 x 1024 x 224 with band-to-band AR(1) noise
+    # (rho 0.98), MIXED LRX and DWRX on every pixel, checked on sampled pixels and every
+    # implanted one against the oracle (FP32 bar of the arithmetic, 1e-6 where re-solved)
+    from parity import TOL_SCORE, relerr
+    from paper_1201_2025_gb300 import synth
+    sc = synth.make_scene(1024, 1024, 224, seed=3, n_anom=400, anom_side=(1, 3), abundance=(0.1, 0.5), margin=10,
+                          ar_rho=0.98)
+    x = _gpu(sc.cube)
+    rng = np.random.default_rng(1024)
+    pix = np.unique(np.concatenate([rng.choice(1024 * 1024, 160, replace=False), np.flatnonzero(sc.mask)[::8],
+                                    [0, 1023, 1024 * 1024 - 1]]))
+    _, aux = oracle.detect(sc.cube, 0, 3, 11, pixels=pix, want_aux=True, want_cond=True)
+    kappa = aux[..., 1] / aux[..., 0]
+    for det in (0, 1):
+        flags = torch.zeros((1024, 1024), dtype=torch.uint8, device="cuda")
+        got = wd.wdad_detect(x, det, reduce=False, inner=3, outer=11, precision=1, flags=flags)
+        got = got.cpu().numpy().ravel()[pix]
+        re = (flags.cpu().numpy().ravel()[pix] & 1).astype(bool)
+        tol = np.where(re, 1e-6, np.maximum(TOL_SCORE, 32 * 2.0 ** -24 * kappa))
+        e = relerr(got, oracle.detect(sc.cube, det, 3, 11, pixels=pix))
+        assert np.all(e <= tol), (det, e.max(), np.max(e / tol))
