@@ -227,10 +227,13 @@ def bench_batching(dev, stream, peak, side_lo=128, side_hi=1024):
     res = {"jobs": len(jobs), "pixels": npx, "cube_GB": sum(j["cube"].numel() * 4 for j in jobs) / 1e9,
            "workload": f"64 cubes, side U{{{side_lo}..{side_hi}}}, L in {{128,188,224}}, windows (3,9)/(5,15)/(7,21), "
                        "one detector each (LRX/DWRX/DWEST), f32, device-generated (same recipe)"}
+    batched = None
     for name, tuned in (("default_plans", False), ("autotuned", True)):
         b = wdad.wdad_batch(jobs, autotune=tuned, use_graph=True)
         ms = _time(b.launch, n=5)
         st, ths = b.status()
+        if not tuned:
+            batched = [j["scores"].clone() for j in jobs]
         res[name] = {"graph_ms": ms, "Mpixel_s": npx / (ms * 1e-3) / 1e6, "status": st,
                      "algorithmic_GBps": nbytes / (ms * 1e-3) / 1e9, "frac_of_hbm": nbytes / (ms * 1e-3) / 1e9 / peak,
                      "tile_heights": {str(t): ths.count(t) for t in sorted(set(ths))}}
@@ -243,7 +246,9 @@ def bench_batching(dev, stream, peak, side_lo=128, side_hi=1024):
     res["sequential"] = {"ms": ms, "Mpixel_s": npx / (ms * 1e-3) / 1e6,
                          "algorithmic_GBps": nbytes / (ms * 1e-3) / 1e9}
     res["speedup_graph_vs_sequential"] = ms / res["default_plans"]["graph_ms"]
-    del jobs
+    # the default-plan batch must give the single-cube entry points' scores bit for bit
+    res["default_plans"]["bit_identical_to_sequential"] = all(torch.equal(a, j["scores"]) for a, j in zip(batched, jobs))
+    del jobs, batched
     torch.cuda.empty_cache()
     return res
 

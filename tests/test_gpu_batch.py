@@ -148,3 +148,24 @@ def test_large_jobs_run_as_their_own_launches(wd, scenes, use_graph):
     for job in only_large:
         assert torch.equal(job["scores"], _alone(wd, job))
     b.close()
+
+
+def test_full_batching_workload_bit_identical(wd):
+    # the batching workload at full size: 64 cubes, side U{128..1024}, L in {128, 188, 224},
+    # mixed windows and detectors (device-generated, about 20 GB), one graph launch
+    from paper_1201_2025_gb300 import synth
+    jobs = []
+    for sp in synth.batch_specs(64, seed=0):
+        cube, _ = synth.make_scene_device(sp["H"], sp["W"], sp["L"], seed=sp["seed"], n_anom=4, anom_side=(1, 3),
+                                          abundance=(0.1, 0.5), margin=10, device=torch.device("cuda", 0))
+        jobs.append({"cube": cube, "detector": sp["detector"], "scores": torch.full((sp["H"], sp["W"]), -1.0,
+                                                                                    device="cuda"),
+                     "over": {"inner": sp["inner"], "outer": sp["outer"]}})
+    b = wd.wdad_batch(jobs, autotune=False, use_graph=True)
+    b.launch()
+    assert b.status()[0] == wd.WDAD_OK
+    for job in jobs:
+        assert torch.equal(job["scores"], _alone(wd, job))
+    b.close()
+    del jobs
+    torch.cuda.empty_cache()
