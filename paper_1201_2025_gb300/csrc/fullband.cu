@@ -7,7 +7,9 @@
 // as 4x4 tiles of its lower triangle ("tile-packed").
 //   LRX / DWRX (Eq. 1, 5): C_o + delta I, delta = loading * trace(C_o) / D, blocked
 //     Cholesky on the tiles bordered by the two right-hand sides r - mu_o and
-//     mu_i - mu_o (so it also yields L^-1 d), score = ||L^-1 d||^2.
+//     mu_i - mu_o (so it also yields L^-1 d), score = ||L^-1 d||^2.  With fewer
+//     background samples than bands (N < D) the same scores come from the N x N sample
+//     Gram through the Woodbury identity, so the factorisation runs at dimension N.
 //   DWEST (Eq. 2-4): C_diff = C_i - C_o; Householder tridiagonalisation; the
 //     eigenvalues above tau = dwest_tau * max|lambda| by Sturm-count bisection (a
 //     warp evaluates 32 points per step); their eigenvectors by inverse iteration on
