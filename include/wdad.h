@@ -132,6 +132,15 @@ wdad_status wdad_detect_all(wdad_handle h, const float* cube, int H, int W, int 
                             int reduce, const wdad_params* p,
                             float* scores, uint8_t* flags, void* stream);
 
+/* All three detectors at nwin windows (params[0..nwin-1], same wavelet and level) in one
+ * call: scores [nwin][3][H][W] device float32, flags (nullable) [nwin][H][W] uint8.  On the
+ * reduced cube (and any cube of at most 8 bands) up to four windows share one launch, one
+ * grid whose blocks each take a tile of one window; every window's maps equal those of
+ * wdad_detect_all with the same params.  reduce = 1 runs the DWT first (handle workspace);
+ * more than 8 bands run one full-band pass per window.  nwin 1..64. */
+wdad_status wdad_detect_windows(wdad_handle h, const float* cube, int H, int W, int L, int reduce, int nwin,
+                                const wdad_params* params, float* scores, uint8_t* flags, void* stream);
+
 /* The same pass from HOST memory, for callers whose cube lives on the host: the
  * cube is reduced once (reduce = 1), all three detectors run for each of the nwin
  * parameter sets params[0..nwin-1] (same wavelet and level), and the score maps are

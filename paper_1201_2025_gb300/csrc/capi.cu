@@ -197,6 +197,43 @@ wdad_status detect_bands(wdad_ctx* h, const float* x, int H, int W, int D, const
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+// nwin windows of all three detectors on a D-band device cube x: out[w] = [3][H][W] at
+// out + w * 3 * H * W, flags (nullable) [nwin][H][W].  D <= 8: the windows go in groups of up
+// to four into single launches; larger D: one full-band pass per window (scratch: ws).
+wdad_status detect_windows(wdad_ctx* h, const float* x, int H, int W, int D, int nwin, const wdad_params* params,
+                           float* out, uint8_t* flags, void* ws, size_t ws_bytes, cudaStream_t s) {
+    const size_t P = (size_t)H * W;
+    if (D <= 8) {
+        for (int w0 = 0; w0 < nwin; w0 += wdad::kMaxWindowsPerLaunch) {
+            const int n = std::min(wdad::kMaxWindowsPerLaunch, nwin - w0);
+            wdad::DetectArgs a[wdad::kMaxWindowsPerLaunch];
+            for (int i = 0; i < n; ++i) {
+                const wdad_params* p = &params[w0 + i];
+                if (wdad::detect_small_smem(D, p->inner, p->outer, 1) > 227 * 1024)
+                    return fail(h, WDAD_ERR_UNSUPPORTED, "window %d/%d too large for %d bands", p->inner, p->outer, D);
+                a[i] = wdad::DetectArgs{};
+                a[i].x = x; a[i].H = H; a[i].W = W; a[i].D = D;
+                a[i].inner = p->inner; a[i].outer = p->outer; a[i].loading = p->loading; a[i].border = p->border;
+                a[i].dwest_mode = p->dwest_mode; a[i].dwest_tau = p->dwest_tau;
+                float* o = out + (size_t)(w0 + i) * 3 * P;
+                a[i].out[0] = o; a[i].out[1] = o + P; a[i].out[2] = o + 2 * P;
+                a[i].flags = flags ? flags + (size_t)(w0 + i) * P : nullptr;
+            }
+            cudaError_t e = wdad::launch_detect_small_multi(a, n, s);
+            if (e != cudaSuccess) return cuda_fail(h, e, "detect_small (windows) launch");
+        }
+        return WDAD_OK;
+    }
+    for (int w = 0; w < nwin; ++w) {
+        float* o = out + (size_t)w * 3 * P;
+        float* out3[3] = {o, o + P, o + 2 * P};
+        wdad_status st = detect_bands(h, x, H, W, D, &params[w], out3, flags ? flags + (size_t)w * P : nullptr, ws,
+                                      ws_bytes, s);
+        if (st != WDAD_OK) return st;
+    }
+    return WDAD_OK;
+}
+
 wdad_status full_ws_need(wdad_ctx* h, int H, int W, int D, const wdad_params* p, size_t* need) {
     *need = 0;
     if (D <= 8) return WDAD_OK;
@@ -496,6 +533,53 @@ wdad_status wdad_detect_all(wdad_handle h, const float* cube, int H, int W, int 
     }
 }
 
+wdad_status wdad_detect_windows(wdad_handle h, const float* cube, int H, int W, int L, int reduce, int nwin,
+                                const wdad_params* params, float* scores, uint8_t* flags, void* stream) {
+    if (!h) return WDAD_ERR_ARG;
+    if (nwin < 1 || nwin > 64 || !params) return fail(h, WDAD_ERR_ARG, "nwin must be 1..64 with params[nwin]");
+    if (reduce != 0 && reduce != 1) return fail(h, WDAD_ERR_ARG, "reduce must be 0 or 1");
+    try {
+        DeviceGuard g(h->device);
+        for (int w = 0; w < nwin; ++w) {
+            wdad_status st = check_params(h, &params[w]);
+            if (st != WDAD_OK) return st;
+            if (reduce && (params[w].wavelet_taps != params[0].wavelet_taps || params[w].level != params[0].level))
+                return fail(h, WDAD_ERR_ARG, "all windows of one call share the wavelet and level");
+        }
+        wdad_status st = check_cube(h, cube, H, W, L);
+        if (st != WDAD_OK) return st;
+        const int64_t P = (int64_t)H * W;
+        if (P == 0) return WDAD_OK;
+        if (!scores) return fail(h, WDAD_ERR_ARG, "scores is NULL");
+        cudaStream_t s = (cudaStream_t)stream;
+        const int D = reduce ? wdad_query_K(L, params[0].wavelet_taps, params[0].level) : L;
+        size_t full = 0;
+        for (int w = 0; w < nwin; ++w) {
+            size_t need = 0;
+            st = full_ws_need(h, H, W, D, &params[w], &need);
+            if (st != WDAD_OK) return st;
+            full = std::max(full, need);
+        }
+        const size_t b_red = reduce ? align256(sizeof(float) * (size_t)P * D) : 0;
+        st = ensure_ws(h, b_red + full);
+        if (st != WDAD_OK) return st;
+        const float* x = cube;
+        if (reduce) {
+            const float* A = nullptr;
+            int k2 = 0;
+            st = get_dwt_plan(h, L, params[0].wavelet_taps, params[0].level, &A, &k2, s);
+            if (st != WDAD_OK) return st;
+            float* xr = (float*)h->ws;
+            cudaError_t e = wdad::launch_dwt_approx(cube, P, L, A, D, xr, h->num_sms, s);
+            if (e != cudaSuccess) return cuda_fail(h, e, "dwt_approx launch");
+            x = xr;
+        }
+        return detect_windows(h, x, H, W, D, nwin, params, scores, flags, (char*)h->ws + b_red, full, s);
+    } catch (...) {
+        return fail(h, WDAD_ERR_NOMEM, "host exception");
+    }
+}
+
 wdad_status wdad_detect_all_host(wdad_handle h, const float* host_cube, int H, int W, int L, int reduce,
                                  int nwin, const wdad_params* params, float* host_scores, void* stream) {
     if (!h) return WDAD_ERR_ARG;
@@ -558,12 +642,8 @@ wdad_status wdad_detect_all_host(wdad_handle h, const float* host_cube, int H, i
             if (e != cudaSuccess) return cuda_fail(h, e, "dwt_approx launch");
             x = d_red;
         }
-        for (int w = 0; w < nwin; ++w) {
-            float* o = d_out + (size_t)w * 3 * P;
-            float* out3[3] = {o, o + P, o + 2 * P};
-            st = detect_bands(h, x, H, W, D, &params[w], out3, nullptr, scratch, full, s);
-            if (st != WDAD_OK) return st;
-        }
+        st = detect_windows(h, x, H, W, D, nwin, params, d_out, nullptr, scratch, full, s);
+        if (st != WDAD_OK) return st;
         e = cudaMemcpyAsync(host_scores, d_out, sizeof(float) * (size_t)P * 3 * nwin, cudaMemcpyDeviceToHost, s);
         if (e != cudaSuccess) return cuda_fail(h, e, "copy scores to host");
         return WDAD_OK;

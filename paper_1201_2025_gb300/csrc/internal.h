@@ -57,6 +57,9 @@ struct DetectArgs {
 cudaError_t launch_detect_small(const DetectArgs& a, int tile_h, cudaStream_t s);
 // exact tile height (the plan); default plan of a configuration
 cudaError_t launch_detect_small_th(const DetectArgs& a, int th, cudaStream_t s);
+// up to kMaxWindowsPerLaunch windows of one cube (same x, H, W, D; default plans) in one launch
+constexpr int kMaxWindowsPerLaunch = 4;
+cudaError_t launch_detect_small_multi(const DetectArgs* a, int n, cudaStream_t s);
 int detect_small_default_th(int D, int inner, int outer);
 // Global RX of Eq. 1 on a [P][L] cube (L <= kGlobalRxMaxBands), scores [P]; workspace from
 // global_rx_workspace_bytes (0 for unsupported sizes).

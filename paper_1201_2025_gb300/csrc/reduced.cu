@@ -9,6 +9,40 @@ __global__ void __launch_bounds__(512) detect_small_kernel(DetectArgs a, int th)
     detect_tile<D>(a, th, blockIdx.x, blockIdx.y, smem_raw);
 }
 
+// Several windows of one cube in one launch: the CTAs of window w are blocks
+// [first[w], first[w + 1]) of a 1-D grid; each copies its window's arguments to shared
+// memory and runs the same tile code (whose results do not depend on the block size), so
+// every window's scores equal its own launch's.  One grid leaves no tail between windows.
+struct MultiArgs {
+    DetectArgs a[kMaxWindowsPerLaunch];
+    int th[kMaxWindowsPerLaunch];
+    int tiles_x[kMaxWindowsPerLaunch];
+    int first[kMaxWindowsPerLaunch + 1];
+    int n;
+};
+
+template <int D>
+__global__ void __launch_bounds__(512) detect_multi_kernel(MultiArgs m) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ DetectArgs s_args;
+    __shared__ int s_w;
+    if (threadIdx.x == 0) {
+        int w = 0;
+        while (w + 1 < m.n && (int)blockIdx.x >= m.first[w + 1]) ++w;
+        s_w = w;
+        // compile-time indices: a runtime index into the parameter array would copy it locally
+        if (w == 0) s_args = m.a[0];
+        else if (w == 1) s_args = m.a[1];
+        else if (w == 2) s_args = m.a[2];
+        else s_args = m.a[3];
+    }
+    __syncthreads();
+    const int w = s_w;
+    const int t = (int)blockIdx.x - m.first[w];
+    const int tx = m.tiles_x[w];
+    detect_tile<D>(s_args, m.th[w], t % tx, t / tx, smem_raw);
+}
+
 // ---------------------------------------------------------------- census kernel
 __global__ void __launch_bounds__(512) census_kernel(int H, int W, int inner, int outer, int border, int th,
                                                      long long* __restrict__ out) {
@@ -119,6 +153,49 @@ cudaError_t launch_detect_small(const DetectArgs& a, int tile_h, cudaStream_t s)
         case 6: return launch_d<6>(a, th, s);
         case 7: return launch_d<7>(a, th, s);
         case 8: return launch_d<8>(a, th, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int D>
+static cudaError_t launch_multi_d(const MultiArgs& m, size_t smem, int blocks, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(detect_multi_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    detect_multi_kernel<D><<<blocks, 512, smem, s>>>(m);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_detect_small_multi(const DetectArgs* a, int n, cudaStream_t s) {
+    if (n < 1 || n > kMaxWindowsPerLaunch) return cudaErrorInvalidValue;
+    MultiArgs m{};
+    m.n = n;
+    size_t smem = 0;
+    int64_t blocks = 0;
+    for (int w = 0; w < n; ++w) {
+        if (a[w].D != a[0].D || a[w].H != a[0].H || a[w].W != a[0].W || a[w].x != a[0].x)
+            return cudaErrorInvalidValue;
+        const int th = pick_th(a[w].D, a[w].inner, a[w].outer, 16);
+        if (th == 0) return cudaErrorInvalidValue;
+        m.a[w] = a[w];
+        m.th[w] = th;
+        m.tiles_x[w] = (a[w].W + TW - 1) / TW;
+        m.first[w] = (int)blocks;
+        blocks += (int64_t)m.tiles_x[w] * ((a[w].H + th - 1) / th);
+        smem = std::max(smem, detect_small_smem(a[w].D, a[w].inner, a[w].outer, th));
+    }
+    m.first[n] = (int)blocks;
+    if (blocks == 0) return cudaSuccess;
+    if (blocks > INT32_MAX) return cudaErrorInvalidValue;
+    switch (a[0].D) {
+        case 1: return launch_multi_d<1>(m, smem, (int)blocks, s);
+        case 2: return launch_multi_d<2>(m, smem, (int)blocks, s);
+        case 3: return launch_multi_d<3>(m, smem, (int)blocks, s);
+        case 4: return launch_multi_d<4>(m, smem, (int)blocks, s);
+        case 5: return launch_multi_d<5>(m, smem, (int)blocks, s);
+        case 6: return launch_multi_d<6>(m, smem, (int)blocks, s);
+        case 7: return launch_multi_d<7>(m, smem, (int)blocks, s);
+        case 8: return launch_multi_d<8>(m, smem, (int)blocks, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -93,6 +93,7 @@ def lib() -> ctypes.CDLL:
     L.wdad_adaptive_threshold.argtypes = [vp, f32p, i64, ctypes.c_double, vp, vp, vp]
     L.wdad_wavelet_filter.argtypes = [i32, vp]
     L.wdad_global_rx.argtypes = [vp, f32p, i32, i32, i32, i32, pp, f32p, vp]
+    L.wdad_detect_windows.argtypes = [vp, f32p, i32, i32, i32, i32, i32, pp, f32p, vp, vp]
     for name in ("wdad_create", "wdad_destroy", "wdad_last_error_detail", "wdad_dwt_approx", "wdad_detect",
                  "wdad_detect_all", "wdad_detect_all_host", "wdad_window_census", "wdad_auc",
                  "wdad_detect_all_noalloc", "wdad_window_moments", "wdad_autotune", "wdad_batch_create",
@@ -100,7 +101,7 @@ def lib() -> ctypes.CDLL:
                  "wdad_cnn_create", "wdad_cnn_destroy", "wdad_cnn_set_norm", "wdad_cnn_params",
                  "wdad_cnn_set_params", "wdad_cnn_forward", "wdad_cnn_grad", "wdad_cnn_train", "wdad_cnn_save",
                  "wdad_cnn_load", "wdad_screen_run", "wdad_scene_whitening", "wdad_adaptive_threshold",
-                 "wdad_wavelet_filter", "wdad_global_rx"):
+                 "wdad_wavelet_filter", "wdad_global_rx", "wdad_detect_windows"):
         getattr(L, name).restype = i32
     L.wdad_query_K.restype = i32
     _lib = L
@@ -202,6 +203,22 @@ def wdad_detect(cube, detector: int, reduce: bool = True, params: wdad_params | 
     h = handle(cube.device.index or 0)
     _check(lib().wdad_detect(h, cube.data_ptr(), H, W, L, int(detector), int(bool(reduce)), ctypes.byref(p),
                              out.data_ptr(), flags.data_ptr() if flags is not None else None, _stream(cube)), h)
+    return out
+
+
+def wdad_detect_windows(cube, params, reduce: bool = True, out=None, flags=None):
+    """LRX, DWRX, DWEST at several windows in one call: [nwin, 3, H, W] float32.
+    params: a list of wdad_params (same wavelet and level)."""
+    import torch
+    cube = _cube(cube)
+    H, W, L = cube.shape
+    n = len(params)
+    arr = (wdad_params * n)(*params)
+    if out is None:
+        out = torch.empty((n, 3, H, W), device=cube.device, dtype=torch.float32)
+    h = handle(cube.device.index or 0)
+    _check(lib().wdad_detect_windows(h, cube.data_ptr(), H, W, L, int(bool(reduce)), n, arr, out.data_ptr(),
+                                     flags.data_ptr() if flags is not None else None, _stream(cube)), h)
     return out
 
 

@@ -258,3 +258,29 @@ def test_host_entry_point_matches_device_path(wd, scene48, pinned):
     for i, (a, b) in enumerate(wins):
         dev = wd.wdad_detect_all(x, reduce=True, inner=a, outer=b).cpu()
         assert torch.equal(out[i], dev)
+
+
+@pytest.mark.parametrize("case", ["reduced", "direct5", "fullband"])
+def test_detect_windows_equal_to_one_window_at_a_time(wd, scene48, case):
+    # up to four windows share one launch (one grid, tiles of every window); each window's maps
+    # and flags must be those of wdad_detect_all with the same parameters, bit for bit
+    wins = [(3, 9), (5, 15), (7, 21), (1, 5), (3, 11), (5, 13)]
+    if case == "reduced":
+        x, reduce = _gpu(scene48.cube), True
+    elif case == "direct5":
+        rng = np.random.default_rng(5)
+        x, reduce = _gpu(1.0 + 0.2 * rng.standard_normal((37, 70, 5))), False
+    else:
+        rng = np.random.default_rng(6)
+        x, reduce, wins = _gpu(1.0 + 0.2 * rng.standard_normal((14, 17, 20))), False, wins[:2]
+    params = [wd.wdad_default_params(inner=a, outer=b, border=i % 2, dwest_mode=(i // 2) % 2)
+              for i, (a, b) in enumerate(wins)]
+    H, W = x.shape[:2]
+    flags = torch.zeros((len(wins), H, W), dtype=torch.uint8, device="cuda")
+    got = wd.wdad_detect_windows(x, params, reduce=reduce, flags=flags)
+    for i, p in enumerate(params):
+        f1 = torch.zeros((H, W), dtype=torch.uint8, device="cuda")
+        want = wd.wdad_detect_all(x, reduce=reduce, params=p, flags=f1)
+        # bitwise (the border windows hold NaN)
+        assert torch.equal(got[i].contiguous().view(torch.int32), want.view(torch.int32)), (case, wins[i])
+        assert torch.equal(flags[i], f1)
