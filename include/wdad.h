@@ -228,7 +228,10 @@ wdad_status wdad_batch_create(wdad_handle h, int n, const wdad_job* jobs, int au
 wdad_status wdad_batch_launch(wdad_batch b, void* stream);
 /* Synchronise the batch's last launch and report its device status: WDAD_OK, or
  * WDAD_ERR_TIMEOUT when a tile gave up waiting for its cube's DWT (that job's scores are
- * then not written).  *tile_h_out (nullable, n entries) receives each job's tile height. */
+ * then not written).  *tile_h_out (nullable, n entries) receives each job's tile height.
+ * Fault injection for tests: with the environment variable WDAD_FAULT_DROP_DWT_ITEM=j set
+ * when the batch is created, the work list of persistent-kernel job j loses one DWT item, so
+ * that job's tiles run into their bounded wait (host-side; no device fault is raised). */
 wdad_status wdad_batch_status(wdad_batch b, int* tile_h_out);
 wdad_status wdad_batch_destroy(wdad_batch b);
 /* One-shot: create (default plans, no graph), launch on `stream`, synchronise, destroy. */
