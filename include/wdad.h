@@ -7,7 +7,9 @@
  * through a Daubechies DWT along the band axis, only the approximation
  * coefficients are kept (Sec. 4, Eq. 7/9, Fig. 1), and the local detectors LRX
  * (Sec. 2.1, Eq. 1), DWRX (Sec. 2.3, Eq. 5) and DWEST (Sec. 2.2, Eq. 2-4) run on
- * that reduced cube or on the full-band cube.
+ * that reduced cube or on the full-band cube.  Also: global RX (Eq. 1 with the whole
+ * image as background), the adaptive cut-off of Eq. 12, batches of uneven cubes, and a
+ * learned screening pass that runs the exact detector on selected pixels only.
  *
  * Conventions shared by every entry point
  *   - Cubes are float32, band-interleaved-by-pixel: element (y, x, l) sits at
