@@ -149,3 +149,23 @@ def test_fullband_fewer_samples_than_bands(wd, D, win, prec):
     want, aux = oracle.detect(c64, 2, win[0], win[1], pixels=pix, want_aux=True)
     e = dwest_relerr(got[2].ravel()[pix], want, aux)
     assert e.max() <= (1e-6 if prec == 2 else TOL_SCORE), e.max()
+
+
+def test_fullband_fewer_samples_valid_border_and_flags(wd):
+    # the sample-Gram form with border = 1: NaN and flag bit 2 outside the valid region, the
+    # oracle's scores inside
+    rng = np.random.default_rng(12)
+    cube = (0.2 * rng.standard_normal((18, 21, 64)) + 1.0).astype(np.float32)
+    flags = torch.zeros((18, 21), dtype=torch.uint8, device="cuda")
+    got = wd.wdad_detect_all(_gpu(cube), reduce=False, inner=3, outer=7, border=1, precision=0,
+                             flags=flags).cpu().numpy()
+    f = flags.cpu().numpy()
+    inv = np.ones((18, 21), bool)
+    inv[3:-3, 3:-3] = False
+    assert np.isnan(got[:2, inv]).all() and np.all(f[inv] == 4)
+    c64 = cube.astype(np.float64)
+    for det in (0, 1):
+        want = oracle.detect(c64, det, 3, 7, border=1)
+        e = relerr(got[det], want)[~inv]
+        tol = np.asarray(_fp32_rx_tol(c64, det, (3, 7), None)).reshape(18, 21)[~inv]
+        assert np.all(e <= tol), (det, e.max())

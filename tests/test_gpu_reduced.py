@@ -284,3 +284,20 @@ def test_detect_windows_equal_to_one_window_at_a_time(wd, scene48, case):
         # bitwise (the border windows hold NaN)
         assert torch.equal(got[i].contiguous().view(torch.int32), want.view(torch.int32)), (case, wins[i])
         assert torch.equal(flags[i], f1)
+
+
+def test_detect_windows_arguments(wd, scene48):
+    x = _gpu(scene48.cube[:20, :20])
+    with pytest.raises(wd.WdadError) as ei:  # windows of one call share the wavelet and level
+        wd.wdad_detect_windows(x, [wd.wdad_default_params(), wd.wdad_default_params(wavelet_taps=4)])
+    assert ei.value.status == wd.WDAD_ERR_ARG
+    with pytest.raises(wd.WdadError) as ei:
+        wd.wdad_detect_windows(x, [wd.wdad_default_params(inner=4, outer=9)])
+    assert ei.value.status == wd.WDAD_ERR_ARG
+    # eight-band direct cube, exactly four windows (one full launch)
+    rng = np.random.default_rng(8)
+    c8 = _gpu(1.0 + 0.2 * rng.standard_normal((29, 45, 8)))
+    params = [wd.wdad_default_params(inner=a, outer=b) for a, b in ((1, 3), (3, 7), (3, 9), (5, 11))]
+    got = wd.wdad_detect_windows(c8, params, reduce=False)
+    for i, p in enumerate(params):
+        assert torch.equal(got[i], wd.wdad_detect_all(c8, reduce=False, params=p))
