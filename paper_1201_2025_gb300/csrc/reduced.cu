@@ -1,4 +1,6 @@
 // Launchers and kernels of the reduced-band detectors (device code in reduced_dev.cuh).
+#include <algorithm>
+
 #include "reduced_dev.cuh"
 
 namespace wdad {
@@ -172,16 +174,21 @@ cudaError_t launch_detect_small_multi(const DetectArgs* a, int n, cudaStream_t s
     m.n = n;
     size_t smem = 0;
     int64_t blocks = 0;
-    for (int w = 0; w < n; ++w) {
+    // the widest windows' tiles (the slowest) first, so that the grid ends on short tiles
+    int order[kMaxWindowsPerLaunch];
+    for (int w = 0; w < n; ++w) order[w] = w;
+    std::stable_sort(order, order + n, [&](int p, int q) { return a[p].outer > a[q].outer; });
+    for (int j = 0; j < n; ++j) {
+        const int w = order[j];
         if (a[w].D != a[0].D || a[w].H != a[0].H || a[w].W != a[0].W || a[w].x != a[0].x)
             return cudaErrorInvalidValue;
         const int th = pick_th(a[w].D, a[w].inner, a[w].outer, 16);
         if (th == 0) return cudaErrorInvalidValue;
-        m.a[w] = a[w];
-        m.th[w] = th;
-        m.tiles_x[w] = (a[w].W + TW - 1) / TW;
-        m.first[w] = (int)blocks;
-        blocks += (int64_t)m.tiles_x[w] * ((a[w].H + th - 1) / th);
+        m.a[j] = a[w];
+        m.th[j] = th;
+        m.tiles_x[j] = (a[w].W + TW - 1) / TW;
+        m.first[j] = (int)blocks;
+        blocks += (int64_t)m.tiles_x[j] * ((a[w].H + th - 1) / th);
         smem = std::max(smem, detect_small_smem(a[w].D, a[w].inner, a[w].outer, th));
     }
     m.first[n] = (int)blocks;
