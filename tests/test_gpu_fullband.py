@@ -37,12 +37,19 @@ def _sample(H, W, mask, n=96, seed=0):
     return np.array(sorted(pix))
 
 
+# FP32 full-band bar: max(1e-4, C_FP32 u kappa(C_o + delta I)) per pixel.  C_o (or the N x N
+# sample Gram of the Woodbury form) is formed and factored in FP32, so the score carries a
+# relative error of a multiple of u kappa.  Measured on GB300 over these tests' cases, the L x L
+# form at 13-224 bands and the sample-Gram form at N = 8..200: at most 0.50 u kappa (37 bands,
+# window 3/9), 0.45 (224 bands, 5/15 sample Gram), 0.30 (224 bands, 1/5, N = 24).  C_FP32 = 1.5
+# leaves a factor of 3.
+C_FP32 = 1.5
+
+
 def _fp32_rx_tol(cube, det, win, pix):
-    """FP32 bound from the arithmetic: C_o is formed and stored in FP32, so an
-    FP32 score carries a relative error up to ~ c u kappa(C_o + delta I) (c = 32)."""
     _, aux = oracle.detect(cube, det, win[0], win[1], pixels=pix, want_aux=True, want_cond=True)
     kappa = aux[..., 1] / aux[..., 0]
-    return np.maximum(TOL_SCORE, 32 * U32 * kappa)
+    return np.maximum(TOL_SCORE, C_FP32 * U32 * kappa)
 
 
 @pytest.mark.parametrize("prec", [2, 0])
