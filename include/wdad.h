@@ -187,8 +187,10 @@ wdad_status wdad_window_census(wdad_handle h, int H, int W, const wdad_params* p
  *   - Limits: H * W * K <= 4,194,304 (e.g. 1024 x 1024 pixels at K = 4), L <= 1024,
  *     K <= 8.  Larger sizes return WDAD_ERR_ARG; windows whose tile does not fit
  *     shared memory return WDAD_ERR_UNSUPPORTED.  Other argument rules as wdad_detect_all.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress).  Make that first call before any stream capture.
+ *   - Every call looks up the array's device address in the current context
+ *     (cudaGetSymbolAddress; not a stream operation), so a context torn down and made
+ *     again is handled.  The first call on a device may also load the library's module
+ *     into the context.  Make that first call before any stream capture.
  *   - Every call on a device shares the one array.  Calls that overlap on the GPU (other
  *     streams, other host threads) race on it and must be serialised by the caller.
  *     Nothing in it needs clearing: each call overwrites what it reads.
@@ -230,7 +232,10 @@ wdad_status wdad_batch_create(wdad_handle h, int n, const wdad_job* jobs, int au
 wdad_status wdad_batch_launch(wdad_batch b, void* stream);
 /* Synchronise the batch's last launch and report its device status: WDAD_OK, or
  * WDAD_ERR_TIMEOUT when a tile gave up waiting for its cube's DWT (that job's scores are
- * then not written).  *tile_h_out (nullable, n entries) receives each job's tile height.
+ * then not written) or a staged DWT chunk never arrived, or WDAD_ERR_CUDA when, after such a
+ * chunk, the copies queued behind it did not land either: a CTA then left while bulk copies
+ * may still write its shared memory, so the batch must be destroyed and the device context
+ * reset before further use.  *tile_h_out (nullable, n entries) receives each job's tile height.
  * Fault injection for tests: with the environment variable WDAD_FAULT_DROP_DWT_ITEM=j set
  * when the batch is created, the work list of persistent-kernel job j loses one DWT item, so
  * that job's tiles run into their bounded wait (host-side; no device fault is raised). */

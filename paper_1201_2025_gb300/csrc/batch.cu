@@ -117,13 +117,19 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2)
                 }
             }
             if (!ok) {
-                // a staged chunk never arrived: report it, let the copies in flight land, stop
+                // a staged chunk never arrived: report it, let the copies in flight land (with a
+                // longer bound), stop.  If one of those copies does not land either, the CTA
+                // cannot know when it will write its shared memory: that is reported as
+                // WDAD_ERR_CUDA, a state the host must not reuse (destroy the batch, reset the
+                // context).
                 if (threadIdx.x == 0) {
-                    atomicExch(&status[0], (int)WDAD_ERR_TIMEOUT);
+                    int drained = 1;
                     for (int r = q + 1; r < min(nchunk, q + kStages); ++r) {
                         const uint32_t g = gchunk + (uint32_t)r;
-                        tc::mbar_wait_bounded(&s_full[g % kStages], (g / kStages) & 1u, kStageWait);
+                        drained &= tc::mbar_wait_bounded(&s_full[g % kStages], (g / kStages) & 1u, 16u * kStageWait)
+                                       ? 1 : 0;
                     }
+                    atomicExch(&status[0], drained ? (int)WDAD_ERR_TIMEOUT : (int)WDAD_ERR_CUDA);
                 }
                 __syncthreads();
                 return;

@@ -858,7 +858,11 @@ wdad_status wdad_batch_status(wdad_batch b, int* tile_h_out) {
     int dev_status = 0;
     if (e == cudaSuccess) e = cudaMemcpy(&dev_status, b->d_counters + 1 + b->n, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(b->h, e, "batch status");
-    if (dev_status != 0) return fail(b->h, (wdad_status)dev_status, "a batched tile gave up waiting for its DWT");
+    if (dev_status == (int)WDAD_ERR_CUDA)
+        return fail(b->h, WDAD_ERR_CUDA,
+                    "a staged DWT chunk and the copies behind it never landed: unrecoverable, destroy the batch "
+                    "and reset the device context");
+    if (dev_status != 0) return fail(b->h, (wdad_status)dev_status, "a batched item gave up waiting (DWT chunk or tile)");
     return WDAD_OK;
 }
 

@@ -11,34 +11,27 @@
 // size that lives in the module for as long as the library is loaded: the K x L DWT
 // matrix and the H x W x K approximation matrix.  The caller passes the cube and the
 // score and flag buffers, as for wdad_detect_all.
-#include <mutex>
-
 #include "internal.h"
 
 namespace {
 
 constexpr size_t kMatFloats = 8 * 1024;             // DWT matrix: K <= 8 rows, L <= 1024 columns
 constexpr size_t kApproxFloats = (size_t)1 << 22;   // approximation matrix: H * W * K <= 4,194,304
-constexpr int kMaxDevices = 64;
 
 // Scratch shared by every call on a device (16 MiB + 32 KiB); each call overwrites the
 // parts it reads, so nothing has to start at zero.
 static __device__ __align__(256) float g_noalloc_scratch[kMatFloats + kApproxFloats];
 
-std::mutex g_setup_mu;
-float* g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of the scratch array for the current device (host code may not use the
-// symbol itself as a pointer).  Looked up once per device, with that device current.
-cudaError_t scratch_ptr(int dev, float** out) {
-    std::lock_guard<std::mutex> lk(g_setup_mu);
-    if (!g_scratch_ptr[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = static_cast<float*>(p);
-    }
-    *out = g_scratch_ptr[dev];
+// Device address of the scratch array in the current context (host code may not use the
+// symbol itself as a pointer).  Looked up on every call, with the caller's device current:
+// the lookup is not a stream operation, and a context that was torn down and made again
+// (cudaDeviceReset) reloads the module, which can place the array elsewhere, so an address
+// cached from an earlier context could point at memory the array no longer occupies.
+cudaError_t scratch_ptr(float** out) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    *out = static_cast<float*>(p);
     return cudaSuccess;
 }
 
@@ -70,9 +63,9 @@ extern "C" wdad_status wdad_detect_all_noalloc(const float* cube, int H, int W, 
     if (wdad::detect_small_smem(K, p->inner, p->outer, 1) > 227 * 1024) return WDAD_ERR_UNSUPPORTED;
 
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return WDAD_ERR_CUDA;
+    if (cudaGetDevice(&dev) != cudaSuccess) return WDAD_ERR_CUDA;
     float* base = nullptr;
-    if (scratch_ptr(dev, &base) != cudaSuccess) return WDAD_ERR_CUDA;
+    if (scratch_ptr(&base) != cudaSuccess) return WDAD_ERR_CUDA;
     int num_sms = 1;
     if (cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return WDAD_ERR_CUDA;
 

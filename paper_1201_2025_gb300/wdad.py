@@ -151,6 +151,17 @@ def _cube(t):
     return t.contiguous()
 
 
+def _check_out(t, shape, dtype, device, name="out"):
+    """A caller-supplied buffer must be a contiguous CUDA tensor of exactly this shape and
+    dtype on the cube's device: the kernels write shape's element count through its pointer."""
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.device == device and t.dtype == dtype
+            and tuple(t.shape) == tuple(shape) and t.is_contiguous()):
+        got = (tuple(t.shape), t.dtype, str(t.device), t.is_contiguous()) if isinstance(t, torch.Tensor) else type(t)
+        raise ValueError(f"{name} must be a contiguous {dtype} tensor of shape {tuple(shape)} on {device}; got {got}")
+    return t
+
+
 def _params(params, over):
     if params is None:
         return wdad_default_params(**over)
@@ -184,6 +195,7 @@ def wdad_dwt_approx(cube, params: wdad_params | None = None, out=None, **over):
         raise WdadError(WDAD_ERR_ARG, "bad L/taps/level")
     if out is None:
         out = torch.empty((H, W, K), device=cube.device, dtype=torch.float32)
+    _check_out(out, (H, W, K), torch.float32, cube.device)
     h = handle(cube.device.index or 0)
     k = ctypes.c_int(0)
     _check(lib().wdad_dwt_approx(h, cube.data_ptr(), H, W, L, ctypes.byref(p), out.data_ptr(), ctypes.byref(k),
@@ -200,6 +212,9 @@ def wdad_detect(cube, detector: int, reduce: bool = True, params: wdad_params | 
     H, W, L = cube.shape
     if out is None:
         out = torch.empty((H, W), device=cube.device, dtype=torch.float32)
+    _check_out(out, (H, W), torch.float32, cube.device)
+    if flags is not None:
+        _check_out(flags, (H, W), torch.uint8, cube.device, "flags")
     h = handle(cube.device.index or 0)
     _check(lib().wdad_detect(h, cube.data_ptr(), H, W, L, int(detector), int(bool(reduce)), ctypes.byref(p),
                              out.data_ptr(), flags.data_ptr() if flags is not None else None, _stream(cube)), h)
@@ -216,6 +231,9 @@ def wdad_detect_windows(cube, params, reduce: bool = True, out=None, flags=None)
     arr = (wdad_params * n)(*params)
     if out is None:
         out = torch.empty((n, 3, H, W), device=cube.device, dtype=torch.float32)
+    _check_out(out, (n, 3, H, W), torch.float32, cube.device)
+    if flags is not None:
+        _check_out(flags, (n, H, W), torch.uint8, cube.device, "flags")
     h = handle(cube.device.index or 0)
     _check(lib().wdad_detect_windows(h, cube.data_ptr(), H, W, L, int(bool(reduce)), n, arr, out.data_ptr(),
                                      flags.data_ptr() if flags is not None else None, _stream(cube)), h)
@@ -230,6 +248,7 @@ def wdad_global_rx(cube, reduce: bool = True, params: wdad_params | None = None,
     H, W, L = cube.shape
     if out is None:
         out = torch.empty((H, W), device=cube.device, dtype=torch.float32)
+    _check_out(out, (H, W), torch.float32, cube.device)
     h = handle(cube.device.index or 0)
     _check(lib().wdad_global_rx(h, cube.data_ptr(), H, W, L, int(bool(reduce)), ctypes.byref(p), out.data_ptr(),
                                 _stream(cube)), h)
@@ -244,6 +263,9 @@ def wdad_detect_all(cube, reduce: bool = True, params: wdad_params | None = None
     H, W, L = cube.shape
     if out is None:
         out = torch.empty((3, H, W), device=cube.device, dtype=torch.float32)
+    _check_out(out, (3, H, W), torch.float32, cube.device)
+    if flags is not None:
+        _check_out(flags, (H, W), torch.uint8, cube.device, "flags")
     h = handle(cube.device.index or 0)
     _check(lib().wdad_detect_all(h, cube.data_ptr(), H, W, L, int(bool(reduce)), ctypes.byref(p), out.data_ptr(),
                                  flags.data_ptr() if flags is not None else None, _stream(cube)), h)
@@ -265,6 +287,9 @@ def wdad_detect_all_host(cube, reduce: bool = True, params=None, out=None, devic
     H, W, L = cube.shape
     if out is None:
         out = torch.empty((n, 3, H, W), dtype=torch.float32).pin_memory()
+    if not (isinstance(out, torch.Tensor) and not out.is_cuda and out.dtype == torch.float32
+            and tuple(out.shape) == (n, 3, H, W) and out.is_contiguous()):
+        raise ValueError(f"out must be a contiguous CPU float32 tensor of shape {(n, 3, H, W)}")
     h = handle(device)
     st = ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
     _check(lib().wdad_detect_all_host(h, cube.data_ptr(), H, W, L, int(bool(reduce)), n, arr, out.data_ptr(), st), h)
@@ -281,6 +306,9 @@ def wdad_detect_all_noalloc(cube, params: wdad_params | None = None, out=None, f
     H, W, L = cube.shape
     if out is None:
         out = torch.empty((3, H, W), device=cube.device, dtype=torch.float32)
+    _check_out(out, (3, H, W), torch.float32, cube.device)
+    if flags is not None:
+        _check_out(flags, (H, W), torch.uint8, cube.device, "flags")
     with torch.cuda.device(cube.device):
         st = lib().wdad_detect_all_noalloc(cube.data_ptr(), H, W, L, ctypes.byref(p), out.data_ptr(),
                                            flags.data_ptr() if flags is not None else None, _stream(cube))
@@ -321,6 +349,10 @@ def _jobs(jobs):
         cube = _cube(j["cube"])
         H, W, L = cube.shape
         p = j.get("params") or wdad_default_params(**j.get("over", {}))
+        import torch
+        _check_out(j["scores"], (3, H, W) if int(j["detector"]) == 3 else (H, W), torch.float32, cube.device, "scores")
+        if j.get("flags") is not None:
+            _check_out(j["flags"], (H, W), torch.uint8, cube.device, "flags")
         arr[i] = wdad_job(cube.data_ptr(), H, W, L, int(j["detector"]), p, j["scores"].data_ptr(),
                           j["flags"].data_ptr() if j.get("flags") is not None else None)
     return arr
@@ -430,6 +462,7 @@ class wdad_cnn:
         B, H, W, _ = x.shape
         if out is None:
             out = torch.empty((B, H, W), device=x.device, dtype=torch.float32)
+        _check_out(out, (B, H, W), torch.float32, x.device)
         _check(lib().wdad_cnn_forward(self._c, x.data_ptr(), B, H, W, out.data_ptr(), self._stream()), self._h)
         return out
 
@@ -521,6 +554,8 @@ def wdad_adaptive_threshold(score, z_alpha: float, mask=None, want_mask: bool = 
     n = score.numel()
     if want_mask and mask is None:
         mask = torch.empty(score.shape, device=score.device, dtype=torch.uint8)
+    if mask is not None:
+        _check_out(mask, score.shape, torch.uint8, score.device, "mask")
     stats = np.zeros(4, dtype=np.float64)
     h = handle(score.device.index or 0)
     _check(lib().wdad_adaptive_threshold(h, score.data_ptr() if n else None, n, float(z_alpha),

@@ -114,7 +114,8 @@ def _check_scene(wd, cube, win, loading=1e-3, dwest_mode=0, label="", taps=8):
     ok = dwest_ok_mask(aux)
     e = dwest_relerr(got[2], want, aux)
     # (other filters leave more pixels with an eigenvalue near the selection cut-off)
-    assert ok.mean() > (0.9 if taps == 8 else 0.5), f"{label}: only {ok.mean():.3f} of DWEST pixels are well determined"
+    # db4: 2.4-3.2% of the pixels are undetermined on the scenes of these tests
+    assert ok.mean() >= (0.95 if taps == 8 else 0.5), f"{label}: only {ok.mean():.3f} of DWEST pixels are well determined"
     assert e[ok].max() <= TOL_SCORE, f"{label} DWEST win {win}: max rel err {e[ok].max():.3g} ({(~ok).sum()} excluded)"
     return got
 
@@ -240,7 +241,7 @@ def test_reduced_detectors_512_sampled(wd, scene512, win):
         assert e.max() <= TOL_SCORE, (det, e.max())
     want, aux = oracle.detect(a, 2, win[0], win[1], pixels=pix, want_aux=True)
     ok = dwest_ok_mask(aux)
-    assert ok.mean() > 0.9
+    assert ok.mean() >= 0.95  # 2.9-3.4% undetermined on these samples
     assert dwest_relerr(got[2].ravel()[pix], want, aux)[ok].max() <= TOL_SCORE
 
 

@@ -4,17 +4,23 @@ This entry point serves callers that cannot call cudaMalloc (fixed memory budget
 framework-owned device pools, latency-critical code).  It keeps its scratch in a fixed
 array inside the library that every call shares.  The test calls it twice in a row on
 different scenes, so stale contents from the first call would show up in the second.
-It compares each result with the handle-based entry point under the score tolerance
-of the other tests.  The file runs last so that a stop at the first failure has already
-run everything else.
+Both entry points run the same kernels with the same tile plan, so scores and flags must be
+bit-identical.  A fresh process checks that repeated calls leave the device's free memory
+unchanged.  The file runs last so that a stop at the first failure has already run
+everything else.
 """
+import os
+import subprocess
+import sys
+import textwrap
+
 import numpy as np
 import pytest
 
-from parity import TOL_SCORE
-
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 @pytest.fixture(scope="module")
@@ -24,12 +30,14 @@ def wd():
     return wdad
 
 
-def _close(a, b):
-    a = a.cpu().numpy().astype(np.float64)
-    b = b.cpu().numpy().astype(np.float64)
-    floor = 1e-6 * np.median(np.abs(b))
-    err = np.abs(a - b) / np.maximum(np.abs(b), floor)
-    return np.nanmax(err) <= TOL_SCORE and np.array_equal(np.isnan(a), np.isnan(b))
+def _both(wd, x, **over):
+    H, W, _ = x.shape
+    f1 = torch.full((H, W), 255, dtype=torch.uint8, device="cuda")
+    f2 = torch.full((H, W), 254, dtype=torch.uint8, device="cuda")
+    got = wd.wdad_detect_all_noalloc(x, flags=f1, **over)
+    want = wd.wdad_detect_all(x, reduce=True, flags=f2, **over)
+    torch.cuda.synchronize()
+    return got, want, f1, f2
 
 
 def test_noalloc_matches_detect_all_on_two_calls_in_a_row(wd):
@@ -38,11 +46,9 @@ def test_noalloc_matches_detect_all_on_two_calls_in_a_row(wd):
     second = synth.make_scene(37, 53, 189, seed=12, n_anom=4, margin=4)
     for sc, win in ((first, (3, 11)), (second, (5, 13))):
         x = torch.from_numpy(sc.cube).cuda()
-        got = wd.wdad_detect_all_noalloc(x, inner=win[0], outer=win[1])
-        torch.cuda.synchronize()
-        want = wd.wdad_detect_all(x, reduce=True, inner=win[0], outer=win[1])
-        torch.cuda.synchronize()
-        assert _close(got, want)
+        got, want, f1, f2 = _both(wd, x, inner=win[0], outer=win[1])
+        assert torch.equal(got, want)
+        assert torch.equal(f1, f2)
 
 
 @pytest.mark.parametrize("taps", [4, 12])
@@ -50,11 +56,8 @@ def test_noalloc_other_filters(wd, taps):
     from paper_1201_2025_gb300 import synth
     sc = synth.make_scene(40, 50, 224, seed=13, n_anom=4, margin=4)
     x = torch.from_numpy(sc.cube).cuda()
-    got = wd.wdad_detect_all_noalloc(x, inner=3, outer=9, wavelet_taps=taps)
-    torch.cuda.synchronize()
-    want = wd.wdad_detect_all(x, reduce=True, inner=3, outer=9, wavelet_taps=taps)
-    torch.cuda.synchronize()
-    assert _close(got, want)
+    got, want, f1, f2 = _both(wd, x, inner=3, outer=9, wavelet_taps=taps)
+    assert torch.equal(got, want) and torch.equal(f1, f2)
     with pytest.raises(wd.WdadError) as ei:
         wd.wdad_detect_all_noalloc(x, wavelet_taps=taps + 1)
     assert ei.value.status == wd.WDAD_ERR_ARG
@@ -65,3 +68,45 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(wd):
     with pytest.raises(wd.WdadError) as ei:
         wd.wdad_detect_all_noalloc(x)
     assert ei.value.status == wd.WDAD_ERR_ARG
+
+
+def test_noalloc_window_beyond_shared_memory_is_unsupported(wd):
+    # a 63 x 63 window's tile does not fit shared memory: both entry points refuse it
+    x = torch.ones((70, 70, 16), device="cuda")
+    for fn in (lambda: wd.wdad_detect_all_noalloc(x, inner=61, outer=63),
+               lambda: wd.wdad_detect_all(x, reduce=True, inner=61, outer=63)):
+        with pytest.raises(wd.WdadError) as ei:
+            fn()
+        assert ei.value.status == wd.WDAD_ERR_UNSUPPORTED
+
+
+def test_noalloc_allocates_no_device_memory():
+    # a fresh process: the first call may load the library's module (and with it the fixed
+    # array); later calls of other sizes must leave the device's free memory and torch's
+    # allocator untouched, and no library handle (which owns workspace) may be created
+    code = textwrap.dedent(f"""
+        import sys, numpy as np, torch
+        sys.path.insert(0, {ROOT!r})
+        from paper_1201_2025_gb300 import synth, wdad
+        bufs = []
+        for H, W in ((60, 100), (200, 250), (128, 512)):
+            sc = synth.make_scene(H, W, 224, seed=H, n_anom=4, margin=4)
+            x = torch.from_numpy(sc.cube).cuda()
+            bufs.append((x, torch.empty((3, H, W), device="cuda"), torch.empty((H, W), dtype=torch.uint8, device="cuda")))
+        x, out, fl = bufs[0]
+        wdad.wdad_detect_all_noalloc(x, inner=3, outer=11, out=out, flags=fl)
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        alloc0 = torch.cuda.memory_allocated()
+        for x, out, fl in bufs[1:] + bufs[:1]:
+            wdad.wdad_detect_all_noalloc(x, inner=3, outer=11, out=out, flags=fl)
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        assert free1 == free0, (free0, free1)
+        assert torch.cuda.memory_allocated() == alloc0
+        assert not wdad._handles, wdad._handles
+        assert bool(torch.isfinite(bufs[1][1]).all())
+        print("no-alloc ok")
+    """)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0 and "no-alloc ok" in r.stdout, r.stdout + r.stderr
