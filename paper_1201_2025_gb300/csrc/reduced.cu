@@ -1,5 +1,8 @@
 // Launchers and kernels of the reduced-band detectors (device code in reduced_dev.cuh).
 #include <algorithm>
+#include <mutex>
+#include <set>
+#include <utility>
 
 #include "reduced_dev.cuh"
 
@@ -48,53 +51,16 @@ __global__ void __launch_bounds__(512) detect_multi_kernel(MultiArgs m) {
 // ---------------------------------------------------------------- census kernel
 __global__ void __launch_bounds__(512) census_kernel(int H, int W, int inner, int outer, int border, int th,
                                                      long long* __restrict__ out) {
-    using P = CensusPayload;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const TileGeom g(H, W, inner, outer, th, blockIdx.x, blockIdx.y);
-    long long* xs = reinterpret_cast<long long*>(smem_raw);
-    long long* hso = xs + (size_t)g.HR * g.XP;
-    long long* hsi = hso + (size_t)P::NC * g.HR * HP;
-    load_halo_census(g, xs);
-    __syncthreads();
-    auto chan = [&](int r, int col, long long (&ch)[3]) {
-        const long long q = xs[(size_t)r * g.XP + col];
-        ch[0] = 1; ch[1] = q; ch[2] = q * q;
-    };
-    horizontal_sums<P>(g, chan, hso, hsi);
-    __syncthreads();
-    vertical_sums_inplace<P>(g, hso, hsi);
-    __syncthreads();
-    for (int pix = threadIdx.x; pix < th * TW; pix += blockDim.x) {
-        const int i = pix / TW, j = pix - i * TW;
-        const int y = g.ty0 + i, xq = g.tx0 + j;
-        if (y >= H || xq >= W) continue;
-        long long* o = out + ((size_t)y * W + xq) * 6;
-        if (border == 1 && (y - g.ro < 0 || y + g.ro >= H || xq - g.ro < 0 || xq + g.ro >= W)) {
-            for (int t = 0; t < 6; ++t) o[t] = -1;
-            continue;
-        }
-        long long So[3], Si[3];
-        for (int q = 0; q < 3; ++q) {
-            So[q] = hso[q * g.HR * HP + i * HP + j];
-            Si[q] = hsi[q * g.nin * HP + i * HP + j];
-        }
-        o[0] = So[0] - Si[0]; o[1] = So[1] - Si[1]; o[2] = So[2] - Si[2];
-        o[3] = Si[0]; o[4] = Si[1]; o[5] = Si[2];
-    }
+    census_tile(H, W, inner, outer, border, th, blockIdx.x, blockIdx.y, out, smem_raw);
 }
 
 // ---------------------------------------------------------------- launchers
-static size_t smem_bytes(int words_per_px, int nc, int tsize, int inner, int outer, int th) {
-    const int ro = outer / 2, ri = inner / 2;
-    const size_t HR = th + 2 * ro, XP = halo_pitch(TW + 2 * ro);
-    return HR * XP * words_per_px * 4 + (size_t)nc * HR * HP * tsize + (size_t)nc * (th + 2 * ri) * HP * tsize;
-}
-
 static int spec_nc(int D) { return D + D * (D + 1) / 2; }
 static int spec_dp(int D) { return D <= 4 ? 4 : 8; }
 
 size_t detect_small_smem(int D, int inner, int outer, int tile_h) {
-    return smem_bytes(spec_dp(D), spec_nc(D), 4, inner, outer, tile_h) + sizeof(float) * 8;  // + tile reference
+    return tile_smem_bytes(spec_dp(D), spec_nc(D), 4, inner, outer, tile_h);
 }
 
 // Tallest tile (<= want, >= 8 rows) that lets two CTAs share an SM; else the tallest that
@@ -112,11 +78,37 @@ static int pick_th(int D, int inner, int outer, int want) {
     return 0;
 }
 
+// The dynamic shared memory limit of a kernel is raised once per kernel and device to the
+// largest size any plan uses, so that launches from several host threads never lower it
+// between another thread's set and launch.
+template <class K>
+static cudaError_t set_max_smem(K* kernel) {
+    static std::mutex mu;
+    static std::set<std::pair<const void*, int>> done;  // (kernel, device) pairs already raised
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    const auto key = std::make_pair(reinterpret_cast<const void*>(kernel), dev);
+    if (!done.count(key)) {
+        // the opt-in limit covers static and dynamic shared memory together
+        int optin = 0;
+        cudaFuncAttributes fa{};
+        e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
+        if (e != cudaSuccess) return e;
+        const int dyn = std::min<int>(kMaxSmem, optin - (int)fa.sharedSizeBytes);
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        if (e != cudaSuccess) return e;
+        done.insert(key);
+    }
+    return cudaSuccess;
+}
+
 template <int D>
 static cudaError_t launch_d(const DetectArgs& a, int th, cudaStream_t s) {
     const size_t smem = detect_small_smem(D, a.inner, a.outer, th);
-    cudaError_t e = cudaFuncSetAttribute(detect_small_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = set_max_smem(detect_small_kernel<D>);
     if (e != cudaSuccess) return e;
     dim3 grid((a.W + TW - 1) / TW, (a.H + th - 1) / th);
     const int threads = std::min(512, std::max(256, th * 32));  // one thread per output pixel when th >= 8
@@ -161,8 +153,7 @@ cudaError_t launch_detect_small(const DetectArgs& a, int tile_h, cudaStream_t s)
 
 template <int D>
 static cudaError_t launch_multi_d(const MultiArgs& m, size_t smem, int blocks, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(detect_multi_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = set_max_smem(detect_multi_kernel<D>);
     if (e != cudaSuccess) return e;
     detect_multi_kernel<D><<<blocks, 512, smem, s>>>(m);
     return cudaGetLastError();
@@ -210,10 +201,11 @@ cudaError_t launch_detect_small_multi(const DetectArgs* a, int n, cudaStream_t s
 cudaError_t launch_window_census(int H, int W, int inner, int outer, int border, int64_t* out, cudaStream_t s) {
     if ((int64_t)H * W == 0) return cudaSuccess;
     int th = 16;
-    while (th > 1 && smem_bytes(CensusPayload::WORDS, 3, 8, inner, outer, th) > (size_t)kMaxSmem) th >>= 1;
-    const size_t smem = smem_bytes(CensusPayload::WORDS, 3, 8, inner, outer, th);
+    while (th > 1 && tile_smem_bytes(CensusPayload::WORDS, CensusPayload::NC, 8, inner, outer, th) > (size_t)kMaxSmem)
+        th >>= 1;
+    const size_t smem = tile_smem_bytes(CensusPayload::WORDS, CensusPayload::NC, 8, inner, outer, th);
     if (smem > (size_t)kMaxSmem) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(census_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = set_max_smem(census_kernel);
     if (e != cudaSuccess) return e;
     dim3 grid((W + TW - 1) / TW, (H + th - 1) / th);
     census_kernel<<<grid, th >= 16 ? 512 : 256, smem, s>>>(H, W, inner, outer, border, th,

@@ -1,28 +1,36 @@
 // A2-A5 on few bands (dim D <= 8, the DWT approximation matrix of Sec. 4):
 // dual-window statistics, regularised solve and eigen-decomposition, fused in
-// one kernel per output tile.
+// one kernel per output tile of 32 columns x th rows.
 //
-//  stage 0  the tile plus a halo of outer/2 pixels is loaded into shared memory,
-//           every index reflected at the image border (reflect-101);
-//  stage 1  (float payload) a tile reference spectrum c = mean of the loaded
-//           pixels is subtracted, so the second moments below are sums of
-//           (x - c)(x - c)^T with little cancellation;
-//  stage 2  horizontal box sums over the outer and the inner window width of the
-//           D first-order and D(D+1)/2 second-order channels: one thread per halo
-//           row and 8-column segment, a direct sum for the first column and a
-//           sliding update (add the entering, subtract the leaving column) after;
-//  stage 3  vertical box sums of those, one thread per (channel, column) sliding
-//           down the tile rows, written in place over the horizontal sums: sums
-//           over the outer square and over the inner square; the background
-//           annulus is outer minus inner (Sec. 2.2 dual window);
-//  stage 4  per pixel: mu_o, C_o (1/N), mu_i, C_i (1/n_i); LRX (Eq. 1) and DWRX
+//  stage 0  warp 0 forms a tile reference spectrum c (the mean of the middle halo
+//           row, read from global memory in a fixed order) while every warp
+//           fetches its share of the tile plus a halo of outer/2 pixels; after one
+//           barrier the pixels are stored shifted, x - c, so that the second
+//           moments below are sums of (x - c)(x - c)^T with little cancellation.
+//           Every index is reflected at the image border (reflect-101).
+//  stage 1  vertical box sums, one work item per (channel group, halo column,
+//           outer or inner height): the D first-order and D(D+1)/2 second-order
+//           channels of each pixel are formed where they are needed (two groups of
+//           channels, so that each pixel is read from shared memory twice), and the
+//           sums over the outer and the inner window height slide down the th
+//           output rows (a direct sum for the first row, then add the entering
+//           and subtract the leaving row).
+//  stage 2  horizontal box sums of those, in place, one work item per (channel,
+//           output row, outer or inner): segments of 8 output columns, each a
+//           direct sum and 7 sliding updates; for radii up to 10 a segment's
+//           inputs are held in registers.  Afterwards the planes hold, per
+//           output pixel, the sums over the outer square and over the inner
+//           square; the background annulus is outer minus inner (Sec. 2.2).
+//  stage 3  per pixel: mu_o, C_o (1/N), mu_i, C_i (1/n_i); LRX (Eq. 1) and DWRX
 //           (Eq. 5) through a Cholesky factor of C_o + delta I, delta =
 //           loading * trace(C_o) / D; DWEST (Eq. 2-4) through a cyclic Jacobi
 //           eigen-decomposition of C_i - C_o.
 //
-// Stages 0, 2 and 3 are templated on the payload so that the window census
-// (integer pixel indices instead of spectra) runs exactly the indexing code of
-// the detectors and can be checked bit for bit.
+// Every sliding sum restarts at least every 16 rows and every 8 columns, which bounds
+// the FP32 rounding it accumulates.  Stages 0-2 are templated on the payload, so the
+// window census (integer pixel indices instead of spectra) runs exactly the indexing
+// and summation code of the detectors and can be checked bit for bit.  Results do not
+// depend on the block size (a multiple of 32, at most 512): every sum has a fixed order.
 #pragma once
 #include <float.h>
 
@@ -30,20 +38,25 @@
 
 namespace wdad {
 
-
-constexpr int TW = 32;          // tile width = one warp across
+constexpr int TW = 32;          // tile width in output columns
 constexpr int kMaxSmem = 227 * 1024;
-
-constexpr int SEG = 8;          // output columns per stage-2 thread
-constexpr int HP = TW + 1;      // row pitch of the sum planes (words): conflict-free column access
+constexpr int kSeg = 8;         // horizontal outputs per sliding segment
+constexpr int kRegRadius = 10;  // horizontal radii whose segments are held in registers
 
 __host__ __device__ __forceinline__ int halo_pitch(int WR) { return WR | 1; }  // odd pixel pitch
+// Row pitch (elements) of a sum plane: at least n and 4 mod 8, so that 16-byte loads of
+// eight consecutive rows fall on eight different bank groups.
+__host__ __device__ __forceinline__ int plane_pitch(int n) {
+    const int p = (n + 3) & ~3;
+    return (p & 7) ? p : p + 4;
+}
 
 struct TileGeom {
     int H, W, ro, ri, th;        // image, radii, tile height
     int ty0, tx0;                // tile origin
-    int HR, WR, XP;              // halo region rows / cols, halo row pitch in pixels
-    int nin;                     // halo rows that carry inner sums
+    int HR, WR, XP;              // halo rows / cols, halo row pitch in pixels
+    int WI;                      // columns that carry inner sums (TW + 2 ri)
+    int VP, VPI;                 // row pitch of the outer / inner sum planes
     __device__ TileGeom(int H_, int W_, int inner, int outer, int th_, int tile_x, int tile_y)
         : H(H_), W(W_), ro(outer / 2), ri(inner / 2), th(th_) {
         ty0 = tile_y * th;
@@ -51,9 +64,22 @@ struct TileGeom {
         HR = th + 2 * ro;
         WR = TW + 2 * ro;
         XP = halo_pitch(WR);
-        nin = th + 2 * ri;
+        WI = TW + 2 * ri;
+        VP = plane_pitch(WR);
+        VPI = plane_pitch(WI);
     }
 };
+
+// Shared memory of one tile: the halo (words_per_px 4-byte words per pixel, rounded up
+// to 16 bytes), the outer and inner sum planes (nc channels of tsize bytes), the tile
+// reference (32 bytes).
+__host__ __device__ __forceinline__ size_t tile_smem_bytes(int words_per_px, int nc, int tsize, int inner, int outer,
+                                                           int th) {
+    const int ro = outer / 2, ri = inner / 2;
+    const size_t HR = th + 2 * ro, XP = halo_pitch(TW + 2 * ro);
+    const size_t xs = (HR * XP * words_per_px * 4 + 15) & ~(size_t)15;
+    return xs + (size_t)nc * th * (plane_pitch(TW + 2 * ro) + plane_pitch(TW + 2 * ri)) * tsize + 32;
+}
 
 // ---------------------------------------------------------------- payloads
 template <int D>
@@ -72,172 +98,337 @@ struct SpecPayload {                          // D-band spectra, float
 #pragma unroll
             for (int b = a; b < D; ++b) ch[q++] = v[a] * v[b];
     }
+    static constexpr int PX = DP;                // elements of T per halo pixel
+    // vertical-pass channel groups [0, QSPLIT) and [QSPLIT, NC): the first-order channels
+    // with the products x_0 x_b, then the other products (4 + 4 and 6 channels at D = 4)
+    static constexpr int QSPLIT = 2 * D < NC ? 2 * D : NC;
+    // the channels of the halo pixel at p
+    static __device__ __forceinline__ void pixel_channels(const float* p, float (&ch)[NC]) {
+        float v[D];
+        if constexpr (D == 4) {
+            const float4 q = *reinterpret_cast<const float4*>(p);
+            v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+        } else {
+#pragma unroll
+            for (int k = 0; k < D; ++k) v[k] = p[k];
+        }
+        channels(v, ch);
+    }
 };
 
 struct CensusPayload {                        // linear pixel index, int64
     using T = long long;
     static constexpr int NC = 3;                 // 1, q, q^2
     static constexpr int WORDS = 2;
+    static constexpr int PX = 1;
+    static constexpr int QSPLIT = 2;             // groups (1, q) and (q^2)
+    static __device__ __forceinline__ void pixel_channels(const long long* p, long long (&ch)[NC]) {
+        const long long q = *p;
+        ch[0] = 1; ch[1] = q; ch[2] = q * q;
+    }
 };
 
-// ---------------------------------------------------------------- stage 0: reflected halo load
+// ---------------------------------------------------------------- stage 0: reflected, shifted halo
+// Tile reference: the mean of halo row HR / 2, summed lane-strided then by a fixed
+// shuffle tree (one warp; the same value whatever the block size).
 template <int D>
-__device__ __forceinline__ void load_halo_spec(const TileGeom& g, const float* __restrict__ x, float* xs) {
-    using P = SpecPayload<D>;
-    const int n = g.HR * g.WR;
-    if constexpr (D == 4) {
-        // eight 16-byte loads in flight per thread before any is stored
-        constexpr int B = 8;
-        for (int base = threadIdx.x; base < n; base += B * blockDim.x) {
-            float4 v[B];
-            int dsti[B];
+__device__ __forceinline__ void tile_reference(const TileGeom& g, const float* __restrict__ x, float* cref, int lane) {
+    float acc[D];
 #pragma unroll
-            for (int u = 0; u < B; ++u) {
-                const int idx = base + u * blockDim.x;
-                dsti[u] = -1;
-                v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (idx < n) {
-                    const int r = idx / g.WR, c = idx - r * g.WR;
-                    const int gy = reflect101(g.ty0 - g.ro + r, g.H);
-                    const int gx = reflect101(g.tx0 - g.ro + c, g.W);
-                    v[u] = __ldg(reinterpret_cast<const float4*>(x + ((size_t)gy * g.W + gx) * 4));
-                    dsti[u] = r * g.XP + c;
-                }
-            }
+    for (int k = 0; k < D; ++k) acc[k] = 0.f;
+    const int gy = reflect101(g.ty0 - g.ro + g.HR / 2, g.H);
+    for (int c = lane; c < g.WR; c += 32) {
+        const int gx = reflect101(g.tx0 - g.ro + c, g.W);
+        const float* px = x + ((size_t)gy * g.W + gx) * D;
+        if constexpr (D == 4) {
+            const float4 v = __ldg(reinterpret_cast<const float4*>(px));
+            acc[0] += v.x; acc[1] += v.y; acc[2] += v.z; acc[3] += v.w;
+        } else {
 #pragma unroll
-            for (int u = 0; u < B; ++u)
-                if (dsti[u] >= 0) {
-                    *reinterpret_cast<float4*>(xs + (size_t)dsti[u] * P::DP) = v[u];
-                }
+            for (int k = 0; k < D; ++k) acc[k] += __ldg(px + k);
         }
-    } else {
-        for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-            const int r = idx / g.WR, c = idx - r * g.WR;
-            const int gy = reflect101(g.ty0 - g.ro + r, g.H);
-            const int gx = reflect101(g.tx0 - g.ro + c, g.W);
-            const float* src = x + ((size_t)gy * g.W + gx) * D;
-            float* dst = xs + ((size_t)r * g.XP + c) * P::DP;
+    }
 #pragma unroll
-            for (int k = 0; k < D; ++k) dst[k] = __ldg(src + k);
+    for (int k = 0; k < D; ++k) {
+        float t = acc[k];
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) cref[k] = t / (float)g.WR;
+    }
+}
+
+template <int D>
+__device__ __forceinline__ void fetch_pixel(const float* __restrict__ x, int W, int gy, int gx, float (&v)[D]) {
+    const float* px = x + ((size_t)gy * W + gx) * D;
+    if constexpr (D == 4) {
+        const float4 t = __ldg(reinterpret_cast<const float4*>(px));
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    } else {
+#pragma unroll
+        for (int k = 0; k < D; ++k) v[k] = __ldg(px + k);
+    }
+}
+
+template <int D>
+__device__ __forceinline__ void store_shifted(float* dst, const float (&v)[D], const float (&c)[D]) {
+    if constexpr (D == 4) {
+        *reinterpret_cast<float4*>(dst) = make_float4(v[0] - c[0], v[1] - c[1], v[2] - c[2], v[3] - c[3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < D; ++k) dst[k] = v[k] - c[k];
+    }
+}
+
+// Warp w takes halo rows w, w + nw, ...; lanes take columns.  The first 64 columns of
+// every warp's first kHeld rows are fetched before the barrier that publishes the tile
+// reference, so their latency overlaps warp 0's reference sum; the rest after it.
+constexpr int kHeld = 3;
+template <int D>
+__device__ __forceinline__ void load_halo_spec(const TileGeom& g, const float* __restrict__ x, float* xs, float* cref) {
+    using P = SpecPayload<D>;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    float v[kHeld][2][D];
+    int dst[kHeld][2];
+#pragma unroll
+    for (int k = 0; k < kHeld; ++k) {
+        const int r = warp + k * nw;
+        const int gy = reflect101(g.ty0 - g.ro + (r < g.HR ? r : 0), g.H);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int c = lane + 32 * h;
+            dst[k][h] = -1;
+            if (r < g.HR && c < g.WR) {
+                fetch_pixel<D>(x, g.W, gy, reflect101(g.tx0 - g.ro + c, g.W), v[k][h]);
+                dst[k][h] = r * g.XP + c;
+            }
+        }
+    }
+    if (warp == 0) tile_reference<D>(g, x, cref, lane);
+    __syncthreads();
+    float c[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) c[k] = cref[k];
+#pragma unroll
+    for (int k = 0; k < kHeld; ++k)
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+            if (dst[k][h] >= 0) store_shifted<D>(xs + dst[k][h] * P::DP, v[k][h], c);
+    for (int r = warp; r < g.HR; r += nw) {
+        // columns the held rows did not cover (halos wider than 64 pixels), then the rest
+        const int c0 = (r < warp + kHeld * nw) ? 64 : 0;
+        if (c0 >= g.WR) continue;
+        const int gy = reflect101(g.ty0 - g.ro + r, g.H);
+        for (int cc = lane + c0; cc < g.WR; cc += 32) {
+            float t[D];
+            fetch_pixel<D>(x, g.W, gy, reflect101(g.tx0 - g.ro + cc, g.W), t);
+            store_shifted<D>(xs + (r * g.XP + cc) * P::DP, t, c);
         }
     }
 }
 
 __device__ __forceinline__ void load_halo_census(const TileGeom& g, long long* xs) {
-    const int n = g.HR * g.WR;
-    for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-        const int r = idx / g.WR, c = idx - r * g.WR;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int r = warp; r < g.HR; r += nw) {
         const int gy = reflect101(g.ty0 - g.ro + r, g.H);
-        const int gx = reflect101(g.tx0 - g.ro + c, g.W);
-        xs[(size_t)r * g.XP + c] = (long long)gy * g.W + gx;
+        for (int c = lane; c < g.WR; c += 32)
+            xs[(size_t)r * g.XP + c] = (long long)gy * g.W + reflect101(g.tx0 - g.ro + c, g.W);
     }
 }
 
-// ---------------------------------------------------------------- stage 2: horizontal sums
-// hso[ch][r][j] = sum over the outer width of channel ch at halo row r, output column j;
-// hsi[ch][r'][j] = the same over the inner width for the th + 2 ri halo rows the inner
-// squares use (r' = r - (ro - ri)).  Thread (r, seg) owns SEG consecutive output columns
-// of one halo row: a direct sum for the first, then sliding updates.
-template <class P, int Q0, int Q1, class ChanFn>
-__device__ __forceinline__ void horizontal_sums_part(const TileGeom& g, ChanFn chan, typename P::T* hso,
-                                                     typename P::T* hsi, int t) {
+// ---------------------------------------------------------------- stage 1: vertical sums
+// Item (channel group, halo column, outer or inner): channels [Q0, Q0 + NQ) of the halo
+// column at `in` (its row r0) summed over w rows starting at row r0 + i, for output rows
+// i = 0 .. th-1, into out + q * plane + i * pitch.  rs: elements of T per halo row.
+template <class P, int Q0, int NQ>
+__device__ __forceinline__ void vertical_item(const typename P::T* __restrict__ in, int rs,
+                                              typename P::T* __restrict__ out, int plane, int pitch, int th, int w) {
     using T = typename P::T;
     constexpr int NC = P::NC;
-    constexpr int NQ = Q1 - Q0;
-    const int wo = 2 * g.ro + 1, i0 = g.ro - g.ri, i1 = g.ro + g.ri;  // inner columns dc in [i0, i1]
-    const int rin0 = g.ro - g.ri;
-    const int plane_o = g.HR * HP, plane_i = g.nin * HP;
-    const int r = t % g.HR, j0 = (t / g.HR) * SEG;
-    const bool inner_row = (r >= rin0) && (r < rin0 + g.nin);
-    T so[NQ], si[NQ], ch[NC], c2[NC];
+    if (w == 1) {  // a window one row high: the channels themselves
+        for (int i = 0; i < th; ++i, in += rs, out += pitch) {
+            T ch[NC];
+            P::pixel_channels(in, ch);
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) { so[q] = T(0); si[q] = T(0); }
-    for (int dc = 0; dc < wo; ++dc) {
-        chan(r, j0 + dc, ch);
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) so[q] += ch[Q0 + q];
-        if (inner_row && dc >= i0 && dc <= i1) {
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) si[q] += ch[Q0 + q];
+            for (int j = 0; j < NQ; ++j) out[(Q0 + j) * plane] = ch[Q0 + j];
         }
+        return;
     }
-    T* po = hso + Q0 * plane_o + r * HP + j0;
-    T* pi = hsi + Q0 * plane_i + (r - rin0) * HP + j0;
+    T acc[NQ];
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) po[q * plane_o] = so[q];
-    if (inner_row) {
+    for (int j = 0; j < NQ; ++j) acc[j] = T(0);
+    const T* pe = in;
+    for (int k = 0; k < w; ++k, pe += rs) {
+        T ch[NC];
+        P::pixel_channels(pe, ch);
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) pi[q * plane_i] = si[q];
+        for (int j = 0; j < NQ; ++j) acc[j] += ch[Q0 + j];
     }
-    for (int jj = 1; jj < SEG; ++jj) {
-        const int j = j0 + jj;
-        chan(r, j + wo - 1, ch);  // entering column
-        chan(r, j - 1, c2);       // leaving column
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            so[q] += ch[Q0 + q] - c2[Q0 + q];  // one rounding at the running-sum magnitude
-            po[q * plane_o + jj] = so[q];
-        }
-        if (inner_row) {
-            chan(r, j + i1, ch);
-            chan(r, j - 1 + i0, c2);
+    for (int j = 0; j < NQ; ++j) out[(Q0 + j) * plane] = acc[j];
+    // pe: the row entering the window of output row i, in: the row leaving it
+#pragma unroll 2
+    for (int i = 1; i < th; ++i) {
+        out += pitch;
+        T e[NC], l[NC];
+        P::pixel_channels(pe, e);
+        P::pixel_channels(in, l);
+        pe += rs;
+        in += rs;
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                si[q] += ch[Q0 + q] - c2[Q0 + q];
-                pi[q * plane_i + jj] = si[q];
-            }
+        for (int j = 0; j < NQ; ++j) {
+            acc[j] += e[Q0 + j] - l[Q0 + j];  // one rounding at the running-sum magnitude
+            out[(Q0 + j) * plane] = acc[j];
         }
     }
 }
 
-// hso[ch][r][j] = sum over the outer width of channel ch at halo row r, output column j;
-// hsi[ch][r'][j] = the same over the inner width for the th + 2 ri halo rows the inner
-// squares use (r' = r - (ro - ri)).  Work item (r, seg, half) owns SEG consecutive output
-// columns of one halo row and one half of the channels: a direct sum for the first
-// column, then sliding updates.  The channel halves run in different warps.
-template <class P, class ChanFn>
-__device__ __forceinline__ void horizontal_sums(const TileGeom& g, ChanFn chan, typename P::T* hso,
-                                                typename P::T* hsi) {
-    constexpr int NC = P::NC;
-    constexpr int NH = NC / 2;
-    const int nwork = g.HR * (TW / SEG);
-    const int nwork_pad = (nwork + 31) & ~31;  // each half starts on a warp boundary
-    for (int t = threadIdx.x; t < 2 * nwork_pad; t += blockDim.x) {
-        const int half = t >= nwork_pad;
-        const int u = t - half * nwork_pad;
-        if (u >= nwork) continue;
-        if (half == 0) horizontal_sums_part<P, 0, NH>(g, chan, hso, hsi, u);
-        else horizontal_sums_part<P, NH, NC>(g, chan, hso, hsi, u);
-    }
+template <class P, int G>
+__device__ __forceinline__ void vertical_group(const typename P::T* in, int rs, typename P::T* out, int plane,
+                                               int pitch, int th, int w) {
+    constexpr int Q0 = G == 0 ? 0 : P::QSPLIT;
+    constexpr int NQ = G == 0 ? P::QSPLIT : P::NC - P::QSPLIT;
+    if constexpr (NQ > 0) vertical_item<P, Q0, NQ>(in, rs, out, plane, pitch, th, w);
 }
 
-// ---------------------------------------------------------------- stage 3: vertical sums, in place
-// Thread (ch, j) slides down the tile rows: afterwards hso[ch][i][j] holds the sum over
-// the outer square of output pixel (i, j) and hsi[ch][i][j] the sum over its inner square.
+// Items are laid out so that every warp holds one (group, outer or inner) pair: the outer
+// columns and the inner columns of a group each start on a warp boundary.  Two channel
+// groups: every item reloads its pixels from shared memory, so fewer groups move fewer
+// bytes, and two keep enough items in flight.
 template <class P>
-__device__ __forceinline__ void vertical_sums_inplace(const TileGeom& g, typename P::T* hso, typename P::T* hsi) {
-    using T = typename P::T;
-    constexpr int NC = P::NC;
-    const int wo = 2 * g.ro + 1, wi = 2 * g.ri + 1;
-    const int plane_o = g.HR * HP, plane_i = g.nin * HP;
-    for (int t = threadIdx.x; t < NC * TW; t += blockDim.x) {
-        const int j = t % TW, q = t / TW;
-        T* ho = hso + q * plane_o + j;
-        T* hi = hsi + q * plane_i + j;
-        T so = T(0), si = T(0);
-        for (int dr = 0; dr < wi; ++dr) { so += ho[dr * HP]; si += hi[dr * HP]; }
-        for (int dr = wi; dr < wo; ++dr) so += ho[dr * HP];
-        for (int i = 1; i < g.th; ++i) {
-            const T lo = ho[(i - 1) * HP], eo = ho[(i + wo - 1) * HP];
-            const T li = hi[(i - 1) * HP], ei = hi[(i + wi - 1) * HP];
-            ho[(i - 1) * HP] = so;
-            hi[(i - 1) * HP] = si;
-            so += eo - lo;  // one rounding at the running-sum magnitude
-            si += ei - li;
-        }
-        ho[(g.th - 1) * HP] = so;
-        hi[(g.th - 1) * HP] = si;
+__device__ __forceinline__ void vertical_sums(const TileGeom& g, const typename P::T* xs, typename P::T* Vo,
+                                              typename P::T* Vi) {
+    constexpr int NG = P::QSPLIT < P::NC ? 2 : 1;
+    const int no = (g.WR + 31) & ~31, ni = (g.WI + 31) & ~31;
+    const int per = no + ni;
+    const int rs = g.XP * P::PX;
+    for (int t = threadIdx.x; t < NG * per; t += blockDim.x) {
+        const int grp = t / per, rem = t - grp * per;
+        const bool outer = rem < no;
+        const int c = outer ? rem : rem - no;
+        if (c >= (outer ? g.WR : g.WI)) continue;
+        const typename P::T* in = outer ? xs + c * P::PX : xs + ((g.ro - g.ri) * g.XP + c + g.ro - g.ri) * P::PX;
+        typename P::T* out = outer ? Vo + c : Vi + c;
+        const int pitch = outer ? g.VP : g.VPI;
+        const int w = outer ? 2 * g.ro + 1 : 2 * g.ri + 1;
+        const int plane = g.th * pitch;
+        if (grp == 0) vertical_group<P, 0>(in, rs, out, plane, pitch, g.th, w);
+        else vertical_group<P, 1>(in, rs, out, plane, pitch, g.th, w);
     }
+}
+
+// ---------------------------------------------------------------- stage 2: horizontal sums, in place
+template <class T, int N>
+__device__ __forceinline__ void load_row(const T* p, T (&v)[N]) {
+    constexpr int V = 16 / sizeof(T);  // elements per 16-byte load (p is 16-byte aligned)
+#pragma unroll
+    for (int k = 0; k < N; k += V) {
+        if constexpr (sizeof(T) == 4) {
+            const float4 q = *reinterpret_cast<const float4*>(p + k);
+            const float e[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (k + u < N) v[k + u] = e[u];
+        } else {
+            const longlong2 q = *reinterpret_cast<const longlong2*>(p + k);
+            v[k] = q.x;
+            if (k + 1 < N) v[k + 1] = q.y;
+        }
+    }
+}
+
+template <class T>
+__device__ __forceinline__ void store_seg(T* p, const T (&o)[kSeg]) {
+#pragma unroll
+    for (int k = 0; k < kSeg; k += 16 / (int)sizeof(T)) {
+        if constexpr (sizeof(T) == 4) {
+            *reinterpret_cast<float4*>(p + k) = make_float4(o[k], o[k + 1], o[k + 2], o[k + 3]);
+        } else {
+            *reinterpret_cast<longlong2*>(p + k) = make_longlong2(o[k], o[k + 1]);
+        }
+    }
+}
+
+// Row of TW + 2R column sums -> TW window sums of width 2R + 1, in place; segment s reads
+// columns [8s, 8s + 8 + 2R) into registers and writes [8s, 8s + 8).
+template <class T, int R>
+__device__ __forceinline__ void hrow_reg(T* row) {
+    constexpr int NV = kSeg + 2 * R;
+    if constexpr (R > 0) {  // (a window one column wide: the column sums already are the window sums)
+#pragma unroll
+        for (int s = 0; s < TW / kSeg; ++s) {
+            T v[NV];
+            load_row<T, NV>(row + s * kSeg, v);
+            T o[kSeg];
+            T acc = v[0];
+#pragma unroll
+            for (int k = 1; k < 2 * R + 1; ++k) acc += v[k];
+            o[0] = acc;
+#pragma unroll
+            for (int j = 1; j < kSeg; ++j) {
+                acc += v[j + 2 * R] - v[j - 1];
+                o[j] = acc;
+            }
+            store_seg<T>(row + s * kSeg, o);
+        }
+    }
+}
+
+// The same for any radius, reading shared memory as it goes: the value leaving the window
+// at column j - 1 is kept from before that column was overwritten.
+template <class T>
+__device__ __forceinline__ void hrow_smem(T* row, int R) {
+    if (R == 0) return;
+    for (int s = 0; s < TW / kSeg; ++s) {
+        T* p = row + s * kSeg;
+        T acc = p[0];
+        for (int k = 1; k < 2 * R + 1; ++k) acc += p[k];
+        T carry = p[0];
+        p[0] = acc;
+        for (int j = 1; j < kSeg; ++j) {
+            acc += p[j + 2 * R] - carry;
+            carry = p[j];
+            p[j] = acc;
+        }
+    }
+}
+
+template <class T>
+__device__ __forceinline__ void hrow(T* row, int R) {
+    switch (R) {
+        case 0: hrow_reg<T, 0>(row); break;
+        case 1: hrow_reg<T, 1>(row); break;
+        case 2: hrow_reg<T, 2>(row); break;
+        case 3: hrow_reg<T, 3>(row); break;
+        case 4: hrow_reg<T, 4>(row); break;
+        case 5: hrow_reg<T, 5>(row); break;
+        case 6: hrow_reg<T, 6>(row); break;
+        case 7: hrow_reg<T, 7>(row); break;
+        case 8: hrow_reg<T, 8>(row); break;
+        case 9: hrow_reg<T, 9>(row); break;
+        case 10: hrow_reg<T, 10>(row); break;
+        default: hrow_smem<T>(row, R); break;
+    }
+}
+
+template <class P>
+__device__ __forceinline__ void horizontal_sums(const TileGeom& g, typename P::T* Vo, typename P::T* Vi) {
+    constexpr int NC = P::NC;
+    const int rows = NC * g.th;
+    for (int t = threadIdx.x; t < 2 * rows; t += blockDim.x) {
+        if (t < rows) hrow(Vo + t * g.VP, g.ro);
+        else hrow(Vi + (t - rows) * g.VPI, g.ri);
+    }
+}
+
+// Stages 0-2 of one tile for a payload: afterwards Vo[(q th + i) VP + j] holds the outer-square
+// sum and Vi[(q th + i) VPI + j] the inner-square sum of channel q at output pixel (i, j).
+template <class P>
+__device__ __forceinline__ void tile_sums(const TileGeom& g, typename P::T* xs, typename P::T* Vo,
+                                          typename P::T* Vi) {
+    vertical_sums<P>(g, xs, Vo, Vi);
+    __syncthreads();
+    horizontal_sums<P>(g, Vo, Vi);
+    __syncthreads();
 }
 
 // ---------------------------------------------------------------- small dense algebra in registers
@@ -408,7 +599,7 @@ __device__ __forceinline__ void jacobi_inplace(float (&A)[D][D], float (&V)[D][D
     }
 }
 
-// ---------------------------------------------------------------- detector kernel
+// ---------------------------------------------------------------- detector tile
 // One output tile (tile_x, tile_y) of height th; any block size that is a multiple of 32
 // and at most 512 gives the same results (every reduction has a fixed order).
 template <int D>
@@ -417,68 +608,13 @@ __device__ void detect_tile(const DetectArgs& a, int th, int tile_x, int tile_y,
     constexpr int NC = P::NC;
     const TileGeom g(a.H, a.W, a.inner, a.outer, th, tile_x, tile_y);
     float* xs = reinterpret_cast<float*>(smem_raw);
-    float* hso = xs + (size_t)g.HR * g.XP * P::DP;
-    float* hsi = hso + (size_t)NC * g.HR * HP;
-    // tile reference after the inner sums (in the dynamic buffer, not static shared memory,
-    // so that a kernel holding several instantiations keeps its static size small)
-    float* cref = hsi + (size_t)NC * g.nin * HP;  // [8]
-
-    // stage 0 + tile reference: the mean of the middle halo row (a tile row), summed by warp 0
-    // in a fixed order whatever the block size.  Any value near the tile's data serves: the
-    // shift only keeps the second-moment sums from cancelling.
-    load_halo_spec<D>(g, a.x, xs);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int xs_bytes = (g.HR * g.XP * P::DP * 4 + 15) & ~15;
+    float* Vo = reinterpret_cast<float*>(smem_raw + xs_bytes);
+    float* Vi = Vo + NC * th * g.VP;
+    float* cref = Vi + NC * th * g.VPI;  // [8]
+    load_halo_spec<D>(g, a.x, xs, cref);
     __syncthreads();
-    if (warp == 0) {
-        float acc[D];
-#pragma unroll
-        for (int k = 0; k < D; ++k) acc[k] = 0.f;
-        const int r = g.HR / 2;
-        for (int c = lane; c < g.WR; c += 32) {
-            const float* px = xs + ((size_t)r * g.XP + c) * P::DP;
-#pragma unroll
-            for (int k = 0; k < D; ++k) acc[k] += px[k];
-        }
-#pragma unroll
-        for (int k = 0; k < D; ++k) {
-            float t = acc[k];
-#pragma unroll
-            for (int o = 16; o >= 1; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-            if (lane == 0) cref[k] = t / (float)g.WR;
-        }
-    }
-    __syncthreads();
-    // stage 1: shift in place
-    {
-        float c[D];
-#pragma unroll
-        for (int k = 0; k < D; ++k) c[k] = cref[k];
-        const int n = g.HR * g.WR;
-        for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-            const int r = idx / g.WR, cc = idx - r * g.WR;
-            float* v = xs + ((size_t)r * g.XP + cc) * P::DP;
-#pragma unroll
-            for (int k = 0; k < D; ++k) v[k] -= c[k];
-        }
-    }
-    __syncthreads();
-    // stage 2
-    auto chan = [&](int r, int col, float (&ch)[NC]) {
-        const float* v = xs + ((size_t)r * g.XP + col) * P::DP;
-        float t[D];
-        if constexpr (D == 4) {
-            const float4 q = *reinterpret_cast<const float4*>(v);
-            t[0] = q.x; t[1] = q.y; t[2] = q.z; t[3] = q.w;
-        } else {
-#pragma unroll
-            for (int k = 0; k < D; ++k) t[k] = v[k];
-        }
-        P::channels(t, ch);
-    };
-    horizontal_sums<P>(g, chan, hso, hsi);
-    __syncthreads();
-    vertical_sums_inplace<P>(g, hso, hsi);
-    __syncthreads();
+    tile_sums<P>(g, xs, Vo, Vi);
 
     // stage 4, one pixel per thread and step
     const int N = (2 * g.ro + 1) * (2 * g.ro + 1) - (2 * g.ri + 1) * (2 * g.ri + 1);
@@ -497,10 +633,15 @@ __device__ void detect_tile(const DetectArgs& a, int th, int tile_x, int tile_y,
             continue;
         }
         float So[NC], Si[NC];
+        {
+            const float* po = Vo + i * g.VP + j;
+            const float* pi = Vi + i * g.VPI + j;
+            const int plo = th * g.VP, pli = th * g.VPI;
 #pragma unroll
-        for (int q = 0; q < NC; ++q) {
-            So[q] = hso[q * g.HR * HP + i * HP + j];
-            Si[q] = hsi[q * g.nin * HP + i * HP + j];
+            for (int q = 0; q < NC; ++q) {
+                So[q] = po[q * plo];
+                Si[q] = pi[q * pli];
+            }
         }
         float mo[D], mi[D], Co[D][D];
 #pragma unroll
@@ -589,6 +730,38 @@ __device__ void detect_tile(const DetectArgs& a, int th, int tile_x, int tile_y,
             a.out[2][o] = (a.dwest_mode == 0) ? fabsf(acc) : sqrtf(acc2);
         }
         if (a.flags) a.flags[o] = flag;
+    }
+}
+
+// The census tile: stages 0-2 with linear pixel indices as the payload (channels 1, q, q^2),
+// out[p][6] = background count, sum, sum of squares, then the inner ones.
+__device__ __forceinline__ void census_tile(int H, int W, int inner, int outer, int border, int th, int tile_x,
+                                            int tile_y, long long* __restrict__ out, unsigned char* smem_raw) {
+    using P = CensusPayload;
+    const TileGeom g(H, W, inner, outer, th, tile_x, tile_y);
+    long long* xs = reinterpret_cast<long long*>(smem_raw);
+    const size_t xs_bytes = ((size_t)g.HR * g.XP * P::WORDS * 4 + 15) & ~(size_t)15;
+    long long* Vo = reinterpret_cast<long long*>(smem_raw + xs_bytes);
+    long long* Vi = Vo + (size_t)P::NC * th * g.VP;
+    load_halo_census(g, xs);
+    __syncthreads();
+    tile_sums<P>(g, xs, Vo, Vi);
+    for (int pix = threadIdx.x; pix < th * TW; pix += blockDim.x) {
+        const int i = pix / TW, j = pix - i * TW;
+        const int y = g.ty0 + i, xq = g.tx0 + j;
+        if (y >= H || xq >= W) continue;
+        long long* o = out + ((size_t)y * W + xq) * 6;
+        if (border == 1 && (y - g.ro < 0 || y + g.ro >= H || xq - g.ro < 0 || xq + g.ro >= W)) {
+            for (int t = 0; t < 6; ++t) o[t] = -1;
+            continue;
+        }
+        long long So[3], Si[3];
+        for (int q = 0; q < 3; ++q) {
+            So[q] = Vo[(q * th + i) * g.VP + j];
+            Si[q] = Vi[(q * th + i) * g.VPI + j];
+        }
+        o[0] = So[0] - Si[0]; o[1] = So[1] - Si[1]; o[2] = So[2] - Si[2];
+        o[3] = Si[0]; o[4] = Si[1]; o[5] = Si[2];
     }
 }
 

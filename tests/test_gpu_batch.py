@@ -77,7 +77,7 @@ def test_autotuned_batch_matches_oracle(wd, scenes):
     b = wd.wdad_batch(jobs, autotune=True, use_graph=True)
     b.launch()
     st, ths = b.status()
-    assert st == wd.WDAD_OK and all(t in (2, 4, 8, 16) for t in ths)
+    assert st == wd.WDAD_OK and all(1 <= t <= 16 for t in ths)
     for sc, job, (H, W, L, win, det) in zip(scenes, jobs, SHAPES):
         a = oracle.dwt_approx(sc.cube)
         got = job["scores"].cpu().numpy()
@@ -95,7 +95,7 @@ def test_autotuned_batch_matches_oracle(wd, scenes):
 
 def test_autotune_returns_a_feasible_tile_height(wd):
     th = wd.wdad_autotune(4, 7, 21)
-    assert th in (2, 4, 8, 16)
+    assert 1 <= th <= 16
     assert wd.wdad_autotune(4, 7, 21) == th  # cached
 
 

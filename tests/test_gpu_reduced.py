@@ -86,7 +86,8 @@ def test_dwt_scene_and_ragged_pixel_count(wd, scene48):
 
 # ---------------------------------------------------------------- A2 windows, bit-exact
 @pytest.mark.parametrize("H,W", [(48, 48), (5, 7), (1, 40), (40, 1), (37, 70), (100, 33), (2, 2)])
-@pytest.mark.parametrize("win", [(1, 3), (3, 9), (3, 11), (5, 15), (7, 21), (5, 13), (1, 15)])
+@pytest.mark.parametrize("win", [(1, 3), (3, 9), (3, 11), (5, 15), (7, 21), (5, 13), (1, 15), (3, 25), (23, 31),
+                                 (61, 63)])
 @pytest.mark.parametrize("border", [0, 1])
 def test_window_census_bit_exact(wd, H, W, win, border):
     got = wd.wdad_window_census(H, W, inner=win[0], outer=win[1], border=border).cpu().numpy().reshape(-1, 6)
@@ -206,9 +207,29 @@ def test_empty_and_invalid_inputs(wd):
     with pytest.raises(wd.WdadError) as ei:
         wd.wdad_detect(x, 7)
     assert ei.value.status == wd.WDAD_ERR_ARG
-    with pytest.raises(wd.WdadError) as ei:  # shared memory cannot hold a 61/63 dual window tile
-        wd.wdad_detect(x, 0, inner=61, outer=63)
-    assert ei.value.status == wd.WDAD_ERR_UNSUPPORTED
+    with pytest.raises(wd.WdadError) as ei:  # windows are capped at 63 pixels
+        wd.wdad_detect(x, 0, inner=61, outer=65)
+    assert ei.value.status == wd.WDAD_ERR_ARG
+
+
+def test_widest_windows_match_oracle(wd):
+    # windows wider than 21 pixels: the halo is wider than 64 pixels and the horizontal sums
+    # slide through shared memory instead of registers (radius > 10)
+    rng = np.random.default_rng(63)
+    cube = (1.0 + 0.2 * rng.standard_normal((40, 70, 4)) @ (np.eye(4) + 0.3 * rng.standard_normal((4, 4)))
+            ).astype(np.float32)
+    for win in ((61, 63), (3, 25), (23, 31)):
+        got = wd.wdad_detect_all(_gpu(cube), reduce=False, inner=win[0], outer=win[1]).cpu().numpy()
+        for det in (0, 1):
+            e = relerr(got[det], oracle.detect(cube, det, win[0], win[1]))
+            assert e.max() <= TOL_SCORE, (win, det, e.max())
+        want, aux = oracle.detect(cube, 2, win[0], win[1], want_aux=True)
+        ok = dwest_ok_mask(aux)
+        # a 61 x 61 inner window: C_i comes from direct FP32 sums of 61 terms in each direction
+        # (3721 pixels), a rounding about 30 times that of a 3 x 3 window's
+        tol = 1e-3 if win[0] > 31 else TOL_SCORE
+        e = dwest_relerr(got[2], want, aux)[ok]
+        assert ok.mean() >= 0.5 and e.max() <= tol, (win, e.max())
 
 
 def test_auc_matches_oracle_and_paper_direction(wd, scene48):

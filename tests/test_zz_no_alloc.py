@@ -70,14 +70,19 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(wd):
     assert ei.value.status == wd.WDAD_ERR_ARG
 
 
-def test_noalloc_window_beyond_shared_memory_is_unsupported(wd):
-    # a 63 x 63 window's tile does not fit shared memory: both entry points refuse it
-    x = torch.ones((70, 70, 16), device="cuda")
-    for fn in (lambda: wd.wdad_detect_all_noalloc(x, inner=61, outer=63),
-               lambda: wd.wdad_detect_all(x, reduce=True, inner=61, outer=63)):
+def test_noalloc_widest_window(wd):
+    # the widest window the library takes (63 pixels): both entry points agree bit for bit;
+    # one wider is refused by both
+    from paper_1201_2025_gb300 import synth
+    sc = synth.make_scene(70, 90, 64, seed=14, n_anom=4, margin=4)
+    x = torch.from_numpy(sc.cube).cuda()
+    got, want, f1, f2 = _both(wd, x, inner=61, outer=63)
+    assert torch.equal(got, want) and torch.equal(f1, f2)
+    for fn in (lambda: wd.wdad_detect_all_noalloc(x, inner=61, outer=65),
+               lambda: wd.wdad_detect_all(x, reduce=True, inner=61, outer=65)):
         with pytest.raises(wd.WdadError) as ei:
             fn()
-        assert ei.value.status == wd.WDAD_ERR_UNSUPPORTED
+        assert ei.value.status == wd.WDAD_ERR_ARG
 
 
 def test_noalloc_allocates_no_device_memory():
