@@ -57,6 +57,41 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def _bf16_peak():
+    """Sustained dense BF16 tensor rate (TFLOP/s) for kernels timed inside a longer run."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops_sustained"]), "measured (sustained)"
+    except Exception:
+        return 1700.0, "fallback (sustained)"
+
+
+def fullband_ceiling_flops(L: int, inner: int, outer: int, detectors: str):
+    """Definitional work per pixel of the full-band detectors (the window Gram on the tensor
+    cores, the factorisations on FP32 SIMT): (tensor flops, SIMT flops).
+    LRX/DWRX: background Gram 2 N L^2, Cholesky L^3 / 3 and two triangular solves 2 L^2.
+    DWEST adds the inner Gram 2 n_i L^2 and a symmetric eigen-decomposition, about 9 L^3."""
+    N = outer * outer - inner * inner
+    ni = inner * inner
+    tc = 2.0 * N * L * L
+    simt = L ** 3 / 3.0 + 2.0 * L * L
+    if detectors == "all3":
+        tc += 2.0 * ni * L * L
+        simt += 9.0 * L ** 3
+    return tc, simt
+
+
+def fullband_roofline(L, inner, outer, detectors, mpx_s, tc_peak_tflops, fp32_peak_tflops):
+    """Fraction of the full-band ceiling: ceiling time per pixel (Gram at the tensor rate plus
+    the factorisation at the FP32 SIMT rate) over the measured time per pixel."""
+    tc, simt = fullband_ceiling_flops(L, inner, outer, detectors)
+    t_ceiling = tc / (tc_peak_tflops * 1e12) + simt / (fp32_peak_tflops * 1e12)
+    t_meas = 1.0 / (mpx_s * 1e6)
+    return {"ceiling_Mpixel_s": 1e-6 / t_ceiling, "achieved_Mpixel_s": mpx_s, "frac": t_ceiling / t_meas,
+            "tensor_flops_per_px": tc, "simt_flops_per_px": simt}
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
@@ -493,13 +528,23 @@ def run_ours(args):
         strip = x[:rows].contiguous()
         sout = torch.empty((3, rows, W), device=dev)
         sone = torch.empty((rows, W), device=dev)
+        tc_peak, tc_kind = _bf16_peak()
         for (wi, wo), p in zip(WINDOWS, params):
             ms_all = _time(lambda: wdad.wdad_detect_all(strip, reduce=False, params=p, out=sout), n=2)
             ms_lrx = _time(lambda: wdad.wdad_detect(strip, 0, reduce=False, params=p, out=sone), n=2)
-            full[f"{wi}/{wo}"] = {"all3_Mpixel_s": rows * W / (ms_all * 1e-3) / 1e6,
-                                  "lrx_Mpixel_s": rows * W / (ms_lrx * 1e-3) / 1e6,
-                                  "reduced_speedup_all3": (ms_all / (rows * W)) / ((dwt_alone_ms + det_ms[WINDOWS.index((wi, wo))]) / (H * W))}
-        full["sample"] = f"{rows} x {W} x {L} strip of the cube, FP32, all pixels of the strip"
+            pm = wdad.wdad_default_params(inner=wi, outer=wo, precision=1)
+            ms_lrx_mixed = _time(lambda: wdad.wdad_detect(strip, 0, reduce=False, params=pm, out=sone), n=2)
+            ent = {"all3_Mpixel_s": rows * W / (ms_all * 1e-3) / 1e6,
+                   "lrx_Mpixel_s": rows * W / (ms_lrx * 1e-3) / 1e6,
+                   "lrx_mixed_Mpixel_s": rows * W / (ms_lrx_mixed * 1e-3) / 1e6,
+                   "reduced_speedup_all3": (ms_all / (rows * W)) / ((dwt_alone_ms + det_ms[WINDOWS.index((wi, wo))]) / (H * W))}
+            ent["roofline_lrx_fp32"] = fullband_roofline(L, wi, wo, "lrx", ent["lrx_Mpixel_s"], tc_peak, alu_peak)
+            ent["roofline_lrx_mixed"] = fullband_roofline(L, wi, wo, "lrx", ent["lrx_mixed_Mpixel_s"], tc_peak, alu_peak)
+            ent["roofline_all3_fp32"] = fullband_roofline(L, wi, wo, "all3", ent["all3_Mpixel_s"], tc_peak, alu_peak)
+            full[f"{wi}/{wo}"] = ent
+        full["sample"] = f"{rows} x {W} x {L} strip of the cube, all pixels of the strip"
+        full["roofline_peaks"] = {"tensor_TFLOP_s": tc_peak, "tensor_source": tc_kind, "fp32_simt_TFLOP_s": alu_peak,
+                                  "fp32_source": f"derived: 152 SMs x 128 FP32 lanes x 2 at {sm_mhz:.0f} MHz"}
     # mixed precision against the FP32 and FP64 full-band forms on an ill-conditioned AR(1) scene.
     # Window 3/11 (N = 112 < L): LRX/DWRX take the FP32 sample-Gram (Woodbury) form in every
     # precision, DWEST the BF16 tensor-core Gram in MIXED; window 7/21 (N = 392 >= L): all three
@@ -594,7 +639,14 @@ def run_ours(args):
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded AVIRIS-shaped linear-mixing cube)",
         "config": _config(ws),
-        "roofline": roofline, "roofline_other_kernel": roofline_other, "breakdown": breakdown, "e2e": e2e,
+        "per_detector": {"value": 3 * value, "unit": "Mpixel/s per detector",
+                         "note": "pixel-window-detector evaluations per second: value x 3 detectors"},
+        "step_frac_of_hbm": breakdown["step_algorithmic_GBps"] / peak,
+        "roofline": roofline, "roofline_other_kernel": roofline_other,
+        "roofline_fullband": {k: {f: full[k][f]["frac"] for f in ("roofline_lrx_fp32", "roofline_lrx_mixed",
+                                                                   "roofline_all3_fp32")}
+                              for k in full if isinstance(full.get(k), dict) and "roofline_lrx_fp32" in full[k]},
+        "breakdown": breakdown, "e2e": e2e,
         "cpu_baseline": cpu, "gpu_launches": nsteps * 2, "clocks": clocks,
     }), flush=True)
 
