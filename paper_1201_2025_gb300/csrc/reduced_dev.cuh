@@ -182,7 +182,7 @@ __device__ __forceinline__ void store_shifted(float* dst, const float (&v)[D], c
 // Warp w takes halo rows w, w + nw, ...; lanes take columns.  The first 64 columns of
 // every warp's first kHeld rows are fetched before the barrier that publishes the tile
 // reference, so their latency overlaps warp 0's reference sum; the rest after it.
-constexpr int kHeld = 3;
+constexpr int kHeld = 2;
 template <int D>
 __device__ __forceinline__ void load_halo_spec(const TileGeom& g, const float* __restrict__ x, float* xs, float* cref) {
     using P = SpecPayload<D>;
