@@ -212,9 +212,12 @@ typedef struct {
 
 typedef struct wdad_batch_ctx* wdad_batch;
 
-/* Tile height the library's autotuner picks for D bands and a window: candidate heights
- * (16, 8, 4, 2 rows: sliding sums restart at least every 16 rows) are timed with CUDA events
- * on a synthetic 256 x 256 cube; the winner is cached in the handle.  Synchronises `stream`; do not call while `stream` is being captured. */
+/* Tile height the library's autotuner picks for D bands and a window: every height from 16
+ * down to 4 rows that fits shared memory (sliding sums restart at least every 16 rows) is
+ * timed with CUDA events on a synthetic 256 x 256 cube (the batch tunes on a 1024 x 1024
+ * cube, where the per-pixel cost that matters in a full GPU shows); the default plan is kept
+ * unless another height is at least 3% faster.  The winner is cached in the handle.  Synchronises `stream`; do not call while
+ * `stream` is being captured. */
 wdad_status wdad_autotune(wdad_handle h, int D, int inner, int outer, int* tile_h, void* stream);
 
 /* Prepare a batch of n jobs: DWT plans, tile plans (autotune != 0: the autotuner's, else

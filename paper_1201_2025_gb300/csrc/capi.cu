@@ -27,6 +27,9 @@ struct wdad_ctx {
     struct DwtPlan { int L, taps, J, K; float* A; };
     std::vector<DwtPlan> dwt_plans;
     std::map<long long, int> tuned;  // (D, inner, outer) -> autotuned tile height
+    // second stream and events of the host entry point's row-band pipeline
+    cudaStream_t aux = nullptr;
+    std::vector<cudaEvent_t> evs;
     std::string err;
 };
 
@@ -292,54 +295,79 @@ __global__ void fill_pattern_kernel(float* x, int64_t n) {
     }
 }
 
-// Time every feasible tile height on a synthetic 256 x 256 x D cube and keep the fastest.
-// Fastest tile height for D bands and a window, timed on a 256 x 256 pattern.  two_per_sm:
-// only plans that keep two CTAs on an SM (the batch kernel shares one plan size across all
-// of its jobs, so a taller tile for one job would halve the occupancy of the whole batch).
-wdad_status autotune(wdad_ctx* h, int D, int inner, int outer, int* out, cudaStream_t s, bool two_per_sm = false) {
-    const long long key = tune_key(D, inner, outer) * 2 + (two_per_sm ? 1 : 0);
+// Tile height for D bands, a window and a cube shape, by measurement.  The candidates are every
+// height from 16 down to 4 rows that fits shared memory (two_per_sm: only plans that keep two
+// CTAs on an SM, since the batch kernel sizes one plan for all of its jobs), timed on a
+// synthetic cube of the given shape (at most 1024 x 1024 pixels) with CUDA events,
+// median of five launches after two warm-ups.  The default plan (the tallest tile that keeps
+// two CTAs per SM) is the incumbent: another height replaces it only when it is at least 3%
+// faster, so a tuned plan is never slower than the default by more than the timing noise.
+// Heights above 16 are not candidates: the sliding sums restart every th rows, and taller
+// tiles accumulate more FP32 rounding than the parity bars allow.  The block size follows the
+// height (one thread per output pixel, 512 threads at 16 rows): layouts with two pixels per
+// thread (256 or 384 threads per CTA) measured 5-15% slower on the 512 x 512 workload.
+wdad_status autotune(wdad_ctx* h, int D, int inner, int outer, int H, int W, int* out, cudaStream_t s,
+                     bool two_per_sm = false) {
+    H = std::max(32, std::min(H > 0 ? H : 256, 1024));
+    W = std::max(32, std::min(W > 0 ? W : 256, 1024));
+    // shape class: the next power of two of each side
+    int hb = 32, wb = 32;
+    while (hb < H) hb <<= 1;
+    while (wb < W) wb <<= 1;
+    const long long key = ((tune_key(D, inner, outer) * 2 + (two_per_sm ? 1 : 0)) << 8) ^ ((long long)hb << 4) ^ wb;
     auto it = h->tuned.find(key);
     if (it != h->tuned.end()) { *out = it->second; return WDAD_OK; }
-    const int S = 256;
-    const size_t nx = (size_t)S * S * D, ns = (size_t)3 * S * S;
+    H = hb;
+    W = wb;
+    const size_t nx = (size_t)H * W * D, ns = (size_t)3 * H * W;
     wdad_status st = ensure_ws(h, sizeof(float) * (nx + ns) + 256);
     if (st != WDAD_OK) return st;
     float* x = (float*)h->ws;
     float* sc = x + nx;
     fill_pattern_kernel<<<256, 256, 0, s>>>(x, (int64_t)nx);
     wdad::DetectArgs a{};
-    a.x = x; a.H = S; a.W = S; a.D = D; a.inner = inner; a.outer = outer; a.loading = 1e-3f;
+    a.x = x; a.H = H; a.W = W; a.D = D; a.inner = inner; a.outer = outer; a.loading = 1e-3f;
     a.dwest_tau = 1e-6f;
-    for (int t = 0; t < 3; ++t) a.out[t] = sc + (size_t)t * S * S;
-    cudaEvent_t e0, e1;
-    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
-        return fail(h, WDAD_ERR_CUDA, "autotune events");
+    for (int t = 0; t < 3; ++t) a.out[t] = sc + (size_t)t * H * W;
+    cudaEvent_t ev[6];
+    for (auto& e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) return fail(h, WDAD_ERR_CUDA, "autotune events");
+    auto feasible = [&](int th) {
+        const size_t need = wdad::detect_small_smem(D, inner, outer, th);
+        return need <= 227 * 1024 && (!two_per_sm || need <= wdad::detect_small_two_per_sm_bytes());
+    };
+    auto time_plan = [&](int th) -> float {
+        for (int r = 0; r < 2; ++r)
+            if (wdad::launch_detect_small_th(a, th, s) != cudaSuccess) { cudaGetLastError(); return -1.f; }
+        float t[5];
+        for (int r = 0; r < 5; ++r) {
+            cudaEventRecord(ev[r], s);
+            wdad::launch_detect_small_th(a, th, s);
+            cudaEventRecord(ev[r + 1], s);
+            if (cudaEventSynchronize(ev[r + 1]) != cudaSuccess) return -1.f;
+            cudaEventElapsedTime(&t[r], ev[r], ev[r + 1]);
+        }
+        std::sort(t, t + 5);
+        return t[2];
+    };
+    const int th_default = wdad::detect_small_default_th(D, inner, outer);
     int best = 0;
     float best_ms = 1e30f;
-    // sliding box sums restart every th rows; th <= 16 keeps the FP32 error at the level the
-    // parity tests pin
-    // candidates: 16 rows, the default plan (the tallest height that keeps two CTAs per SM),
-    // and the smaller powers of two
-    std::vector<int> cands = {16};
-    const int th_default = wdad::detect_small_default_th(D, inner, outer);
-    if (th_default > 0 && th_default < 16) cands.push_back(th_default);
-    for (int t : {8, 4, 2})
-        if (t != th_default) cands.push_back(t);
-    for (int th : cands) {
-        const size_t need = wdad::detect_small_smem(D, inner, outer, th);
-        if (need > 227 * 1024 || (two_per_sm && need > wdad::detect_small_two_per_sm_bytes())) continue;
-        if (wdad::launch_detect_small_th(a, th, s) != cudaSuccess) { cudaGetLastError(); continue; }
-        cudaEventRecord(e0, s);
-        for (int r = 0; r < 3; ++r) wdad::launch_detect_small_th(a, th, s);
-        cudaEventRecord(e1, s);
-        if (cudaEventSynchronize(e1) != cudaSuccess) break;
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best_ms) { best_ms = ms; best = th; }
+    if (th_default > 0 && feasible(th_default)) {
+        const float ms = time_plan(th_default);
+        if (ms > 0.f) { best = th_default; best_ms = ms; }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    if (best == 0 && two_per_sm) return autotune(h, D, inner, outer, out, s, false);
+    const float incumbent = best_ms;
+    int challenger = 0;
+    float challenger_ms = 1e30f;
+    for (int th = 16; th >= 4; --th) {
+        if (th == th_default || !feasible(th)) continue;
+        const float ms = time_plan(th);
+        if (ms > 0.f && ms < challenger_ms) { challenger_ms = ms; challenger = th; }
+    }
+    if (challenger && (best == 0 || challenger_ms < 0.97f * incumbent)) { best = challenger; best_ms = challenger_ms; }
+    for (auto& e : ev) cudaEventDestroy(e);
+    if (best == 0 && two_per_sm) return autotune(h, D, inner, outer, H, W, out, s, false);
     if (best == 0) return fail(h, WDAD_ERR_UNSUPPORTED, "no tile height fits window %d/%d for %d bands", inner, outer, D);
     h->tuned[key] = best;
     *out = best;
@@ -413,6 +441,8 @@ wdad_status wdad_destroy(wdad_handle h) {
         cudaDeviceSynchronize();
         if (h->ws) cudaFree(h->ws);
         for (auto& p : h->dwt_plans) cudaFree(p.A);
+        for (auto e : h->evs) cudaEventDestroy(e);
+        if (h->aux) cudaStreamDestroy(h->aux);
     }
     delete h;
     return WDAD_OK;
@@ -633,6 +663,69 @@ wdad_status wdad_detect_all_host(wdad_handle h, const float* host_cube, int H, i
             if (e != cudaSuccess) return cuda_fail(h, e, "copy cube to device");
         }
         const float* x = mapped ? mapped : d_cube;
+        if (reduce && D <= 8) {
+            // Row-band pipeline: the bands' (copy and) DWT run in order on `s`; on a second
+            // stream the detector tiles of band b, which read reduced rows up to the next
+            // band, wait for the DWT of band b + 1, and their score rows go back to the host
+            // while later bands still stream in.  The same kernels and plans as the one-pass
+            // path, so the same scores.
+            const float* A = nullptr;
+            int k2 = 0;
+            st = get_dwt_plan(h, L, params[0].wavelet_taps, params[0].level, &A, &k2, s);
+            if (st != WDAD_OK) return st;
+            int ro_max = 0;
+            for (int w = 0; w < nwin; ++w) ro_max = std::max(ro_max, params[w].outer / 2);
+            const int RC = std::max(64, 2 * (16 + ro_max));
+            const int nb = (H + RC - 1) / RC;
+            if (!h->aux && cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking) != cudaSuccess)
+                return fail(h, WDAD_ERR_CUDA, "host pipeline stream");
+            while ((int)h->evs.size() < nb + 1) {
+                cudaEvent_t ev;
+                if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
+                    return fail(h, WDAD_ERR_CUDA, "host pipeline events");
+                h->evs.push_back(ev);
+            }
+            // the previous call's detectors and copies on the second stream come first
+            e = cudaEventRecord(h->evs[nb], h->aux);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->evs[nb], 0);
+            for (int b = 0; b < nb && e == cudaSuccess; ++b) {
+                const int r0 = b * RC, r1 = std::min(H, r0 + RC);
+                const size_t off = (size_t)r0 * W, npx = (size_t)(r1 - r0) * W;
+                if (!mapped)
+                    e = cudaMemcpyAsync(d_cube + off * L, host_cube + off * L, sizeof(float) * npx * L,
+                                        cudaMemcpyHostToDevice, s);
+                if (e == cudaSuccess) e = wdad::launch_dwt_approx(x + off * L, (int64_t)npx, L, A, D, d_red + off * D,
+                                                                  h->num_sms, s);
+                if (e == cudaSuccess) e = cudaEventRecord(h->evs[b], s);
+            }
+            if (e != cudaSuccess) return cuda_fail(h, e, "host pipeline: copy and DWT");
+            for (int b = 0; b < nb && e == cudaSuccess; ++b) {
+                const int r0 = b * RC, r1 = std::min(H, r0 + RC);
+                e = cudaStreamWaitEvent(h->aux, h->evs[std::min(b + 1, nb - 1)], 0);
+                for (int w0 = 0; w0 < nwin && e == cudaSuccess; w0 += wdad::kMaxWindowsPerLaunch) {
+                    const int n = std::min(wdad::kMaxWindowsPerLaunch, nwin - w0);
+                    wdad::DetectArgs a[wdad::kMaxWindowsPerLaunch];
+                    for (int i = 0; i < n; ++i) {
+                        const wdad_params* p = &params[w0 + i];
+                        a[i] = wdad::DetectArgs{};
+                        a[i].x = d_red; a[i].H = H; a[i].W = W; a[i].D = D;
+                        a[i].inner = p->inner; a[i].outer = p->outer; a[i].loading = p->loading;
+                        a[i].border = p->border; a[i].dwest_mode = p->dwest_mode; a[i].dwest_tau = p->dwest_tau;
+                        float* o = d_out + (size_t)(w0 + i) * 3 * P;
+                        a[i].out[0] = o; a[i].out[1] = o + P; a[i].out[2] = o + 2 * P;
+                    }
+                    e = wdad::launch_detect_small_multi_rows(a, n, r0, r1, h->aux);
+                }
+                for (int m = 0; m < 3 * nwin && e == cudaSuccess; ++m)
+                    e = cudaMemcpyAsync(host_scores + (size_t)m * P + (size_t)r0 * W, d_out + (size_t)m * P + (size_t)r0 * W,
+                                        sizeof(float) * (size_t)(r1 - r0) * W, cudaMemcpyDeviceToHost, h->aux);
+            }
+            // the call is complete on `s` once the second stream's work is
+            if (e == cudaSuccess) e = cudaEventRecord(h->evs[nb], h->aux);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->evs[nb], 0);
+            if (e != cudaSuccess) return cuda_fail(h, e, "host pipeline: detectors and copies");
+            return WDAD_OK;
+        }
         if (reduce) {
             const float* A = nullptr;
             int k2 = 0;
@@ -700,7 +793,7 @@ wdad_status wdad_autotune(wdad_handle h, int D, int inner, int outer, int* tile_
         return fail(h, WDAD_ERR_ARG, "autotune: D in 1..8, odd windows 1 <= inner < outer <= 63");
     try {
         DeviceGuard g(h->device);
-        return autotune(h, D, inner, outer, tile_h, (cudaStream_t)stream);
+        return autotune(h, D, inner, outer, 0, 0, tile_h, (cudaStream_t)stream);
     } catch (...) {
         return fail(h, WDAD_ERR_NOMEM, "host exception");
     }
@@ -752,7 +845,9 @@ wdad_status wdad_batch_create(wdad_handle h, int n, const wdad_job* jobs, int au
             if (st != WDAD_OK) return st;
             int th = wdad::detect_small_default_th(K, j.params.inner, j.params.outer);
             if (autotune_plans) {
-                st = autotune(h, K, j.params.inner, j.params.outer, &th, s, true);
+                // a batch fills the GPU with many jobs: the per-pixel cost of a plan is what counts,
+                // so plans are timed on a cube large enough to fill the GPU, not at the job's size
+                st = autotune(h, K, j.params.inner, j.params.outer, 1024, 1024, &th, s, true);
                 if (st != WDAD_OK) return st;
             }
             if (th < 1) return fail(h, WDAD_ERR_UNSUPPORTED, "batch job %d: window too large", i);

@@ -1015,19 +1015,15 @@ __device__ unsigned process_pixel(const FullArgs& a, const Geo& g, Smem<T>& m, S
     if (want & 4u) {
         // C_diff = C_i - C_o (Eq. 2)
         for (int b = threadIdx.x; b < g.Dp; b += FB_THREADS) m.r2[b] = b < D ? m.mu_i[b] - m.mu_o[b] : T(0);
+        // the eigenproblem's Gram stays in the working precision in every mode: a BF16 Gram
+        // perturbs C_diff by about 2^-9 of its norm, more than the distance of most
+        // noise-level eigenvalues to the selection threshold, so it could not decide Eq. 4's
+        // selection; in mixed precision FP32 decides it and FP64 takes only the pixels whose
+        // selection FP32 cannot decide (the band below)
         mat_zero(m.A, g);
-        if constexpr (sizeof(T) == 4) {
-            if (g.tc) {
-                gram_tc(a.x, a.H, a.W, g, py, px, 0, N, ro, ri, m.mu_o, -1.f / (float)N, m.A, *st);
-                gram_tc(a.x, a.H, a.W, g, py, px, 1, ni, ro, ri, m.mu_i, 1.f / (float)ni, m.A, *st);
-            }
-        }
-        if (!g.tc) {
-            gram_accumulate<T>(a.x, a.H, a.W, g, py, px, 0, N, ro, ri, m.mu_o, T(1), m.A, m.xs);
-            mat_scale(m.A, g, T(-1) / (T)N);
-            gram_accumulate<T>(a.x, a.H, a.W, g, py, px, 1, ni, ro, ri, m.mu_i, T(1) / Num<T>::sqrt_((T)ni), m.A,
-                               m.xs);
-        }
+        gram_accumulate<T>(a.x, a.H, a.W, g, py, px, 0, N, ro, ri, m.mu_o, T(1), m.A, m.xs);
+        mat_scale(m.A, g, T(-1) / (T)N);
+        gram_accumulate<T>(a.x, a.H, a.W, g, py, px, 1, ni, ro, ri, m.mu_i, T(1) / Num<T>::sqrt_((T)ni), m.A, m.xs);
         tridiagonalise(m.A, g, m.v, m.p, m.dd, m.ee, m.red);
         // spectrum bounds (Gershgorin), extreme eigenvalues, threshold, count above it
         T glo, ghi;
@@ -1059,8 +1055,10 @@ __device__ unsigned process_pixel(const FullArgs& a, const Geo& g, Smem<T>& m, S
             *s_m = D - below;
             if (gate && maxabs > T(0)) {
                 // selection conditioning: an eigenvalue within max|lambda| / cond_gate of tau, the
-                // band never narrower than the BF16 perturbation of the Gram (2^-8 max|lambda|)
-                const T band = max(maxabs / (T)a.cond_gate, maxabs * T(0.00390625));
+                // band never narrower than 64 FP32 roundings of the spectrum's scale (2^-17
+                // max|lambda|), a generous bound on what the FP32 Gram, the tridiagonalisation
+                // and the Sturm counts can move an eigenvalue by
+                const T band = max(maxabs / (T)a.cond_gate, maxabs * T(7.62939453125e-6));
                 const int nb = sturm_below(m.dd, m.ee, D, tau + band, pivmin) -
                                sturm_below(m.dd, m.ee, D, tau - band, pivmin);
                 if (nb > 0) *s_m = -1 - *s_m;  // mark for the FP64 re-solve

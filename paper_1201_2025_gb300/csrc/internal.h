@@ -60,6 +60,9 @@ cudaError_t launch_detect_small_th(const DetectArgs& a, int th, cudaStream_t s);
 // up to kMaxWindowsPerLaunch windows of one cube (same x, H, W, D; default plans) in one launch
 constexpr int kMaxWindowsPerLaunch = 4;
 cudaError_t launch_detect_small_multi(const DetectArgs* a, int n, cudaStream_t s);
+// the same for the tiles whose first row lies in [row0, row1) (a band of the image; the
+// tiles read reduced rows up to row1 + th + outer / 2 - 2)
+cudaError_t launch_detect_small_multi_rows(const DetectArgs* a, int n, int row0, int row1, cudaStream_t s);
 int detect_small_default_th(int D, int inner, int outer);
 // Global RX of Eq. 1 on a [P][L] cube (L <= kGlobalRxMaxBands), scores [P]; workspace from
 // global_rx_workspace_bytes (0 for unsupported sizes).

@@ -22,6 +22,7 @@ struct MultiArgs {
     DetectArgs a[kMaxWindowsPerLaunch];
     int th[kMaxWindowsPerLaunch];
     int tiles_x[kMaxWindowsPerLaunch];
+    int ty0[kMaxWindowsPerLaunch];  // first tile row of each window in this launch
     int first[kMaxWindowsPerLaunch + 1];
     int n;
 };
@@ -45,7 +46,7 @@ __global__ void __launch_bounds__(512) detect_multi_kernel(MultiArgs m) {
     const int w = s_w;
     const int t = (int)blockIdx.x - m.first[w];
     const int tx = m.tiles_x[w];
-    detect_tile<D>(s_args, m.th[w], t % tx, t / tx, smem_raw);
+    detect_tile<D>(s_args, m.th[w], t % tx, m.ty0[w] + t / tx, smem_raw);
 }
 
 // ---------------------------------------------------------------- census kernel
@@ -160,7 +161,11 @@ static cudaError_t launch_multi_d(const MultiArgs& m, size_t smem, int blocks, c
 }
 
 cudaError_t launch_detect_small_multi(const DetectArgs* a, int n, cudaStream_t s) {
-    if (n < 1 || n > kMaxWindowsPerLaunch) return cudaErrorInvalidValue;
+    return launch_detect_small_multi_rows(a, n, 0, a[0].H, s);
+}
+
+cudaError_t launch_detect_small_multi_rows(const DetectArgs* a, int n, int row0, int row1, cudaStream_t s) {
+    if (n < 1 || n > kMaxWindowsPerLaunch || row0 < 0 || row1 < row0) return cudaErrorInvalidValue;
     MultiArgs m{};
     m.n = n;
     size_t smem = 0;
@@ -178,8 +183,11 @@ cudaError_t launch_detect_small_multi(const DetectArgs* a, int n, cudaStream_t s
         m.a[j] = a[w];
         m.th[j] = th;
         m.tiles_x[j] = (a[w].W + TW - 1) / TW;
+        // the tiles whose first row lies in [row0, row1)
+        const int y0 = (row0 + th - 1) / th, y1 = std::min((a[w].H + th - 1) / th, (row1 + th - 1) / th);
+        m.ty0[j] = y0;
         m.first[j] = (int)blocks;
-        blocks += (int64_t)m.tiles_x[j] * ((a[w].H + th - 1) / th);
+        blocks += (int64_t)m.tiles_x[j] * std::max(0, y1 - y0);
         smem = std::max(smem, detect_small_smem(a[w].D, a[w].inner, a[w].outer, th));
     }
     m.first[n] = (int)blocks;

@@ -90,8 +90,9 @@ def test_mixed_gate_everything_reproduces_fp64(wd, scene48):
 
 
 def test_mixed_without_gate_is_finite_and_unflagged(wd, scene48):
-    # with the gate off, LRX and DWRX stay on the BF16 Gram + FP32 solve; DWEST's selection
-    # band never falls below the BF16 perturbation of the Gram, so it is re-solved regardless
+    # with the gate off, LRX and DWRX stay on the BF16 Gram + FP32 solve; DWEST decides its
+    # selection in FP32 and re-solves in FP64 only the pixels with an eigenvalue within
+    # 2^-17 max|lambda| of the threshold: the FP32 map elsewhere, the FP64 map there
     cube = scene48.cube[:20, :24]
     x = _gpu(cube)
     for det in (0, 1):
@@ -99,9 +100,25 @@ def test_mixed_without_gate_is_finite_and_unflagged(wd, scene48):
         s = wd.wdad_detect(x, det, reduce=False, inner=3, outer=9, precision=1, cond_gate=1e30, flags=flags)
         assert bool(torch.isfinite(s).all())
         assert not bool(torch.any(flags & 1))
-    flags = torch.zeros(cube.shape[:2], dtype=torch.uint8, device="cuda")
-    wd.wdad_detect(x, 2, reduce=False, inner=3, outer=9, precision=1, cond_gate=1e30, flags=flags)
-    assert bool(torch.all(flags & 1))
+    # n_i + N = 81 < L: C_i - C_o has exact zero eigenvalues, whose FP32 values lie within the
+    # band around tau, so every pixel is re-solved.  At 7/21 (n_i + N = 441 >= L) FP32 decides
+    # the selection of the interior pixels; near the border the reflected window repeats
+    # samples, C_o loses rank and those pixels are re-solved.
+    for win, sub in (((3, 9), x), ((7, 21), _gpu(scene48.cube))):
+        Hh, Ww = sub.shape[:2]
+        flags = torch.zeros((Hh, Ww), dtype=torch.uint8, device="cuda")
+        mixed = wd.wdad_detect(sub, 2, reduce=False, inner=win[0], outer=win[1], precision=1, cond_gate=1e30,
+                               flags=flags)
+        fp32 = wd.wdad_detect(sub, 2, reduce=False, inner=win[0], outer=win[1], precision=0)
+        fp64 = wd.wdad_detect(sub, 2, reduce=False, inner=win[0], outer=win[1], precision=2)
+        re = (flags & 1).bool()
+        assert torch.equal(mixed[~re], fp32[~re]) and torch.equal(mixed[re], fp64[re])
+        if win == (3, 9):
+            assert bool(re.all())
+        else:
+            ro = win[1] // 2
+            frac = float(re[ro:Hh - ro, ro:Ww - ro].float().mean())
+            assert frac < 0.5, frac
 
 
 @pytest.mark.parametrize("win,gate,loading", [((3, 11), 1e6, 1e-3), ((5, 15), 1e6, 1e-3), ((3, 11), 3e4, 1e-3),

@@ -282,6 +282,30 @@ def test_host_entry_point_matches_device_path(wd, scene48, pinned):
         assert torch.equal(out[i], dev)
 
 
+@pytest.mark.parametrize("pinned", [True, False])
+@pytest.mark.parametrize("shape,wins", [((300, 70, 224), ((3, 9), (7, 21))),
+                                        ((203, 45, 128), ((1, 3), (3, 9), (5, 15), (7, 21), (3, 25)))])
+def test_host_entry_point_row_bands(wd, pinned, shape, wins):
+    # several row bands (64 rows or more each): the detector tiles of a band wait for the next
+    # band's DWT, and their score rows are copied back band by band; the maps must equal the
+    # device path's bit for bit, also with more than four windows (two detector launches per
+    # band) and called twice in a row
+    from paper_1201_2025_gb300 import synth
+    H, W, L = shape
+    sc = synth.make_scene(H, W, L, seed=H, n_anom=6, margin=4)
+    hc = torch.from_numpy(sc.cube.copy())
+    if pinned:
+        hc = hc.pin_memory()
+    params = [wd.wdad_default_params(inner=a, outer=b) for a, b in wins]
+    x = _gpu(sc.cube)
+    for _ in range(2):
+        out = wd.wdad_detect_all_host(hc, params=params)
+        torch.cuda.synchronize()
+        for i, (a, b) in enumerate(wins):
+            dev = wd.wdad_detect_all(x, reduce=True, inner=a, outer=b).cpu()
+            assert torch.equal(out[i], dev), (i, a, b)
+
+
 @pytest.mark.parametrize("case", ["reduced", "direct5", "fullband"])
 def test_detect_windows_equal_to_one_window_at_a_time(wd, scene48, case):
     # up to four windows share one launch (one grid, tiles of every window); each window's maps
