@@ -643,8 +643,9 @@ def run_ours(args):
            "link_GBps_achieved": (h2d_b + d2h_b) / (e2e_ms * 1e-3) / 1e9,
            "plain_pinned_copy_GBps": {"h2d": h2d_b / (h2d_ms * 1e-3) / 1e9, "d2h": d2h_b / (d2h_ms * 1e-3) / 1e9},
            "link_bound_ms": h2d_ms + d2h_ms,
-           "pipeline": "row bands: the DWT of band b reads the pinned cube in place while the detectors of "
-                       "band b - 1 run and their score rows are copied back on a second stream"}
+           "pipeline": "row bands over three streams: a copy engine moves band b to the device while the DWT "
+                       "of band b - 1 and the detector tiles of band b - 2 run, and each band's score rows go "
+                       "back in one strided copy behind its tiles"}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:

@@ -28,7 +28,7 @@ struct wdad_ctx {
     std::vector<DwtPlan> dwt_plans;
     std::map<long long, int> tuned;  // (D, inner, outer) -> autotuned tile height
     // second stream and events of the host entry point's row-band pipeline
-    cudaStream_t aux = nullptr;
+    cudaStream_t aux = nullptr, aux2 = nullptr;
     std::vector<cudaEvent_t> evs;
     std::string err;
 };
@@ -443,6 +443,7 @@ wdad_status wdad_destroy(wdad_handle h) {
         for (auto& p : h->dwt_plans) cudaFree(p.A);
         for (auto e : h->evs) cudaEventDestroy(e);
         if (h->aux) cudaStreamDestroy(h->aux);
+        if (h->aux2) cudaStreamDestroy(h->aux2);
     }
     delete h;
     return WDAD_OK;
@@ -664,44 +665,63 @@ wdad_status wdad_detect_all_host(wdad_handle h, const float* host_cube, int H, i
         }
         const float* x = mapped ? mapped : d_cube;
         if (reduce && D <= 8) {
-            // Row-band pipeline: the bands' (copy and) DWT run in order on `s`; on a second
-            // stream the detector tiles of band b, which read reduced rows up to the next
-            // band, wait for the DWT of band b + 1, and their score rows go back to the host
-            // while later bands still stream in.  The same kernels and plans as the one-pass
-            // path, so the same scores.
+            // Row-band pipeline over three streams: the copy engine brings band b to the device
+            // (h->aux2) while the SMs run the DWT of band b - 1 (the caller's stream) and the
+            // detector tiles of band b - 2, which read reduced rows up to band b - 1 (h->aux),
+            // whose score rows go back to the host behind them.  A DWT reading the pinned cube
+            // in place would hold the SMs for the whole transfer; the copy engine leaves them
+            // free.  The same kernels and plans as the one-pass path, so the same scores.
             const float* A = nullptr;
             int k2 = 0;
             st = get_dwt_plan(h, L, params[0].wavelet_taps, params[0].level, &A, &k2, s);
             if (st != WDAD_OK) return st;
+            if (mapped) {  // staged through device memory after all
+                const size_t need = align256(sizeof(float) * (size_t)P * L) + b_red + b_out + full;
+                st = ensure_ws(h, need);
+                if (st != WDAD_OK) return st;
+                base = (char*)h->ws;
+                d_cube = (float*)base;
+                d_red = (float*)(base + align256(sizeof(float) * (size_t)P * L));
+                d_out = (float*)((char*)d_red + b_red);
+            }
             int ro_max = 0;
             for (int w = 0; w < nwin; ++w) ro_max = std::max(ro_max, params[w].outer / 2);
-            const int RC = std::max(64, 2 * (16 + ro_max));
+            const int RC = std::max({64, 2 * (16 + ro_max), (H + 3) / 4});
             const int nb = (H + RC - 1) / RC;
-            if (!h->aux && cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking) != cudaSuccess)
-                return fail(h, WDAD_ERR_CUDA, "host pipeline stream");
-            while ((int)h->evs.size() < nb + 1) {
+            for (cudaStream_t* q : {&h->aux, &h->aux2})
+                if (!*q && cudaStreamCreateWithFlags(q, cudaStreamNonBlocking) != cudaSuccess)
+                    return fail(h, WDAD_ERR_CUDA, "host pipeline streams");
+            while ((int)h->evs.size() < 2 * nb + 2) {
                 cudaEvent_t ev;
                 if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
                     return fail(h, WDAD_ERR_CUDA, "host pipeline events");
                 h->evs.push_back(ev);
             }
-            // the previous call's detectors and copies on the second stream come first
-            e = cudaEventRecord(h->evs[nb], h->aux);
-            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->evs[nb], 0);
+            cudaEvent_t* cev = h->evs.data();           // band b on the device
+            cudaEvent_t* dev_ = h->evs.data() + nb;     // band b reduced
+            cudaEvent_t ev_start = h->evs[2 * nb], ev_done = h->evs[2 * nb + 1];
+            // everything this call touches is free once the caller's stream, which the previous
+            // call ended on, gets here
+            e = cudaEventRecord(ev_start, s);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(h->aux2, ev_start, 0);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(h->aux, ev_start, 0);
             for (int b = 0; b < nb && e == cudaSuccess; ++b) {
-                const int r0 = b * RC, r1 = std::min(H, r0 + RC);
-                const size_t off = (size_t)r0 * W, npx = (size_t)(r1 - r0) * W;
-                if (!mapped)
-                    e = cudaMemcpyAsync(d_cube + off * L, host_cube + off * L, sizeof(float) * npx * L,
-                                        cudaMemcpyHostToDevice, s);
-                if (e == cudaSuccess) e = wdad::launch_dwt_approx(x + off * L, (int64_t)npx, L, A, D, d_red + off * D,
-                                                                  h->num_sms, s);
-                if (e == cudaSuccess) e = cudaEventRecord(h->evs[b], s);
+                const size_t off = (size_t)b * RC * W, npx = (size_t)(std::min(H, (b + 1) * RC) - b * RC) * W;
+                e = cudaMemcpyAsync(d_cube + off * L, host_cube + off * L, sizeof(float) * npx * L,
+                                    cudaMemcpyHostToDevice, h->aux2);
+                if (e == cudaSuccess) e = cudaEventRecord(cev[b], h->aux2);
             }
-            if (e != cudaSuccess) return cuda_fail(h, e, "host pipeline: copy and DWT");
+            for (int b = 0; b < nb && e == cudaSuccess; ++b) {
+                const size_t off = (size_t)b * RC * W, npx = (size_t)(std::min(H, (b + 1) * RC) - b * RC) * W;
+                e = cudaStreamWaitEvent(s, cev[b], 0);
+                if (e == cudaSuccess)
+                    e = wdad::launch_dwt_approx(d_cube + off * L, (int64_t)npx, L, A, D, d_red + off * D, h->num_sms, s);
+                if (e == cudaSuccess) e = cudaEventRecord(dev_[b], s);
+            }
+            if (e != cudaSuccess) return cuda_fail(h, e, "host pipeline: copies and DWT");
             for (int b = 0; b < nb && e == cudaSuccess; ++b) {
                 const int r0 = b * RC, r1 = std::min(H, r0 + RC);
-                e = cudaStreamWaitEvent(h->aux, h->evs[std::min(b + 1, nb - 1)], 0);
+                e = cudaStreamWaitEvent(h->aux, dev_[std::min(b + 1, nb - 1)], 0);
                 for (int w0 = 0; w0 < nwin && e == cudaSuccess; w0 += wdad::kMaxWindowsPerLaunch) {
                     const int n = std::min(wdad::kMaxWindowsPerLaunch, nwin - w0);
                     wdad::DetectArgs a[wdad::kMaxWindowsPerLaunch];
@@ -716,13 +736,15 @@ wdad_status wdad_detect_all_host(wdad_handle h, const float* host_cube, int H, i
                     }
                     e = wdad::launch_detect_small_multi_rows(a, n, r0, r1, h->aux);
                 }
-                for (int m = 0; m < 3 * nwin && e == cudaSuccess; ++m)
-                    e = cudaMemcpyAsync(host_scores + (size_t)m * P + (size_t)r0 * W, d_out + (size_t)m * P + (size_t)r0 * W,
-                                        sizeof(float) * (size_t)(r1 - r0) * W, cudaMemcpyDeviceToHost, h->aux);
+                // the band's rows of all 3 nwin maps in one strided copy
+                if (e == cudaSuccess)
+                    e = cudaMemcpy2DAsync(host_scores + (size_t)r0 * W, sizeof(float) * (size_t)P, d_out + (size_t)r0 * W,
+                                          sizeof(float) * (size_t)P, sizeof(float) * (size_t)(r1 - r0) * W,
+                                          (size_t)(3 * nwin), cudaMemcpyDeviceToHost, h->aux);
             }
-            // the call is complete on `s` once the second stream's work is
-            if (e == cudaSuccess) e = cudaEventRecord(h->evs[nb], h->aux);
-            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->evs[nb], 0);
+            // the call is complete on the caller's stream once the other two streams' work is
+            if (e == cudaSuccess) e = cudaEventRecord(ev_done, h->aux);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_done, 0);
             if (e != cudaSuccess) return cuda_fail(h, e, "host pipeline: detectors and copies");
             return WDAD_OK;
         }
