@@ -5,9 +5,9 @@ targets of 1-3 px at abundance 0.1-0.5), windows (3,9), (5,15) and (7,21).
 A step = one db4 DWT of the cube (approximation matrix, K = 4) followed by the
 fused LRX + DWRX + DWEST pass at the three window pairs (one launch whose grid holds
 the tiles of all three windows): 9 score maps.
-Consecutive steps are pipelined over two streams (the DWT of the next step, which is
-HBM-bound, overlaps the issue-bound detector passes of the current one; two
-approximation buffers, ordered by events).
+The timed steps are one wdad_detect_sequence call over the cube K times: the DWT of
+the next step (HBM-bound, on the library's own stream and part of the SMs) overlaps the
+issue-bound detector launch of the current one, through two approximation buffers.
 value = 3 * H * W / step time (pixel-window evaluations per second, each with all
 three detectors; the DWT is counted once per cube).
 
@@ -389,36 +389,28 @@ def run_ours(args):
     pdwt = wdad.wdad_default_params()
     stream = torch.cuda.current_stream(dev)
     nsteps = args.steps
-    # Steps are pipelined over two streams: the DWT of step k (HBM-bound) writes approximation
-    # buffer k % 2 on s_dwt while the detector passes of step k - 1 (issue-bound) run on the main
-    # stream; events order each buffer's writer after the last reader.  Every step still runs
-    # the whole path (one DWT of the cube, nine score maps).
-    s_dwt = torch.cuda.Stream(dev)
-    approx2 = [approx, torch.empty_like(approx)]
+    # The timed steps are one wdad_detect_sequence call over the same cube K times: the DWT of
+    # step k (HBM-bound) runs on the library's own stream, on part of the SMs, beside the
+    # detector launch of step k - 1 (issue-bound) on the caller's stream, through two
+    # approximation buffers.  Every step still runs the whole path (one DWT of the cube, nine
+    # score maps).  Launch durations are timed with CUDA events on every EV_EVERY-th step only:
+    # a timing event on every step costs a few microseconds of overlap per step.
+    EV_EVERY = 8
 
     def make_events(n, timing):
-        return [[torch.cuda.Event(enable_timing=timing) for _ in range(4)] for _ in range(n)]
+        if not timing:
+            return None
+        evs = [torch.cuda.Event(enable_timing=True) if k % EV_EVERY == 0 else None
+               for k in range(n) for _ in range(4)]
+        for e in evs:  # create the CUDA events now, outside the timed region
+            if e is not None:
+                e.record(stream)
+        return evs
 
-    def run_steps(evs):
-        released = [None, None]
-        start = torch.cuda.Event()
-        start.record(stream)
-        s_dwt.wait_event(start)
-        for k, (ed0, ed1, em0, em1) in enumerate(evs):
-            b = k % 2
-            with torch.cuda.stream(s_dwt):
-                if released[b] is not None:
-                    s_dwt.wait_event(released[b])
-                ed0.record(s_dwt)
-                wdad.wdad_dwt_approx(x, pdwt, out=approx2[b])
-                ed1.record(s_dwt)
-            stream.wait_event(ed1)
-            em0.record(stream)
-            wdad.wdad_detect_windows(approx2[b], params, reduce=False, out=out)  # the three windows, one launch
-            em1.record(stream)
-            released[b] = em1
+    def run_steps(evs, n):
+        wdad.wdad_detect_sequence([x] * n, params, outs=[out] * n, events=evs)
 
-    run_steps(make_events(max(3, args.warmup), False))
+    run_steps(None, max(3, args.warmup))
     torch.cuda.synchronize()
     ev = make_events(nsteps, True)
 
@@ -434,7 +426,7 @@ def run_ours(args):
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record(stream)
-        run_steps(ev)
+        run_steps(ev, nsteps)
         t1.record(stream)
         torch.cuda.synchronize()
         barrier()
@@ -443,8 +435,11 @@ def run_ours(args):
     value = job_value(ws, ms_step)
 
     # launch durations inside the timed region, on each kernel's own stream (they overlap)
-    dwt_ms = sum(e[0].elapsed_time(e[1]) for e in ev) / nsteps
-    det_launch_ms = sum(e[2].elapsed_time(e[3]) for e in ev) / nsteps
+    sampled = [k for k in range(nsteps) if ev[4 * k] is not None]
+    dwt_ms = sum(ev[4 * k].elapsed_time(ev[4 * k + 1]) for k in sampled) / len(sampled)
+    det_launch_ms = sum(ev[4 * k + 2].elapsed_time(ev[4 * k + 3]) for k in sampled) / len(sampled)
+
+    wdad.wdad_dwt_approx(x, pdwt, out=approx)  # the approximation matrix the launches below read
 
     def _time_serial(fn, n=20):
         for _ in range(3):
@@ -605,7 +600,10 @@ def run_ours(args):
     screening = bench_screening(dev, stream, args.screen_train_cubes, args.screen_train_steps) \
         if not args.no_screen else None
     step_bytes = H * W * (BYTES_DWT_PER_PX + 3 * 3 * 4)
-    breakdown = {"pipeline": "DWT of step k on its own stream, overlapping the detector passes of step k-1",
+    breakdown = {"pipeline": "wdad_detect_sequence: the DWT of step k on the library's high-priority stream (3/4 of "
+                             "the SMs, a shared-memory reservation leaving room for one detector CTA per SM) beside "
+                             "the detector launch of step k-1; launch times from events on every "
+                             f"{EV_EVERY}th step",
                  "dwt_ms_in_step": dwt_ms, "detect_launch_ms_in_step": det_launch_ms, "dwt_ms_alone": dwt_alone_ms,
                  "detect_ms_alone": dict(zip([f"{a}/{b}" for a, b in WINDOWS], det_ms)),
                  "detect_three_windows_one_launch_ms_alone": windows_ms,

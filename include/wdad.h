@@ -147,15 +147,38 @@ wdad_status wdad_detect_windows(wdad_handle h, const float* cube, int H, int W, 
  * cube is reduced once (reduce = 1), all three detectors run for each of the nwin
  * parameter sets params[0..nwin-1] (same wavelet and level), and the score maps are
  * copied back to host_scores, laid out [nwin][3][H][W] (LRX, DWRX, DWEST).
- * host_cube and host_scores are HOST pointers.  With reduce = 1 and a page-locked
- * host_cube (cudaMallocHost / cudaHostRegister, device-mapped), the DWT reads the
- * cube in place over the host link (each spectrum once, no staging copy); otherwise
- * the cube is first copied to the handle's workspace on `stream`.  Page-locked memory
- * makes the copies asynchronous, pageable memory makes them synchronous.  The caller
- * synchronises `stream` before reading host_scores, and keeps host_cube unchanged until
- * then. */
+ * host_cube and host_scores are HOST pointers.  With reduce = 1 and K <= 8 the call runs
+ * in row bands (at least 64 rows, twice the widest halo plus a tile, a quarter of the
+ * image) over three streams: the handle's copy stream moves band b of the cube to the
+ * workspace, the DWT of band b - 1 runs on `stream`, and the handle's second stream runs
+ * the detector tiles of band b - 2 and copies that band's score rows back in one strided
+ * copy.  Otherwise the cube is copied to the workspace on `stream` and the one-pass path
+ * runs.  The maps equal wdad_detect_windows' bit for bit.  Page-locked memory makes the
+ * copies asynchronous, pageable memory makes them synchronous.  The caller synchronises
+ * `stream` before reading host_scores, and keeps host_cube unchanged until then. */
 wdad_status wdad_detect_all_host(wdad_handle h, const float* host_cube, int H, int W, int L, int reduce,
                                  int nwin, const wdad_params* params, float* host_scores, void* stream);
+
+/* A1-A5 over a sequence of n cubes of one shape (a stream of scenes), reduced path only:
+ * for each cube the DWT approximation and all three detectors at nwin windows, maps
+ * bit-identical to wdad_detect_windows(reduce = 1) of that cube.  The DWT of cube i runs on
+ * a stream the handle owns (created at the device's highest priority) beside the detector
+ * launch of cube i - 1 on `stream`, through two approximation buffers in the handle's
+ * workspace (2 H W K floats).  The DWT kernel is the standalone one, launched on three
+ * quarters of the SMs with an unused shared-memory reservation (at most 100 KiB) that leaves
+ * room for one detector CTA beside each of its CTAs, so that the two launches share SMs.
+ *   - cubes: host array of n device pointers, each [H][W][L] float32, 16-byte aligned.
+ *   - outs: host array of n device pointers, each [nwin][3][H][W] float32 (LRX, DWRX, DWEST);
+ *     entries may repeat (the detector launches run in order on `stream`).
+ *   - events: NULL, or a host array of 4 n entries, each a cudaEvent_t the caller created or
+ *     NULL: for cube i, events[4i] and [4i+1] are recorded around its DWT (on the handle's
+ *     stream) and [4i+2], [4i+3] around its detector launch (on `stream`).  Each recorded
+ *     timing event costs a few microseconds of overlap; record a sample.
+ *   - The call enqueues everything and returns; the work is complete when `stream` reaches
+ *     the point after the call.  The cubes must stay unchanged until then.  n = 0 does
+ *     nothing.  Windows as for wdad_detect_windows (nwin 1..64, one wavelet and level). */
+wdad_status wdad_detect_sequence(wdad_handle h, int n, const float* const* cubes, int H, int W, int L, int nwin,
+                                 const wdad_params* params, float* const* outs, void* const* events, void* stream);
 
 /* A3 — background statistics of listed pixels (Sec. 2.1, Sec. 2.2): mean mu_o and covariance
  * C_o = (1/N) sum (x - mu_o)(x - mu_o)^T over the annulus between p->inner and p->outer

@@ -30,6 +30,11 @@ struct wdad_ctx {
     // second stream and events of the host entry point's row-band pipeline
     cudaStream_t aux = nullptr, aux2 = nullptr;
     std::vector<cudaEvent_t> evs;
+    // the sequence entry point: its DWT stream (highest priority), ordering events and the
+    // DWT's grid
+    cudaStream_t seq = nullptr;
+    cudaEvent_t seq_ev[5] = {};
+    int seq_dwt_ctas = 0;
     std::string err;
 };
 
@@ -430,6 +435,7 @@ wdad_status wdad_create(wdad_handle* out, int device) {
     h->device = device;
     if (cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
         h->num_sms = 1;
+    h->seq_dwt_ctas = std::max(1, 3 * h->num_sms / 4);
     *out = h;
     return WDAD_OK;
 }
@@ -444,6 +450,9 @@ wdad_status wdad_destroy(wdad_handle h) {
         for (auto e : h->evs) cudaEventDestroy(e);
         if (h->aux) cudaStreamDestroy(h->aux);
         if (h->aux2) cudaStreamDestroy(h->aux2);
+        for (auto e : h->seq_ev)
+            if (e) cudaEventDestroy(e);
+        if (h->seq) cudaStreamDestroy(h->seq);
     }
     delete h;
     return WDAD_OK;
@@ -606,6 +615,98 @@ wdad_status wdad_detect_windows(wdad_handle h, const float* cube, int H, int W, 
             x = xr;
         }
         return detect_windows(h, x, H, W, D, nwin, params, scores, flags, (char*)h->ws + b_red, full, s);
+    } catch (...) {
+        return fail(h, WDAD_ERR_NOMEM, "host exception");
+    }
+}
+
+// A sequence of cubes: cube i's DWT on the handle's high-priority stream beside cube i - 1's
+// detector launch on the caller's stream, through two approximation buffers.  Cube i's DWT
+// (buffer i % 2) waits for cube i - 2's detectors, which read that buffer; cube i's detectors
+// wait for its DWT.  The DWT kernel is launched on three quarters of the SMs with a shared
+// memory reservation that leaves room for exactly one detector CTA beside each of its CTAs:
+// launched the ordinary way (two register-heavy DWT CTAs per SM) it fills SMs the detector
+// launch then cannot use, and the two launches take as long as one after the other.
+wdad_status wdad_detect_sequence(wdad_handle h, int n, const float* const* cubes, int H, int W, int L, int nwin,
+                                 const wdad_params* params, float* const* outs, void* const* events, void* stream) {
+    if (!h) return WDAD_ERR_ARG;
+    if (n < 0 || (n > 0 && (!cubes || !outs))) return fail(h, WDAD_ERR_ARG, "n >= 0 with cubes[n] and outs[n]");
+    if (nwin < 1 || nwin > 64 || !params) return fail(h, WDAD_ERR_ARG, "nwin must be 1..64 with params[nwin]");
+    try {
+        DeviceGuard g(h->device);
+        for (int w = 0; w < nwin; ++w) {
+            wdad_status st = check_params(h, &params[w]);
+            if (st != WDAD_OK) return st;
+            if (params[w].wavelet_taps != params[0].wavelet_taps || params[w].level != params[0].level)
+                return fail(h, WDAD_ERR_ARG, "all windows of one call share the wavelet and level");
+        }
+        for (int i = 0; i < n; ++i) {
+            wdad_status st = check_cube(h, cubes[i], H, W, L);
+            if (st != WDAD_OK) return st;
+            if (!outs[i]) return fail(h, WDAD_ERR_ARG, "outs[%d] is NULL", i);
+        }
+        const int64_t P = (int64_t)H * W;
+        if (n == 0 || P == 0) return WDAD_OK;
+        const int D = wdad_query_K(L, params[0].wavelet_taps, params[0].level);
+        if (D < 1 || D > 8) return fail(h, WDAD_ERR_UNSUPPORTED, "the sequence entry point runs the reduced path (K <= 8)");
+        size_t det_smem = 0;
+        for (int w = 0; w < nwin; ++w) {
+            const int th = wdad::detect_small_default_th(D, params[w].inner, params[w].outer);
+            if (th == 0)
+                return fail(h, WDAD_ERR_UNSUPPORTED, "window %d/%d too large for %d bands", params[w].inner,
+                            params[w].outer, D);
+            det_smem = std::max(det_smem, wdad::detect_small_smem(D, params[w].inner, params[w].outer, th));
+        }
+        const size_t b_red = align256(sizeof(float) * (size_t)P * D);
+        wdad_status st = ensure_ws(h, 2 * b_red);
+        if (st != WDAD_OK) return st;
+        cudaStream_t s = (cudaStream_t)stream;
+        const float* A = nullptr;
+        int k2 = 0;
+        st = get_dwt_plan(h, L, params[0].wavelet_taps, params[0].level, &A, &k2, s);
+        if (st != WDAD_OK) return st;
+        cudaError_t e = cudaSuccess;
+        if (!h->seq) {
+            int lo = 0, hi = 0;
+            e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+            if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->seq, cudaStreamNonBlocking, hi);
+            if (e != cudaSuccess) return cuda_fail(h, e, "sequence stream");
+        }
+        for (auto& ev : h->seq_ev)
+            if (!ev && (e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+                return cuda_fail(h, e, "sequence events");
+        // the DWT's reservation: at most 100 KiB (measured on the 512 x 512 x 224 workload, where
+        // 100 KiB and 3/4 of the SMs gave the shortest step), and no more than what an SM keeps
+        // beside one detector CTA: 228 KiB less the runtime's 1 KiB per CTA and the detector's
+        // dynamic and static shared memory
+        const size_t sm_total = 228 * 1024, overhead = 2 * 1024 + 512;
+        const size_t room = det_smem + overhead < sm_total ? sm_total - det_smem - overhead : 0;
+        const size_t reserve = std::min<size_t>(room, 100 * 1024);
+        float* red[2] = {(float*)h->ws, (float*)((char*)h->ws + b_red)};
+        cudaEvent_t ev_start = h->seq_ev[0], *dwt_done = h->seq_ev + 1, *det_done = h->seq_ev + 3;
+        auto user_ev = [&](int i, int k) { return events ? (cudaEvent_t)events[4 * (size_t)i + k] : nullptr; };
+        // the previous call's work on the caller's stream (detectors reading the buffers) first
+        e = cudaEventRecord(ev_start, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->seq, ev_start, 0);
+        for (int i = 0; i < n && e == cudaSuccess; ++i) {
+            const int b = i & 1;
+            if (i >= 2) e = cudaStreamWaitEvent(h->seq, det_done[b], 0);
+            if (e == cudaSuccess && user_ev(i, 0)) e = cudaEventRecord(user_ev(i, 0), h->seq);
+            if (e == cudaSuccess)
+                e = wdad::launch_dwt_approx_beside(cubes[i], P, L, A, D, red[b], h->num_sms, h->seq_dwt_ctas, reserve,
+                                                   h->seq);
+            if (e == cudaSuccess && user_ev(i, 1)) e = cudaEventRecord(user_ev(i, 1), h->seq);
+            if (e == cudaSuccess) e = cudaEventRecord(dwt_done[b], h->seq);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, dwt_done[b], 0);
+            if (e == cudaSuccess && user_ev(i, 2)) e = cudaEventRecord(user_ev(i, 2), s);
+            if (e != cudaSuccess) break;
+            st = detect_windows(h, red[b], H, W, D, nwin, params, outs[i], nullptr, nullptr, 0, s);
+            if (st != WDAD_OK) return st;
+            if (user_ev(i, 3)) e = cudaEventRecord(user_ev(i, 3), s);
+            if (e == cudaSuccess) e = cudaEventRecord(det_done[b], s);
+        }
+        if (e != cudaSuccess) return cuda_fail(h, e, "sequence launches");
+        return WDAD_OK;
     } catch (...) {
         return fail(h, WDAD_ERR_NOMEM, "host exception");
     }

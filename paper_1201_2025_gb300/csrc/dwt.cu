@@ -11,6 +11,9 @@
 // PX*K results leave as one coalesced store.  The lane partial sums plus the tree
 // of shuffles keep the FP32 rounding error near sqrt(L) ulp instead of L ulp.
 #include <complex>
+#include <mutex>
+#include <set>
+#include <utility>
 #include <vector>
 
 #include "dwt_dev.cuh"
@@ -129,9 +132,34 @@ bool dwt_shape_supported(int L, int K) {
     return (L + 31) / 32 <= (K <= 4 ? 8 : 4);
 }
 
+// The dynamic shared memory limit of a DWT kernel is raised once per kernel and device to the
+// opt-in maximum, so that a launch with a reservation (launch_dwt_approx_beside) never races
+// with another thread's setting.
+template <class Kern>
+static cudaError_t allow_reservation(Kern* kernel) {
+    static std::mutex mu;
+    static std::set<std::pair<const void*, int>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    const auto key = std::make_pair(reinterpret_cast<const void*>(kernel), dev);
+    if (done.count(key)) return cudaSuccess;
+    int optin = 0;
+    cudaFuncAttributes fa{};
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+    if (e == cudaSuccess) done.insert(key);
+    return e;
+}
+
+// ctas > 0 caps the grid at that many CTAs; reserve > 0 launches with that much dynamic shared
+// memory, which the kernel does not use: it only limits how many CTAs share an SM.
 template <int VEC, int NCH, int KP>
 static cudaError_t launch_one(const float* cube, int64_t P, int L, const float* A, int K, float* out, int num_sms,
-                              cudaStream_t s) {
+                              cudaStream_t s, int ctas, size_t reserve) {
     constexpr int PX = px_per_step(NCH, KP);
     static int blocks_per_sm = 0;
     if (blocks_per_sm == 0) {
@@ -140,50 +168,65 @@ static cudaError_t launch_one(const float* cube, int64_t P, int L, const float* 
     }
     const int64_t ngroups = (P + PX - 1) / PX;
     int64_t grid = (ngroups + 7) / 8;
-    const int64_t cap = (int64_t)num_sms * blocks_per_sm;
+    const int64_t cap = ctas > 0 ? (int64_t)ctas : (int64_t)num_sms * blocks_per_sm;
     if (grid > cap) grid = cap;
     if (grid < 1) grid = 1;
-    dwt_apply_kernel<VEC, NCH, KP><<<(unsigned)grid, 256, 0, s>>>(cube, P, L, A, K, out);
+    if (reserve > 0) {
+        cudaError_t e = allow_reservation(dwt_apply_kernel<VEC, NCH, KP>);
+        if (e != cudaSuccess) return e;
+    }
+    dwt_apply_kernel<VEC, NCH, KP><<<(unsigned)grid, 256, reserve, s>>>(cube, P, L, A, K, out);
     return cudaGetLastError();
 }
 
 // Instantiated (VEC, NCH, KP) combinations; dwt_shape_supported() admits exactly these.
 template <int VEC, int KP>
 static cudaError_t dispatch_nch(int nch, const float* cube, int64_t P, int L, const float* A, int K, float* out,
-                                int num_sms, cudaStream_t s) {
-    if (nch <= 1) return launch_one<VEC, 1, KP>(cube, P, L, A, K, out, num_sms, s);
-    if (nch <= 2) return launch_one<VEC, 2, KP>(cube, P, L, A, K, out, num_sms, s);
+                                int num_sms, cudaStream_t s, int ctas, size_t reserve) {
+    if (nch <= 1) return launch_one<VEC, 1, KP>(cube, P, L, A, K, out, num_sms, s, ctas, reserve);
+    if (nch <= 2) return launch_one<VEC, 2, KP>(cube, P, L, A, K, out, num_sms, s, ctas, reserve);
     if constexpr (VEC == 4 && KP == 8) return cudaErrorInvalidValue;
-    if (nch <= 3) return launch_one<VEC, 3, KP>(cube, P, L, A, K, out, num_sms, s);
-    if (nch <= 4) return launch_one<VEC, 4, KP>(cube, P, L, A, K, out, num_sms, s);
+    if (nch <= 3) return launch_one<VEC, 3, KP>(cube, P, L, A, K, out, num_sms, s, ctas, reserve);
+    if (nch <= 4) return launch_one<VEC, 4, KP>(cube, P, L, A, K, out, num_sms, s, ctas, reserve);
     if constexpr (KP <= 4) {
-        if (nch <= 6) return launch_one<VEC, 6, KP>(cube, P, L, A, K, out, num_sms, s);
-        if (nch <= 8) return launch_one<VEC, 8, KP>(cube, P, L, A, K, out, num_sms, s);
+        if (nch <= 6) return launch_one<VEC, 6, KP>(cube, P, L, A, K, out, num_sms, s, ctas, reserve);
+        if (nch <= 8) return launch_one<VEC, 8, KP>(cube, P, L, A, K, out, num_sms, s, ctas, reserve);
     }
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_dwt_approx(const float* cube, int64_t P, int L, const float* A, int K, float* approx, int num_sms,
-                              cudaStream_t s) {
+static cudaError_t dwt_dispatch(const float* cube, int64_t P, int L, const float* A, int K, float* approx,
+                                int num_sms, cudaStream_t s, int ctas, size_t reserve) {
     if (P == 0) return cudaSuccess;
     if (!dwt_shape_supported(L, K)) return cudaErrorInvalidValue;
     const int kp = kpad(K);
     if (L % 4 == 0) {
         const int nch = (L / 4 + 31) / 32;
         switch (kp) {
-            case 1: return dispatch_nch<4, 1>(nch, cube, P, L, A, K, approx, num_sms, s);
-            case 2: return dispatch_nch<4, 2>(nch, cube, P, L, A, K, approx, num_sms, s);
-            case 4: return dispatch_nch<4, 4>(nch, cube, P, L, A, K, approx, num_sms, s);
-            default: return dispatch_nch<4, 8>(nch, cube, P, L, A, K, approx, num_sms, s);
+            case 1: return dispatch_nch<4, 1>(nch, cube, P, L, A, K, approx, num_sms, s, ctas, reserve);
+            case 2: return dispatch_nch<4, 2>(nch, cube, P, L, A, K, approx, num_sms, s, ctas, reserve);
+            case 4: return dispatch_nch<4, 4>(nch, cube, P, L, A, K, approx, num_sms, s, ctas, reserve);
+            default: return dispatch_nch<4, 8>(nch, cube, P, L, A, K, approx, num_sms, s, ctas, reserve);
         }
     }
     const int nch = (L + 31) / 32;
     switch (kp) {
-        case 1: return dispatch_nch<1, 1>(nch, cube, P, L, A, K, approx, num_sms, s);
-        case 2: return dispatch_nch<1, 2>(nch, cube, P, L, A, K, approx, num_sms, s);
-        case 4: return dispatch_nch<1, 4>(nch, cube, P, L, A, K, approx, num_sms, s);
-        default: return dispatch_nch<1, 8>(nch, cube, P, L, A, K, approx, num_sms, s);
+        case 1: return dispatch_nch<1, 1>(nch, cube, P, L, A, K, approx, num_sms, s, ctas, reserve);
+        case 2: return dispatch_nch<1, 2>(nch, cube, P, L, A, K, approx, num_sms, s, ctas, reserve);
+        case 4: return dispatch_nch<1, 4>(nch, cube, P, L, A, K, approx, num_sms, s, ctas, reserve);
+        default: return dispatch_nch<1, 8>(nch, cube, P, L, A, K, approx, num_sms, s, ctas, reserve);
     }
+}
+
+cudaError_t launch_dwt_approx(const float* cube, int64_t P, int L, const float* A, int K, float* approx, int num_sms,
+                              cudaStream_t s) {
+    return dwt_dispatch(cube, P, L, A, K, approx, num_sms, s, 0, 0);
+}
+
+cudaError_t launch_dwt_approx_beside(const float* cube, int64_t P, int L, const float* A, int K, float* approx,
+                                     int num_sms, int ctas, size_t reserve, cudaStream_t s) {
+    if (ctas < 1) return cudaErrorInvalidValue;
+    return dwt_dispatch(cube, P, L, A, K, approx, num_sms, s, ctas, reserve);
 }
 
 }  // namespace wdad

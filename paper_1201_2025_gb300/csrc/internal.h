@@ -41,6 +41,11 @@ cudaError_t build_dwt_matrix(int L, int taps, int J, int K, float* A, double* sc
 cudaError_t launch_dwt_approx(const float* cube, int64_t P, int L, const float* A, int K, float* approx,
                               int num_sms, cudaStream_t s);
 bool dwt_shape_supported(int L, int K);
+// The same kernel shaped to run beside another launch: at most ctas CTAs, each launched with
+// `reserve` bytes of dynamic shared memory that it does not use, which bounds how many of its
+// CTAs share an SM (and so leaves room for the other launch's CTAs).  Same coefficients.
+cudaError_t launch_dwt_approx_beside(const float* cube, int64_t P, int L, const float* A, int K, float* approx,
+                                     int num_sms, int ctas, size_t reserve, cudaStream_t s);
 
 // ---- A2-A5: detectors on few bands (dim <= 8, the DWT-reduced cube) ---------
 struct DetectArgs {

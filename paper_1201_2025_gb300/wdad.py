@@ -94,6 +94,7 @@ def lib() -> ctypes.CDLL:
     L.wdad_wavelet_filter.argtypes = [i32, vp]
     L.wdad_global_rx.argtypes = [vp, f32p, i32, i32, i32, i32, pp, f32p, vp]
     L.wdad_detect_windows.argtypes = [vp, f32p, i32, i32, i32, i32, i32, pp, f32p, vp, vp]
+    L.wdad_detect_sequence.argtypes = [vp, i32, vp, i32, i32, i32, i32, pp, vp, vp, vp]
     for name in ("wdad_create", "wdad_destroy", "wdad_last_error_detail", "wdad_dwt_approx", "wdad_detect",
                  "wdad_detect_all", "wdad_detect_all_host", "wdad_window_census", "wdad_auc",
                  "wdad_detect_all_noalloc", "wdad_window_moments", "wdad_autotune", "wdad_batch_create",
@@ -101,7 +102,7 @@ def lib() -> ctypes.CDLL:
                  "wdad_cnn_create", "wdad_cnn_destroy", "wdad_cnn_set_norm", "wdad_cnn_params",
                  "wdad_cnn_set_params", "wdad_cnn_forward", "wdad_cnn_grad", "wdad_cnn_train", "wdad_cnn_save",
                  "wdad_cnn_load", "wdad_screen_run", "wdad_scene_whitening", "wdad_adaptive_threshold",
-                 "wdad_wavelet_filter", "wdad_global_rx", "wdad_detect_windows"):
+                 "wdad_wavelet_filter", "wdad_global_rx", "wdad_detect_windows", "wdad_detect_sequence"):
         getattr(L, name).restype = i32
     L.wdad_query_K.restype = i32
     _lib = L
@@ -270,6 +271,49 @@ def wdad_detect_all(cube, reduce: bool = True, params: wdad_params | None = None
     _check(lib().wdad_detect_all(h, cube.data_ptr(), H, W, L, int(bool(reduce)), ctypes.byref(p), out.data_ptr(),
                                  flags.data_ptr() if flags is not None else None, _stream(cube)), h)
     return out
+
+
+def wdad_detect_sequence(cubes, params, outs=None, events=None):
+    """All three detectors at several windows on each cube of a sequence (reduced path), the
+    DWT of each cube overlapping the previous cube's detectors: a list of [nwin, 3, H, W]
+    float32 tensors, one per cube, equal to wdad_detect_windows(cube, params) bit for bit.
+    cubes: device tensors [H, W, L] of one shape; outs: optional list of result tensors
+    (entries may repeat); events: optional list of 4 n torch.cuda.Event or None (per cube:
+    DWT start, DWT end on the library's stream; detector start, end on torch's current
+    stream)."""
+    import torch
+    cubes = [_cube(c) for c in cubes]
+    n = len(cubes)
+    plist = list(params)
+    nwin = len(plist)
+    arr = (wdad_params * nwin)(*plist)
+    if n == 0:
+        return []
+    H, W, L = cubes[0].shape
+    dev = cubes[0].device
+    for c in cubes:
+        if tuple(c.shape) != (H, W, L) or c.device != dev:
+            raise ValueError("all cubes of a sequence share one shape and device")
+    if outs is None:
+        outs = [torch.empty((nwin, 3, H, W), device=dev, dtype=torch.float32) for _ in range(n)]
+    if len(outs) != n:
+        raise ValueError(f"outs must hold {n} tensors")
+    for o in outs:
+        _check_out(o, (nwin, 3, H, W), torch.float32, dev)
+    cp = (ctypes.c_void_p * n)(*[c.data_ptr() for c in cubes])
+    op = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
+    ep = None
+    if events is not None:
+        if len(events) != 4 * n:
+            raise ValueError(f"events must hold {4 * n} torch.cuda.Event")
+        stream = torch.cuda.current_stream(dev)
+        for e in events:
+            if e is not None and not e.cuda_event:  # torch creates the CUDA event on its first record
+                e.record(stream)
+        ep = (ctypes.c_void_p * (4 * n))(*[e.cuda_event if e is not None else None for e in events])
+    h = handle(dev.index or 0)
+    _check(lib().wdad_detect_sequence(h, n, cp, H, W, L, nwin, arr, op, ep, _stream(cubes[0])), h)
+    return outs
 
 
 def wdad_detect_all_host(cube, reduce: bool = True, params=None, out=None, device: int = 0, **over):
