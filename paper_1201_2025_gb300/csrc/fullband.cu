@@ -166,41 +166,67 @@ __host__ __device__ inline size_t fb_smem_vectors_bytes(int Dp, int S, int mcap)
 constexpr size_t kTcBufBytes = 2 * 256 * 64 * 2;  // two BF16 chunk buffers (TC_MB x TC_KC)
 
 // ---- statistics ---------------------------------------------------------------
-// mean over a sample list (kind 0 = background, 1 = inner) into out[0..Dp).  The samples
-// are split into G interleaved groups (G threads per band, G <= S so that the partial sums
-// fit the sample-chunk buffer `part`); each thread keeps eight loads in flight, and the G
-// partial sums of a band are added in group order.  Ends with a barrier.
+// pixel index of sample s of a list (kind 0 = background, 1 = inner) around (py, px)
+__device__ __forceinline__ int sample_pixel(int s, int kind, int H, int W, int py, int px, int ro, int ri) {
+    int dy, dx;
+    if (kind == 0) bg_offset(s, ro, ri, dy, dx); else in_offset(s, ri, dy, dx);
+    return reflect101(py + dy, H) * W + reflect101(px + dx, W);
+}
+
+// mean over a sample list (kind 0 = background, 1 = inner) into out[0..Dp).  Thread t takes
+// the band quad t % Q (Q = Dp / 4) of the samples t / Q, t / Q + G, ... (G groups, G <= S so
+// that the partial sums fit the sample-chunk buffer `part`), eight 16-byte loads in flight; the
+// samples' pixel indices come from a shared-memory list filled 256 at a time, and the G partial
+// sums of a band are added in group order.  Ends with a barrier.
+constexpr int kMeanChunk = 256;
 template <typename T>
 __device__ void sample_mean(const float* __restrict__ x, int H, int W, const Geo& g, int py, int px, int kind,
                             int n, int ro, int ri, T* out, T* part) {
-    const int D = g.D, Dp = g.Dp;
-    const int G = max(1, min(FB_THREADS / Dp, g.S));
-    __syncthreads();  // part may still be read by a previous call
-    for (int t = threadIdx.x; t < G * Dp; t += FB_THREADS) {
-        const int grp = t / Dp, b = t - grp * Dp;
-        T acc[4] = {T(0), T(0), T(0), T(0)};
-        if (b < D) {
-            int s = grp;
-            for (; s + 7 * G < n; s += 8 * G) {
-                float v[8];
+    __shared__ int s_q[kMeanChunk];
+    const int D = g.D, Dp = g.Dp, Q = Dp / 4;
+    const int G = max(1, min(FB_THREADS / Q, g.S));
+    const int grp = threadIdx.x / Q, c = threadIdx.x - grp * Q;
+    const bool active = grp < G;
+    const bool vec = (D & 3) == 0;
+    T acc[4] = {T(0), T(0), T(0), T(0)};
+    auto load4 = [&](int q, float (&v)[4]) {
+        const float* src = x + (size_t)q * D + 4 * c;
+        if (vec) {
+            const float4 t = __ldg(reinterpret_cast<const float4*>(src));
+            v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+        } else {
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    int dy, dx;
-                    if (kind == 0) bg_offset(s + u * G, ro, ri, dy, dx); else in_offset(s + u * G, ri, dy, dx);
-                    const size_t q = (size_t)reflect101(py + dy, H) * W + reflect101(px + dx, W);
-                    v[u] = __ldg(x + q * D + b);
-                }
+            for (int e = 0; e < 4; ++e) v[e] = 4 * c + e < D ? __ldg(src + e) : 0.f;
+        }
+    };
+    __syncthreads();  // part and s_q may still be read by a previous call
+    for (int s0 = 0; s0 < n; s0 += kMeanChunk) {
+        const int m = min(kMeanChunk, n - s0);
+        for (int i = threadIdx.x; i < m; i += FB_THREADS) s_q[i] = sample_pixel(s0 + i, kind, H, W, py, px, ro, ri);
+        __syncthreads();
+        if (active && 4 * c < D) {
+            int i = grp;
+            for (; i + 7 * G < m; i += 8 * G) {
+                float v[8][4];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) acc[u & 3] += (T)v[u];
+                for (int u = 0; u < 8; ++u) load4(s_q[i + u * G], v[u]);
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) acc[e] += (T)v[u][e];
             }
-            for (; s < n; s += G) {
-                int dy, dx;
-                if (kind == 0) bg_offset(s, ro, ri, dy, dx); else in_offset(s, ri, dy, dx);
-                const size_t q = (size_t)reflect101(py + dy, H) * W + reflect101(px + dx, W);
-                acc[0] += (T)__ldg(x + q * D + b);
+            for (; i < m; i += G) {
+                float v[4];
+                load4(s_q[i], v);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[e] += (T)v[e];
             }
         }
-        part[t] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+        __syncthreads();  // before s_q is refilled
+    }
+    if (active) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) part[grp * Dp + 4 * c + e] = acc[e];
     }
     __syncthreads();
     for (int b = threadIdx.x; b < Dp; b += FB_THREADS) {
@@ -287,6 +313,7 @@ __device__ void gram_tc(const float* __restrict__ x, int H, int W, const Geo& g,
     const int MT = (g.Dp + 127) / 128;  // 1 or 2 band tiles
     const int nchunk = (n + TC_KC - 1) / TC_KC;
     const uint32_t id128 = tc::idesc_bf16_f32(128, 128), id256 = tc::idesc_bf16_f32(128, 256);
+    __shared__ int s_q[2][TC_KC];  // pixel index of each sample of a chunk (by chunk parity)
     for (int c = 0; c < nchunk; ++c) {
         const int b = c & 1;
         // the tensor cores must be done with this buffer (chunk c - 2)
@@ -294,6 +321,8 @@ __device__ void gram_tc(const float* __restrict__ x, int H, int W, const Geo& g,
             if (!tc::mbar_wait_bounded(&st.bar[b], st.uses[b] & 1, TC_WAIT)) *st.err = 1;
             ++st.uses[b];
         }
+        if (threadIdx.x < TC_KC && c * TC_KC + (int)threadIdx.x < n)
+            s_q[b][threadIdx.x] = sample_pixel(c * TC_KC + threadIdx.x, kind, H, W, py, px, ro, ri);
         __syncthreads();
         if (*st.err) return;
         // fill: one task = 8 consecutive samples x 32 consecutive bands (lane = band)
@@ -308,12 +337,7 @@ __device__ void gram_tc(const float* __restrict__ x, int H, int W, const Geo& g,
             for (int e = 0; e < 8; ++e) {
                 const int s = c * TC_KC + so + e;
                 float val = 0.f;
-                if (s < n && band < g.D) {
-                    int dy, dx;
-                    if (kind == 0) bg_offset(s, ro, ri, dy, dx); else in_offset(s, ri, dy, dx);
-                    const size_t q = (size_t)reflect101(py + dy, H) * W + reflect101(px + dx, W);
-                    val = __ldg(x + q * g.D + band) - m;
-                }
+                if (s < n && band < g.D) val = __ldg(x + (size_t)s_q[b][so + e] * g.D + band) - m;
                 v[e] = __float2bfloat16_rn(val);
             }
             *reinterpret_cast<uint4*>(reinterpret_cast<char*>(buf) + tc_off(band, so)) =
