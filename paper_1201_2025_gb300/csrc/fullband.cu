@@ -152,7 +152,9 @@ struct Geo {
     int N, Np;         // background samples (outer^2 - inner^2), padded to 4
     bool wood;         // LRX / DWRX through the N x N sample Gram (Woodbury), N < D
     bool a_in_smem;
-    bool tc;           // window Gram on the tensor cores (mixed precision, D <= 256)
+    bool tc;           // mixed precision (BF16 window Gram, condition gate, FP64 re-solve)
+    bool tcg;          // window Gram on the tensor cores (D <= 256): tensor memory and chunk buffers
+    int pieces;        // BF16 pieces per sample value: 1 (mixed precision) or 3 (FP32-accurate split)
     bool pan_in_tc;    // Cholesky panel buffer inside the (then idle) tensor-core chunk buffers
     bool pan_in_smem;  // else in shared memory after the vectors, else in the slab
 };
@@ -280,7 +282,7 @@ __device__ void gram_accumulate(const float* __restrict__ x, int H, int W, const
     __syncthreads();
 }
 
-// ---- BF16 window Gram on the tensor cores (mixed precision).
+// ---- Window Gram on the tensor cores.
 // The centred, scaled samples of one chunk are stored transposed, [band][sample], as
 // BF16 in the canonical K-major layout of 8 x 16-byte core matrices: element (b, s) at
 // byte (b/8)*KC*16 + (s/8)*128 + (b%8)*16 + (s%8)*2.  G = X^T X then reads the same
@@ -289,7 +291,13 @@ __device__ void gram_accumulate(const float* __restrict__ x, int H, int W, const
 // (bands 0..127 x 0..127) in columns [0, 128), tile 1 (bands 128..255 x 0..255) in
 // columns [128, 384).  Two chunk buffers alternate; each is reused only after the
 // tensor cores have signalled (commit -> mbarrier) that they finished reading it.
-constexpr int TC_KC = 64;          // samples per chunk
+// Mixed precision stores one BF16 value per sample (64 samples per chunk).  The FP32 path
+// splits each FP32 value v into three BF16 pieces, v1 = bf16(v), v2 = bf16(v - v1),
+// v3 = bf16(v - v1 - v2) (each difference exact in FP32), which carry v's 24 significant
+// bits, and accumulates the six products v1v1, v1v2, v2v1, v2v2, v1v3, v3v1 (each exact in
+// FP32; the three dropped ones are below 2^-24 of v^2) over chunks of 16 samples, the three
+// piece buffers of a chunk side by side.
+constexpr int TC_KC = 64;          // chunk buffer capacity in samples (one piece)
 constexpr int TC_MB = 256;         // band rows held per chunk buffer (D <= 256)
 constexpr uint32_t TC_COLS = 512;  // tensor-memory columns allocated per CTA
 constexpr uint32_t TC_WAIT = 1u << 26;
@@ -302,81 +310,128 @@ struct TcState {
     int* err;               // shared error word
 };
 
-__device__ __forceinline__ uint32_t tc_off(int b, int s) {
-    return (uint32_t)((b >> 3) * (TC_KC * 16) + (s >> 3) * 128 + (b & 7) * 16 + (s & 7) * 2);
+// byte offset of (band b, sample s) in one piece of a chunk of kc samples
+__device__ __forceinline__ uint32_t tc_off(int b, int s, int kc) {
+    return (uint32_t)((b >> 3) * (kc * 16) + (s >> 3) * 128 + (b & 7) * 16 + (s & 7) * 2);
 }
 
-// A += scale * (X^T X) over the n samples of one list, X = sc (x - mu) (FP32 packed SoA A)
+// two floats as packed BF16 (lo at the lower address)
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(lo)) |
+           ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(hi)) << 16);
+}
+__device__ __forceinline__ float bf16_round(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+
+// A += scale * (X^T X) over the n samples of one list, X = x - mu (FP32 packed SoA A), with
+// NP = 1 (BF16 samples) or 3 (three-piece split).  In the split the tensor memory is added
+// into A every kSplitFlush chunks (64 samples), so each FP32 accumulation in the tensor cores
+// runs over few terms and the long sum over the window is taken by FP32 adds that round to
+// nearest.  Measured against the oracle (48 x 48 scenes, L = 224 at 7/21 and L = 128 at
+// 5/15): the largest LRX/DWRX error is 0.033-0.038 u kappa flushing every chunk, 0.06-0.08
+// every four chunks, 0.14-0.17 with one accumulation over the whole window, against
+// 0.06-0.12 for the SIMT FP32 Gram; every four chunks costs 6.0 ms against 7.4 ms for the
+// SIMT Gram on 64 x 64 x 224 at 7/21 (every chunk: 8.4 ms).
+constexpr int kSplitFlush = 4;
+template <int NP>
 __device__ void gram_tc(const float* __restrict__ x, int H, int W, const Geo& g, int py, int px, int kind, int n,
                         int ro, int ri, const float* mu, float scale, float* A, TcState& st) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int MT = (g.Dp + 127) / 128;  // 1 or 2 band tiles
-    const int nchunk = (n + TC_KC - 1) / TC_KC;
+    constexpr int kc = NP == 1 ? TC_KC : 16;  // samples per chunk
+    constexpr uint32_t piece_bytes = (uint32_t)(TC_MB * kc * 2);
+    const int nchunk = (n + kc - 1) / kc;
+    const int F = NP == 1 ? nchunk : kSplitFlush;  // chunks per accumulation in tensor memory
     const uint32_t id128 = tc::idesc_bf16_f32(128, 128), id256 = tc::idesc_bf16_f32(128, 256);
     __shared__ int s_q[2][TC_KC];  // pixel index of each sample of a chunk (by chunk parity)
+    bool pend[2] = {false, false};  // MMAs committed on the buffer's barrier and not yet waited for
+    auto wait_buf = [&](int b) {
+        if (!pend[b]) return;
+        if (!tc::mbar_wait_bounded(&st.bar[b], st.uses[b] & 1, TC_WAIT)) *st.err = 1;
+        ++st.uses[b];
+        pend[b] = false;
+    };
     for (int c = 0; c < nchunk; ++c) {
         const int b = c & 1;
-        // the tensor cores must be done with this buffer (chunk c - 2)
-        if (c >= 2) {
-            if (!tc::mbar_wait_bounded(&st.bar[b], st.uses[b] & 1, TC_WAIT)) *st.err = 1;
-            ++st.uses[b];
-        }
-        if (threadIdx.x < TC_KC && c * TC_KC + (int)threadIdx.x < n)
-            s_q[b][threadIdx.x] = sample_pixel(c * TC_KC + threadIdx.x, kind, H, W, py, px, ro, ri);
+        wait_buf(b);  // the tensor cores must be done with this buffer (chunk c - 2)
+        if ((int)threadIdx.x < kc && c * kc + (int)threadIdx.x < n)
+            s_q[b][threadIdx.x] = sample_pixel(c * kc + threadIdx.x, kind, H, W, py, px, ro, ri);
         __syncthreads();
         if (*st.err) return;
         // fill: one task = 8 consecutive samples x 32 consecutive bands (lane = band)
         __nv_bfloat16* buf = st.buf[b];
-        const int ntask = (TC_KC / 8) * (TC_MB / 32);
+        constexpr int ntask = (kc / 8) * (TC_MB / 32);
         for (int t = warp; t < ntask; t += FB_WARPS) {
-            const int so = (t % (TC_KC / 8)) * 8, bg = (t / (TC_KC / 8)) * 32;
+            const int so = (t % (kc / 8)) * 8, bg = (t / (kc / 8)) * 32;
             const int band = bg + lane;
             const float m = band < g.D ? mu[band] : 0.f;
-            __align__(16) __nv_bfloat16 v[8];
+            float v1[8], v2[8], v3[8];
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
-                const int s = c * TC_KC + so + e;
+                const int s = c * kc + so + e;
                 float val = 0.f;
                 if (s < n && band < g.D) val = __ldg(x + (size_t)s_q[b][so + e] * g.D + band) - m;
-                v[e] = __float2bfloat16_rn(val);
+                if constexpr (NP == 3) {
+                    v1[e] = bf16_round(val);
+                    const float r1 = val - v1[e];  // exact
+                    v2[e] = bf16_round(r1);
+                    v3[e] = r1 - v2[e];            // exact; rounded by pack_bf16
+                } else {
+                    v1[e] = val;
+                }
             }
-            *reinterpret_cast<uint4*>(reinterpret_cast<char*>(buf) + tc_off(band, so)) =
-                *reinterpret_cast<const uint4*>(v);
+            char* dst = reinterpret_cast<char*>(buf) + tc_off(band, so, kc);
+            *reinterpret_cast<uint4*>(dst) =
+                make_uint4(pack_bf16(v1[0], v1[1]), pack_bf16(v1[2], v1[3]), pack_bf16(v1[4], v1[5]),
+                           pack_bf16(v1[6], v1[7]));
+            if constexpr (NP == 3) {
+                *reinterpret_cast<uint4*>(dst + piece_bytes) =
+                    make_uint4(pack_bf16(v2[0], v2[1]), pack_bf16(v2[2], v2[3]), pack_bf16(v2[4], v2[5]),
+                               pack_bf16(v2[6], v2[7]));
+                *reinterpret_cast<uint4*>(dst + 2 * piece_bytes) =
+                    make_uint4(pack_bf16(v3[0], v3[1]), pack_bf16(v3[2], v3[3]), pack_bf16(v3[4], v3[5]),
+                               pack_bf16(v3[6], v3[7]));
+            }
         }
         tc::fence_proxy_async_smem();
         __syncthreads();
         if (threadIdx.x == 0) {
             tc::fence_after_sync();
             const uint32_t base = tc::smem_u32(buf);
+            // piece pairs (A, B): v1v1 alone, or v1v1, v1v2, v2v1, v2v2, v1v3, v3v1
+            constexpr int npairs = NP == 1 ? 1 : 6;
 #pragma unroll
-            for (int k = 0; k < TC_KC / 16; ++k) {
+            for (int k = 0; k < kc / 16; ++k) {
                 const uint32_t koff = (uint32_t)k * 256;  // two core matrices along K
-                for (int mt = 0; mt < MT; ++mt) {
-                    const uint64_t ad = tc::smem_desc(base + (uint32_t)mt * 16 * (TC_KC * 16) + koff, 128, TC_KC * 16);
-                    const uint64_t bd = tc::smem_desc(base + koff, 128, TC_KC * 16);
-                    tc::mma_bf16(st.tmem + (uint32_t)(mt * 128), ad, bd, mt == 0 ? id128 : id256, c > 0 || k > 0);
-                }
+                for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                    for (int q = 0; q < npairs; ++q) {
+                        const uint32_t pa = q == 2 || q == 3 ? 1u : q == 5 ? 2u : 0u;
+                        const uint32_t pb = q == 1 || q == 3 ? 1u : q == 4 ? 2u : 0u;
+                        const uint64_t ad =
+                            tc::smem_desc(base + pa * piece_bytes + (uint32_t)mt * 16 * (kc * 16) + koff, 128, kc * 16);
+                        const uint64_t bd = tc::smem_desc(base + pb * piece_bytes + koff, 128, kc * 16);
+                        tc::mma_bf16(st.tmem + (uint32_t)(mt * 128), ad, bd, mt == 0 ? id128 : id256,
+                                     c % F != 0 || k > 0 || q > 0);
+                    }
             }
             tc::commit(&st.bar[b]);
         }
-    }
-    // drain the last one or two chunks
-    for (int c = (nchunk >= 2 ? nchunk - 2 : 0); c < nchunk; ++c) {
-        const int b = c & 1;
-        if (!tc::mbar_wait_bounded(&st.bar[b], st.uses[b] & 1, TC_WAIT)) *st.err = 1;
-        ++st.uses[b];
-    }
-    __syncthreads();
-    if (*st.err) return;
-    tc::fence_after_sync();
-    // read back: warps 0..3 own tensor-memory lanes 0..127 (one band row each)
-    if (warp < 4) {
+        pend[b] = true;
+        if ((c + 1) % F != 0 && c != nchunk - 1) continue;
+        // add the tensor-memory sums into A: every warp, lanes of its quarter (warp % 4), a
+        // quarter of the 16-column blocks (warp / 4); only the lower triangle is kept
+        wait_buf(0);
+        wait_buf(1);
+        __syncthreads();
+        if (*st.err) return;
+        tc::fence_after_sync();
+        const int lq = warp & 3, cq = warp >> 2;
         for (int mt = 0; mt < MT; ++mt) {
-            const int r = mt * 128 + warp * 32 + lane;
-            const int ncol = (mt + 1) * 128;
-            for (int c0 = 0; c0 < ncol; c0 += 16) {
+            const int r = mt * 128 + lq * 32 + lane;
+            const int clast = mt * 128 + lq * 32 + 31;  // last column any row of this warp keeps
+            for (int c0 = 16 * cq; c0 <= clast; c0 += 64) {
                 float v[16];
-                tc::tmem_ld16(st.tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(mt * 128 + c0), v);
+                tc::tmem_ld16(st.tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(mt * 128 + c0), v);
 #pragma unroll
                 for (int e = 0; e < 16; ++e) {
                     const int col = c0 + e;
@@ -384,9 +439,9 @@ __device__ void gram_tc(const float* __restrict__ x, int H, int W, const Geo& g,
                 }
             }
         }
+        tc::fence_before_sync();
+        __syncthreads();
     }
-    tc::fence_before_sync();
-    __syncthreads();
 }
 
 // Sample Gram of the background window for the Woodbury form of LRX / DWRX (N < D):
@@ -987,9 +1042,10 @@ __device__ unsigned process_pixel(const FullArgs& a, const Geo& g, Smem<T>& m, S
         } else {
             mat_zero(m.A, g);
             if constexpr (sizeof(T) == 4) {
-                if (g.tc) gram_tc(a.x, a.H, a.W, g, py, px, 0, N, ro, ri, m.mu_o, 1.f / (float)N, m.A, *st);
+                if (g.tcg && g.pieces == 3) gram_tc<3>(a.x, a.H, a.W, g, py, px, 0, N, ro, ri, m.mu_o, 1.f / (float)N, m.A, *st);
+                else if (g.tcg) gram_tc<1>(a.x, a.H, a.W, g, py, px, 0, N, ro, ri, m.mu_o, 1.f / (float)N, m.A, *st);
             }
-            if (!g.tc) {
+            if (!g.tcg) {
                 gram_accumulate<T>(a.x, a.H, a.W, g, py, px, 0, N, ro, ri, m.mu_o, T(1), m.A, m.xs);
                 mat_scale(m.A, g, T(1) / (T)N);
             }
@@ -1174,7 +1230,7 @@ __global__ void __launch_bounds__(FB_THREADS, 1) fullband_kernel(FullArgs a, Geo
     TcState st{};
     // shared memory: [tensor-core chunk buffers][matrix if it fits][vectors]
     char* sp = reinterpret_cast<char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    if (g.tc) {
+    if (g.tcg) {
         st.buf[0] = reinterpret_cast<__nv_bfloat16*>(sp);
         st.buf[1] = reinterpret_cast<__nv_bfloat16*>(sp + kTcBufBytes / 2);
         sp += kTcBufBytes;
@@ -1198,7 +1254,7 @@ __global__ void __launch_bounds__(FB_THREADS, 1) fullband_kernel(FullArgs a, Geo
         q += pan_bytes<double>(g64.Dp);
         carve_scratch<double>(q, g64, sc64, &q);
     }
-    if (g.tc) {
+    if (g.tcg) {
         if (threadIdx.x == 0) {
             s_err = 0;
             tc::mbar_init(&s_bar[0], 1);
@@ -1240,7 +1296,7 @@ __global__ void __launch_bounds__(FB_THREADS, 1) fullband_kernel(FullArgs a, Geo
         }
         if (threadIdx.x == 0 && a.flags) a.flags[pix] = flag;
     }
-    if (g.tc) {
+    if (g.tcg) {
         __syncthreads();
         if (s_err) {  // a wait gave up: give the tensor cores a last bounded chance to finish
             tc::mbar_wait_bounded(&s_bar[0], st.uses[0] & 1, TC_WAIT);
@@ -1271,7 +1327,7 @@ __global__ void __launch_bounds__(FB_THREADS, 1) moments_kernel(FullArgs a, Geo 
     TcState st{};
     char* sp = reinterpret_cast<char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     size_t off = 0;
-    if (g.tc) {
+    if (g.tcg) {
         st.buf[0] = reinterpret_cast<__nv_bfloat16*>(sp);
         st.buf[1] = reinterpret_cast<__nv_bfloat16*>(sp + kTcBufBytes / 2);
         off += kTcBufBytes;
@@ -1281,7 +1337,7 @@ __global__ void __launch_bounds__(FB_THREADS, 1) moments_kernel(FullArgs a, Geo 
     else A = reinterpret_cast<T*>(slab);
     T* xs = reinterpret_cast<T*>(sp + off);
     T* mu = xs + (size_t)g.S * g.Dp;
-    if (g.tc) {
+    if (g.tcg) {
         if (threadIdx.x == 0) {
             s_err = 0;
             tc::mbar_init(&s_bar[0], 1);
@@ -1310,9 +1366,9 @@ __global__ void __launch_bounds__(FB_THREADS, 1) moments_kernel(FullArgs a, Geo 
         __syncthreads();
         mat_zero(A, g);
         if constexpr (sizeof(T) == 4) {
-            if (g.tc) gram_tc(a.x, a.H, a.W, g, py, px, 0, N, ro, ri, mu, 1.f / (float)N, A, st);
+            if (g.tcg) gram_tc<1>(a.x, a.H, a.W, g, py, px, 0, N, ro, ri, mu, 1.f / (float)N, A, st);
         }
-        if (!g.tc) {
+        if (!g.tcg) {
             gram_accumulate<T>(a.x, a.H, a.W, g, py, px, 0, N, ro, ri, mu, T(1), A, xs);
             mat_scale(A, g, T(1) / (T)N);
         }
@@ -1322,7 +1378,7 @@ __global__ void __launch_bounds__(FB_THREADS, 1) moments_kernel(FullArgs a, Geo 
             cov_out[t * D * D + e] = (float)(r >= c ? el(A, g.ntl, r, c) : el(A, g.ntl, c, r));
         }
     }
-    if (g.tc) {
+    if (g.tcg) {
         __syncthreads();
         if (s_err) {
             tc::mbar_wait_bounded(&s_bar[0], st.uses[0] & 1, TC_WAIT);
@@ -1349,6 +1405,8 @@ Geo make_geo_only(const FullArgs& a) {
     g.Np = (g.N + 3) & ~3;
     g.wood = g.N < g.D && a.loading > 0.0 && (int64_t)a.H * a.W < (int64_t)INT32_MAX;
     g.tc = false;
+    g.tcg = false;
+    g.pieces = 1;
     g.a_in_smem = false;
     g.pan_in_tc = false;
     g.pan_in_smem = false;
@@ -1356,16 +1414,24 @@ Geo make_geo_only(const FullArgs& a) {
 }
 
 template <typename T>
-Geo make_geo(const FullArgs& a, bool* smem_ok, size_t* smem_bytes, size_t* slab, Geo* g64_out = nullptr) {
+Geo make_geo(const FullArgs& a, bool* smem_ok, size_t* smem_bytes, size_t* slab, Geo* g64_out = nullptr,
+             bool split_ok = false) {
     Geo g = make_geo_only<T>(a);
     const size_t amat = sizeof(T) * (size_t)g.ntl * 16;
     const size_t vecs = vec_bytes<T>(g);
     g.tc = (sizeof(T) == 4) && a.precision == WDAD_PREC_MIXED && a.D <= 256;
-    const size_t tcb = g.tc ? kTcBufBytes : 0;
+    // the FP32 detectors' L x L window Gram (LRX / DWRX with N >= D) on the tensor cores in the
+    // three-piece split, which keeps FP32 accuracy (only while the matrix still fits shared memory
+    // beside the chunk buffers)
+    const bool split = split_ok && (sizeof(T) == 4) && a.precision == WDAD_PREC_FP32 && a.D <= 256 && !g.wood &&
+                       (a.out[0] || a.out[1]) && amat + vecs + kTcBufBytes <= 210 * 1024;
+    g.tcg = g.tc || split;
+    g.pieces = g.tc ? 1 : 3;
+    const size_t tcb = g.tcg ? kTcBufBytes : 0;
     g.a_in_smem = (sizeof(T) == 4) && (amat + vecs + tcb <= 210 * 1024);
     const size_t panb = pan_bytes<T>(g.Dp);
     size_t sm = vecs + tcb + (g.a_in_smem ? amat : 0);
-    g.pan_in_tc = g.tc && panb <= kTcBufBytes;
+    g.pan_in_tc = g.tcg && panb <= kTcBufBytes;
     g.pan_in_smem = !g.pan_in_tc && sm + panb <= 210 * 1024;
     if (g.pan_in_smem) sm += panb;
     *smem_bytes = sm + 1024;  // + alignment slack
@@ -1393,7 +1459,7 @@ size_t fullband_workspace_bytes(const FullArgs& a, int num_sms) {
     bool ok;
     size_t smem, slab;
     if (a.precision == WDAD_PREC_FP64) make_geo<double>(a, &ok, &smem, &slab);
-    else make_geo<float>(a, &ok, &smem, &slab);
+    else make_geo<float>(a, &ok, &smem, &slab, nullptr, true);
     if (!ok) return 0;
     return slab * (size_t)fb_grid(num_sms, a.pix ? a.npix : (int64_t)a.H * a.W) + 256;
 }
@@ -1403,7 +1469,7 @@ static cudaError_t launch_fb(const FullArgs& a, void* ws, int num_sms, cudaStrea
     bool ok;
     size_t smem, slab;
     Geo g64{};
-    const Geo g = make_geo<T>(a, &ok, &smem, &slab, &g64);
+    const Geo g = make_geo<T>(a, &ok, &smem, &slab, &g64, true);
     if (!ok) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(fullband_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
