@@ -726,7 +726,7 @@ def run_c3_table():
 def run_profile_case(case: str):
     """Small workloads for ncu captures of kernels outside the timed step (a few GB at most):
     batch (8 cubes, side <= 512), screen (1024x1024x224 screening pass), mixed (64x64x224 AR(1)
-    full-band LRX, MIXED at window 7/21 then FP32 at 3/11), grx (global RX on a 512x512x224 cube).  Each runs its workload twice and exits."""
+    full-band LRX, MIXED and FP32 at window 7/21, then FP32 at 3/11), grx (global RX on a 512x512x224 cube).  Each runs its workload twice and exits."""
     import torch
     from paper_1201_2025_gb300 import synth, wdad
     dev = torch.device("cuda", 0)
@@ -757,8 +757,9 @@ def run_profile_case(case: str):
         sc = synth.make_scene(64, 64, L, seed=7, n_anom=10, anom_side=(1, 3), abundance=(0.1, 0.5), margin=6,
                               ar_rho=0.98)
         x = torch.from_numpy(sc.cube).to(dev)
-        for _ in range(2):  # MIXED at 7/21 (BF16 tensor-core Gram), FP32 at 3/11 (sample-Gram form)
+        for _ in range(2):  # MIXED and FP32 at 7/21 (BF16 / split tensor-core Gram), FP32 at 3/11 (sample Gram)
             wdad.wdad_detect(x, 0, reduce=False, inner=7, outer=21, precision=1, cond_gate=1e6)
+            wdad.wdad_detect(x, 0, reduce=False, inner=7, outer=21, precision=0)
             wdad.wdad_detect(x, 0, reduce=False, inner=3, outer=11, precision=0)
     elif case == "grx":
         sc = synth.make_scene(512, 512, L, seed=0, n_anom=200, anom_side=(1, 3), abundance=(0.1, 0.5), margin=10)
