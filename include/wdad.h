@@ -243,8 +243,10 @@ typedef struct wdad_batch_ctx* wdad_batch;
  * `stream` is being captured. */
 wdad_status wdad_autotune(wdad_handle h, int D, int inner, int outer, int* tile_h, void* stream);
 
-/* Prepare a batch of n jobs: DWT plans, tile plans (autotune != 0: the autotuner's, else
- * the defaults that wdad_detect uses), a device work list and per-job scratch owned by the
+/* Prepare a batch of n jobs: DWT plans, tile plans (autotune != 0: the autotuner's, kept only
+ * if the whole batch, timed with them and with the defaults over five launches each, runs at
+ * least 1% faster -- those timing launches write the jobs' outputs; else the defaults that
+ * wdad_detect uses), a device work list and per-job scratch owned by the
  * batch, and, when use_graph != 0, a CUDA graph of the whole launch captured on a private
  * stream.  Jobs below 512 x 512 pixels share one persistent kernel (counter reset, then the
  * kernel); a job of at least 512 x 512 pixels fills the GPU alone and runs as its own DWT and

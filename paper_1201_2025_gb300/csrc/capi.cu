@@ -936,8 +936,9 @@ static cudaError_t batch_issue(wdad_batch_ctx* b, cudaStream_t s) {
     return e;
 }
 
-wdad_status wdad_batch_create(wdad_handle h, int n, const wdad_job* jobs, int autotune_plans, int use_graph,
-                              wdad_batch* out, void* stream) {
+// The batch with every job's plan from the autotuner (tuned) or the default plans.
+static wdad_status batch_build(wdad_handle h, int n, const wdad_job* jobs, int autotune_plans, int use_graph,
+                               wdad_batch* out, void* stream) {
     if (!h) return WDAD_ERR_ARG;
     if (!out || n < 1 || !jobs) return fail(h, WDAD_ERR_ARG, "batch: n >= 1 jobs and an output handle");
     *out = nullptr;
@@ -1055,6 +1056,63 @@ wdad_status wdad_batch_create(wdad_handle h, int n, const wdad_job* jobs, int au
         batch_free(b);
         return fail(h, WDAD_ERR_NOMEM, "host exception");
     }
+}
+
+// Median device time of `reps` launches of a batch after two warm-up launches (CUDA events on
+// `stream`); a negative value when a launch or its status fails.
+static float batch_time(wdad_batch b, cudaStream_t s, int reps) {
+    for (int r = 0; r < 2; ++r)
+        if (wdad_batch_launch(b, s) != WDAD_OK) return -1.f;
+    if (wdad_batch_status(b, nullptr) != WDAD_OK) return -1.f;
+    std::vector<cudaEvent_t> ev((size_t)reps + 1);
+    for (auto& e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) return -1.f;
+    std::vector<float> t;
+    bool ok = cudaEventRecord(ev[0], s) == cudaSuccess;
+    for (int r = 0; r < reps && ok; ++r)
+        ok = wdad_batch_launch(b, s) == WDAD_OK && cudaEventRecord(ev[(size_t)r + 1], s) == cudaSuccess;
+    ok = ok && cudaEventSynchronize(ev[(size_t)reps]) == cudaSuccess && wdad_batch_status(b, nullptr) == WDAD_OK;
+    for (int r = 0; r < reps && ok; ++r) {
+        float ms = 0.f;
+        ok = cudaEventElapsedTime(&ms, ev[(size_t)r], ev[(size_t)r + 1]) == cudaSuccess;
+        t.push_back(ms);
+    }
+    for (auto e : ev) cudaEventDestroy(e);
+    if (!ok) return -1.f;
+    std::sort(t.begin(), t.end());
+    return t[t.size() / 2];
+}
+
+// With autotune, the plans the autotuner measured one (K, window) class at a time are checked
+// on the batch itself: the whole batch is timed with the tuned plans and with the default
+// plans, and the tuned set is kept only if it is at least 1% faster, so an autotuned batch is
+// never slower than the default one by more than the timing noise.
+wdad_status wdad_batch_create(wdad_handle h, int n, const wdad_job* jobs, int autotune_plans, int use_graph,
+                              wdad_batch* out, void* stream) {
+    if (!autotune_plans) return batch_build(h, n, jobs, 0, use_graph, out, stream);
+    wdad_batch tuned = nullptr, plain = nullptr;
+    wdad_status st = batch_build(h, n, jobs, 1, use_graph, &tuned, stream);
+    if (st != WDAD_OK) return st;
+    bool all_default = true;
+    for (int i = 0; i < n && all_default; ++i) {
+        const wdad_job& j = jobs[i];
+        const int K = wdad_query_K(j.L, j.params.wavelet_taps, j.params.level);
+        all_default = tuned->th[(size_t)i] == wdad::detect_small_default_th(K, j.params.inner, j.params.outer);
+    }
+    if (all_default) { *out = tuned; return WDAD_OK; }
+    st = batch_build(h, n, jobs, 0, use_graph, &plain, stream);
+    if (st != WDAD_OK) { wdad_batch_destroy(tuned); return st; }
+    cudaStream_t s = (cudaStream_t)stream;
+    const float t_tuned = batch_time(tuned, s, 5), t_plain = batch_time(plain, s, 5);
+    if (t_tuned < 0.f || t_plain < 0.f) {
+        wdad_batch_destroy(tuned);
+        wdad_batch_destroy(plain);
+        return fail(h, WDAD_ERR_CUDA, "batch autotune: a timing launch failed");
+    }
+    const bool keep_tuned = t_tuned < 0.99f * t_plain;
+    wdad_batch_destroy(keep_tuned ? plain : tuned);
+    *out = keep_tuned ? tuned : plain;
+    return WDAD_OK;
 }
 
 wdad_status wdad_batch_launch(wdad_batch b, void* stream) {
