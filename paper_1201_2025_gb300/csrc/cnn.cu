@@ -455,15 +455,15 @@ cudaError_t conv_fwd(const float* in, int B, int H, int W, int Cin, const float*
     const int tiles = ((W + CT - 1) / CT) * ((H + CT - 1) / CT) * B;
     cudaError_t e;
     if (Cout == 32) {
-        e = cudaFuncSetAttribute(conv_fwd_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = raise_smem_limit(conv_fwd_kernel<32>);
         if (e != cudaSuccess) return e;
         conv_fwd_kernel<32><<<tiles, CT * CT, smem, s>>>(in, B, H, W, Cin, w, bias, k, relu, norm, out);
     } else if (Cout == 4) {
-        e = cudaFuncSetAttribute(conv_fwd_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = raise_smem_limit(conv_fwd_kernel<4>);
         if (e != cudaSuccess) return e;
         conv_fwd_kernel<4><<<tiles, CT * CT, smem, s>>>(in, B, H, W, Cin, w, bias, k, relu, norm, out);
     } else if (Cout == 1) {
-        e = cudaFuncSetAttribute(conv_fwd_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = raise_smem_limit(conv_fwd_kernel<1>);
         if (e != cudaSuccess) return e;
         conv_fwd_kernel<1><<<tiles, CT * CT, smem, s>>>(in, B, H, W, Cin, w, bias, k, relu, norm, out);
     } else {

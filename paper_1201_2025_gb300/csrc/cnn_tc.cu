@@ -167,7 +167,7 @@ cudaError_t pack_w5(const float* w, __nv_bfloat16* packed, cudaStream_t s) {
 cudaError_t conv5_tc(const float* in, int B, int H, int W, const __nv_bfloat16* wpk, const float* bias, int relu,
                      float* out, int* err, int num_sms, cudaStream_t s) {
     const size_t smem = (size_t)W5_BYTES + XS_BYTES + 1024;
-    cudaError_t e = cudaFuncSetAttribute(conv5_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_smem_limit(conv5_tc_kernel);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv5_tc_kernel, TC_THREADS, smem);

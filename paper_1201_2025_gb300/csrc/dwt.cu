@@ -11,9 +11,6 @@
 // PX*K results leave as one coalesced store.  The lane partial sums plus the tree
 // of shuffles keep the FP32 rounding error near sqrt(L) ulp instead of L ulp.
 #include <complex>
-#include <mutex>
-#include <set>
-#include <utility>
 #include <vector>
 
 #include "dwt_dev.cuh"
@@ -132,29 +129,6 @@ bool dwt_shape_supported(int L, int K) {
     return (L + 31) / 32 <= (K <= 4 ? 8 : 4);
 }
 
-// The dynamic shared memory limit of a DWT kernel is raised once per kernel and device to the
-// opt-in maximum, so that a launch with a reservation (launch_dwt_approx_beside) never races
-// with another thread's setting.
-template <class Kern>
-static cudaError_t allow_reservation(Kern* kernel) {
-    static std::mutex mu;
-    static std::set<std::pair<const void*, int>> done;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    std::lock_guard<std::mutex> lk(mu);
-    const auto key = std::make_pair(reinterpret_cast<const void*>(kernel), dev);
-    if (done.count(key)) return cudaSuccess;
-    int optin = 0;
-    cudaFuncAttributes fa{};
-    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
-    if (e == cudaSuccess) done.insert(key);
-    return e;
-}
-
 // ctas > 0 caps the grid at that many CTAs; reserve > 0 launches with that much dynamic shared
 // memory, which the kernel does not use: it only limits how many CTAs share an SM.
 template <int VEC, int NCH, int KP>
@@ -172,7 +146,7 @@ static cudaError_t launch_one(const float* cube, int64_t P, int L, const float* 
     if (grid > cap) grid = cap;
     if (grid < 1) grid = 1;
     if (reserve > 0) {
-        cudaError_t e = allow_reservation(dwt_apply_kernel<VEC, NCH, KP>);
+        cudaError_t e = raise_smem_limit(dwt_apply_kernel<VEC, NCH, KP>);
         if (e != cudaSuccess) return e;
     }
     dwt_apply_kernel<VEC, NCH, KP><<<(unsigned)grid, 256, reserve, s>>>(cube, P, L, A, K, out);

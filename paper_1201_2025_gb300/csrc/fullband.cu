@@ -1471,7 +1471,7 @@ static cudaError_t launch_fb(const FullArgs& a, void* ws, int num_sms, cudaStrea
     Geo g64{};
     const Geo g = make_geo<T>(a, &ok, &smem, &slab, &g64, true);
     if (!ok) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(fullband_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_smem_limit(fullband_kernel<T>);
     if (e != cudaSuccess) return e;
     const int grid = fb_grid(num_sms, a.pix ? a.npix : (int64_t)a.H * a.W);
     char* base = reinterpret_cast<char*>(((uintptr_t)ws + 255) & ~(uintptr_t)255);
@@ -1486,7 +1486,7 @@ static cudaError_t launch_mom(const FullArgs& a, const int64_t* pix, int64_t npi
     size_t smem, slab;
     const Geo g = make_geo<T>(a, &ok, &smem, &slab);
     if (!ok) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(moments_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_smem_limit(moments_kernel<T>);
     if (e != cudaSuccess) return e;
     const int grid = fb_grid(num_sms, npix);
     char* base = reinterpret_cast<char*>(((uintptr_t)ws + 255) & ~(uintptr_t)255);

@@ -524,8 +524,7 @@ cudaError_t launch_score(const float* x, int64_t P, int L, const float* mu, cons
                          float* score, cudaStream_t s) {
     constexpr int PX = PW * (GRX_SCORE_THREADS / 32);
     const size_t smem = sizeof(float) * (size_t)PX * L;
-    cudaError_t e = cudaFuncSetAttribute(grx_score_kernel<M, PW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = raise_smem_limit(grx_score_kernel<M, PW>);
     if (e != cudaSuccess) return e;
     const int64_t grid = (P + PX - 1) / PX;
     grx_score_kernel<M, PW><<<(unsigned)grid, GRX_SCORE_THREADS, smem, s>>>(x, P, L, mu, B, status, score);
@@ -537,8 +536,7 @@ cudaError_t launch_score4(const float* x, int64_t P, int L, const float* mu, con
                           float* score, cudaStream_t s) {
     constexpr int PX = PW * (GRX_SCORE_THREADS / 32);
     const size_t smem = sizeof(float) * (size_t)PX * L;
-    cudaError_t e = cudaFuncSetAttribute(grx_score4_kernel<G, PW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = raise_smem_limit(grx_score4_kernel<G, PW>);
     if (e != cudaSuccess) return e;
     const int64_t grid = (P + PX - 1) / PX;
     grx_score4_kernel<G, PW><<<(unsigned)grid, GRX_SCORE_THREADS, smem, s>>>(x, P, L, mu, B, status, score);
@@ -570,7 +568,7 @@ cudaError_t launch_global_rx(const float* x, int64_t P, int L, float loading, fl
     grx_colsum_kernel<<<g.nblk1, 256, 0, s>>>(x, P, L, part1);
     grx_mean_kernel<<<L, 256, 0, s>>>(part1, g.nblk1, L, P, mu);
     const size_t smem_g = sizeof(float) * (size_t)g.S * g.nst * 8;
-    cudaError_t e = cudaFuncSetAttribute(grx_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_g);
+    cudaError_t e = raise_smem_limit(grx_gram_kernel);
     if (e != cudaSuccess) return e;
     grx_gram_kernel<<<dim3(g.nblk2, g.ngroups), GRX_THREADS, smem_g, s>>>(x, P, L, g.range, mu, g.S, part2);
     const int nent = g.nstl * 64;
@@ -581,7 +579,7 @@ cudaError_t launch_global_rx(const float* x, int64_t P, int L, float loading, fl
         const int in_smem = ntri(L) + L + 4 <= GRX_INV_SMEM_FLOATS;
         const size_t smem_i =
             sizeof(float) * (in_smem ? (size_t)(((L + 3) & ~3) + ntri(L)) : (size_t)((L + 3) & ~3));
-        e = cudaFuncSetAttribute(grx_invert_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_i);
+        e = raise_smem_limit(grx_invert_kernel);
         if (e != cudaSuccess) return e;
         grx_invert_kernel<<<1, GRX_THREADS, smem_i, s>>>(M, diag, L, loading, B, status, in_smem);
     }

@@ -3,9 +3,36 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+#include <set>
+#include <utility>
+
 #include "../../include/wdad.h"
 
 namespace wdad {
+
+// The dynamic shared memory limit of a kernel, raised once per kernel and device to the opt-in
+// maximum less the kernel's static shared memory, so that launches of different sizes from
+// several host threads never lower it between another thread's set and launch.
+template <class Kern>
+inline cudaError_t raise_smem_limit(Kern* kernel) {
+    static std::mutex mu;
+    static std::set<std::pair<const void*, int>> done;  // (kernel, device) pairs already raised
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    const auto key = std::make_pair(reinterpret_cast<const void*>(kernel), dev);
+    if (done.count(key)) return cudaSuccess;
+    int optin = 0;
+    cudaFuncAttributes fa{};
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+    if (e == cudaSuccess) done.insert(key);
+    return e;
+}
 
 // Device-side reflect-101 (-1 -> 1, n -> n-2), valid for any integer i.
 __host__ __device__ __forceinline__ int reflect101(int i, int n) {

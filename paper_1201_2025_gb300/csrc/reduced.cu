@@ -1,8 +1,5 @@
 // Launchers and kernels of the reduced-band detectors (device code in reduced_dev.cuh).
 #include <algorithm>
-#include <mutex>
-#include <set>
-#include <utility>
 
 #include "reduced_dev.cuh"
 
@@ -79,37 +76,10 @@ static int pick_th(int D, int inner, int outer, int want) {
     return 0;
 }
 
-// The dynamic shared memory limit of a kernel is raised once per kernel and device to the
-// largest size any plan uses, so that launches from several host threads never lower it
-// between another thread's set and launch.
-template <class K>
-static cudaError_t set_max_smem(K* kernel) {
-    static std::mutex mu;
-    static std::set<std::pair<const void*, int>> done;  // (kernel, device) pairs already raised
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    std::lock_guard<std::mutex> lk(mu);
-    const auto key = std::make_pair(reinterpret_cast<const void*>(kernel), dev);
-    if (!done.count(key)) {
-        // the opt-in limit covers static and dynamic shared memory together
-        int optin = 0;
-        cudaFuncAttributes fa{};
-        e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
-        if (e != cudaSuccess) return e;
-        const int dyn = std::min<int>(kMaxSmem, optin - (int)fa.sharedSizeBytes);
-        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
-        if (e != cudaSuccess) return e;
-        done.insert(key);
-    }
-    return cudaSuccess;
-}
-
 template <int D>
 static cudaError_t launch_d(const DetectArgs& a, int th, cudaStream_t s) {
     const size_t smem = detect_small_smem(D, a.inner, a.outer, th);
-    cudaError_t e = set_max_smem(detect_small_kernel<D>);
+    cudaError_t e = raise_smem_limit(detect_small_kernel<D>);
     if (e != cudaSuccess) return e;
     dim3 grid((a.W + TW - 1) / TW, (a.H + th - 1) / th);
     const int threads = std::min(512, std::max(256, th * 32));  // one thread per output pixel when th >= 8
@@ -154,7 +124,7 @@ cudaError_t launch_detect_small(const DetectArgs& a, int tile_h, cudaStream_t s)
 
 template <int D>
 static cudaError_t launch_multi_d(const MultiArgs& m, size_t smem, int blocks, cudaStream_t s) {
-    cudaError_t e = set_max_smem(detect_multi_kernel<D>);
+    cudaError_t e = raise_smem_limit(detect_multi_kernel<D>);
     if (e != cudaSuccess) return e;
     detect_multi_kernel<D><<<blocks, 512, smem, s>>>(m);
     return cudaGetLastError();
@@ -213,7 +183,7 @@ cudaError_t launch_window_census(int H, int W, int inner, int outer, int border,
         th >>= 1;
     const size_t smem = tile_smem_bytes(CensusPayload::WORDS, CensusPayload::NC, 8, inner, outer, th);
     if (smem > (size_t)kMaxSmem) return cudaErrorInvalidValue;
-    cudaError_t e = set_max_smem(census_kernel);
+    cudaError_t e = raise_smem_limit(census_kernel);
     if (e != cudaSuccess) return e;
     dim3 grid((W + TW - 1) / TW, (H + th - 1) / th);
     census_kernel<<<grid, th >= 16 ? 512 : 256, smem, s>>>(H, W, inner, outer, border, th,
