@@ -148,7 +148,7 @@ wdad_status wdad_detect_windows(wdad_handle h, const float* cube, int H, int W, 
  * parameter sets params[0..nwin-1] (same wavelet and level), and the score maps are
  * copied back to host_scores, laid out [nwin][3][H][W] (LRX, DWRX, DWEST).
  * host_cube and host_scores are HOST pointers.  With reduce = 1 and K <= 8 the call runs
- * in row bands (at least 64 rows, twice the widest halo plus a tile, a quarter of the
+ * in row bands (at least 64 rows, twice the widest halo plus a tile, an eighth of the
  * image) over three streams: the handle's copy stream moves band b of the cube to the
  * workspace, the DWT of band b - 1 runs on `stream`, and the handle's second stream runs
  * the detector tiles of band b - 2 and copies that band's score rows back in one strided

@@ -787,7 +787,7 @@ wdad_status wdad_detect_all_host(wdad_handle h, const float* host_cube, int H, i
             }
             int ro_max = 0;
             for (int w = 0; w < nwin; ++w) ro_max = std::max(ro_max, params[w].outer / 2);
-            const int RC = std::max({64, 2 * (16 + ro_max), (H + 3) / 4});
+            const int RC = std::max({64, 2 * (16 + ro_max), (H + 7) / 8});
             const int nb = (H + RC - 1) / RC;
             for (cudaStream_t* q : {&h->aux, &h->aux2})
                 if (!*q && cudaStreamCreateWithFlags(q, cudaStreamNonBlocking) != cudaSuccess)
