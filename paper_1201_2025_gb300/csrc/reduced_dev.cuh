@@ -500,12 +500,24 @@ __device__ __forceinline__ void jacobi_inplace(float (&A)[D][D], float (&V)[D][D
 #pragma unroll
         for (int b = 0; b < D; ++b) V[a][b] = (a == b) ? 1.f : 0.f;
     if constexpr (D == 1) return;
+    // the eigenvectors are accumulated as row pairs (rows 2h, 2h + 1 of column b in VP[h][b]),
+    // so that each rotation of two columns is two packed multiplies and two packed FMAs per
+    // row pair; an odd last row stays scalar
+    constexpr int HP = D / 2;
+    float2 VP[HP > 0 ? HP : 1][D];
+    float VL[D];
+#pragma unroll
+    for (int h = 0; h < HP; ++h)
+#pragma unroll
+        for (int b = 0; b < D; ++b) VP[h][b] = make_float2(V[2 * h][b], V[2 * h + 1][b]);
+#pragma unroll
+    for (int b = 0; b < D; ++b) VL[b] = V[D - 1][b];
     float fro = 0.f;
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
         for (int b = 0; b < D; ++b) fro = fmaf(A[a][b], A[a][b], fro);
-    if (!(fro > 0.f)) return;  // zero matrix: already diagonal (NaN input stays NaN)
+    if (!(fro > 0.f)) return;  // zero matrix: already diagonal (NaN input stays NaN); V = I
     const float unit = rsqrtf(fro);
 #pragma unroll
     for (int a = 0; a < D; ++a)
@@ -588,14 +600,32 @@ __device__ __forceinline__ void jacobi_inplace(float (&A)[D][D], float (&V)[D][D
                 const int p0 = rr_first(E, r, k), q0 = rr_second(E, r, k);
                 const int p = p0 < q0 ? p0 : q0, q = p0 < q0 ? q0 : p0;
                 if (q >= D) continue;
+                const float2 c2 = make_float2(c[k], c[k]), s2 = make_float2(sn[k], sn[k]);
+                const float2 ns2 = make_float2(-sn[k], -sn[k]);
 #pragma unroll
-                for (int a = 0; a < D; ++a) {
-                    const float vp = V[a][p], vq = V[a][q];
-                    V[a][p] = c[k] * vp - sn[k] * vq;
-                    V[a][q] = sn[k] * vp + c[k] * vq;
+                for (int h = 0; h < HP; ++h) {
+                    const float2 vp = VP[h][p], vq = VP[h][q];
+                    VP[h][p] = __ffma2_rn(vq, ns2, __fmul2_rn(vp, c2));
+                    VP[h][q] = __ffma2_rn(vq, c2, __fmul2_rn(vp, s2));
+                }
+                if constexpr (D & 1) {
+                    const float vp = VL[p], vq = VL[q];
+                    VL[p] = fmaf(-sn[k], vq, c[k] * vp);
+                    VL[q] = fmaf(c[k], vq, sn[k] * vp);
                 }
             }
         }
+    }
+#pragma unroll
+    for (int h = 0; h < HP; ++h)
+#pragma unroll
+        for (int b = 0; b < D; ++b) {
+            V[2 * h][b] = VP[h][b].x;
+            V[2 * h + 1][b] = VP[h][b].y;
+        }
+    if constexpr (D & 1) {
+#pragma unroll
+        for (int b = 0; b < D; ++b) V[D - 1][b] = VL[b];
     }
 }
 
