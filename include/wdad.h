@@ -25,7 +25,9 @@
  *     a handle.
  *   - A handle binds one CUDA device and owns a grow-only device workspace and
  *     plan caches.  Calls on one handle must not run concurrently from several
- *     host threads; use one handle per thread.
+ *     host threads; use one handle per thread.  Each call reuses the workspace from
+ *     its start, so calls on one handle that are given different streams must be
+ *     ordered by the caller (an event), or use one handle per stream.
  */
 #ifndef WDAD_H
 #define WDAD_H
