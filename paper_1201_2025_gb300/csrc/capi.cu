@@ -384,7 +384,7 @@ void cnn_free(wdad_cnn_ctx* c) {
     auto& n = c->net;
     cudaFree(n.w); cudaFree(n.wf); cudaFree(n.m); cudaFree(n.v); cudaFree(n.grad); cudaFree(n.wt);
     cudaFree(n.norm); cudaFree(n.stat); cudaFree(n.act); cudaFree(n.loss); cudaFree(n.cx); cudaFree(n.ct);
-    cudaFree(n.wpk); cudaFree(n.tcerr);
+    cudaFree(n.wpk); cudaFree(n.tcerr); cudaFree(n.gpart);
     delete c;
 }
 
@@ -1188,6 +1188,7 @@ wdad_status wdad_cnn_create(wdad_handle h, int K, int bf16_weights, uint64_t see
         if (e == cudaSuccess) e = cudaMalloc(&n.cx, sizeof(float) * (size_t)max_batch_pixels * K);
         if (e == cudaSuccess) e = cudaMalloc(&n.ct, sizeof(float) * (size_t)max_batch_pixels);
         if (e == cudaSuccess) e = cudaMalloc(&n.wpk, sizeof(__nv_bfloat16) * 2 * 25 * 32 * 32);
+        if (e == cudaSuccess) e = cudaMalloc(&n.gpart, sizeof(float) * wdad::cnn::gpart_floats());
         if (e == cudaSuccess) e = cudaMalloc(&n.tcerr, sizeof(int));
         if (e == cudaSuccess) e = cudaMemset(n.tcerr, 0, sizeof(int));
         if (e != cudaSuccess) { cnn_free(c); return cuda_fail(h, e, "cnn allocation"); }

@@ -18,6 +18,7 @@
 // radix threshold and an audit draw.  At inference, networks with BF16 weights run their
 // two 32-channel layers on the tensor cores (cnn_tc.cu).
 // Random numbers come from splitmix64 (Steele, Lea, Flood 2014) on (seed, counter).
+#include <algorithm>
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -143,25 +144,89 @@ __global__ void __launch_bounds__(256) conv_bwd_weight_kernel(const float* __res
     }
 }
 
-// db[co] = sum over pixels of dz[pix][co] (one block, fixed order)
-__global__ void __launch_bounds__(256) bias_grad_kernel(const float* __restrict__ dz, int64_t n, int Cout,
-                                                        float* __restrict__ db) {
-    __shared__ float red[8][32];
-    float acc[32];
-    for (int co = 0; co < 32; ++co) acc[co] = 0.f;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
-        for (int co = 0; co < Cout; ++co) acc[co] += dz[i * Cout + co];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int co = 0; co < Cout; ++co) {
-        float v = acc[co];
-        for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) red[warp][co] = v;
+// The 32-output-channel weight gradient as chunked outer products: block (tap, chunk) stages
+// 32 pixels at a time (the activations at the tap's offset and the output gradients) in shared
+// memory and accumulates the Cin x 32 products of its chunk's pixels, thread (ci, four co);
+// part[chunk][ci][tap][co] receives the chunk's sums, which grad_chunks_sum adds in chunk order
+// (deterministic: the same sums on every run).
+constexpr int WG_TILE = 32;
+__global__ void __launch_bounds__(256) conv_bwd_weight32_kernel(const float* __restrict__ in,
+                                                                const float* __restrict__ dz, int B, int H, int W,
+                                                                int Cin, int k, int chunk_px,
+                                                                float* __restrict__ part) {
+    __shared__ float as[WG_TILE][33];
+    __shared__ __align__(16) float ds[WG_TILE][32];
+    const int taps = k * k, pd = k / 2;
+    const int tap = blockIdx.x, chunk = blockIdx.y;
+    const int ky = tap / k, kx = tap % k;
+    const int ci = threadIdx.x >> 3, c4 = (threadIdx.x & 7) * 4;
+    const int64_t n = (int64_t)B * H * W;
+    const int64_t p0 = (int64_t)chunk * chunk_px, p1 = min(n, p0 + chunk_px);
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int64_t q0 = p0; q0 < p1; q0 += WG_TILE) {
+        for (int idx = threadIdx.x; idx < WG_TILE * 32; idx += blockDim.x) {
+            const int pp = idx >> 5, cc = idx & 31;
+            const int64_t pix = q0 + pp;
+            float d = 0.f, a = 0.f;
+            if (pix < p1) {
+                d = dz[pix * 32 + cc];
+                if (cc < Cin) {
+                    const int x = (int)(pix % W), y = (int)((pix / W) % H);
+                    const int64_t b = pix / ((int64_t)H * W);
+                    const int yy = y + ky - pd, xx = x + kx - pd;
+                    if (yy >= 0 && yy < H && xx >= 0 && xx < W) a = in[((b * H + yy) * W + xx) * Cin + cc];
+                }
+            }
+            ds[pp][cc] = d;
+            as[pp][cc] = a;
+        }
+        __syncthreads();
+        if (ci < Cin) {
+#pragma unroll 8
+            for (int pp = 0; pp < WG_TILE; ++pp) {
+                const float a = as[pp][ci];
+                const float4 d = *reinterpret_cast<const float4*>(&ds[pp][c4]);
+                acc[0] = fmaf(a, d.x, acc[0]);
+                acc[1] = fmaf(a, d.y, acc[1]);
+                acc[2] = fmaf(a, d.z, acc[2]);
+                acc[3] = fmaf(a, d.w, acc[3]);
+            }
+        }
+        __syncthreads();
     }
+    if (ci < Cin) {
+        float* o = part + (size_t)chunk * Cin * taps * 32 + ((size_t)ci * taps + tap) * 32 + c4;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) o[j] = acc[j];
+    }
+}
+
+// db partial sums: block `chunk` adds its pixels' output gradients, eight pixel groups per
+// channel added in group order
+__global__ void __launch_bounds__(256) bias_grad_chunk_kernel(const float* __restrict__ dz, int64_t n, int Cout,
+                                                              int chunk_px, float* __restrict__ part) {
+    __shared__ float red[8][32];
+    const int co = threadIdx.x & 31, grp = threadIdx.x >> 5;
+    const int64_t p0 = (int64_t)blockIdx.x * chunk_px, p1 = min(n, p0 + chunk_px);
+    float acc = 0.f;
+    if (co < Cout)
+        for (int64_t i = p0 + grp; i < p1; i += 8) acc += dz[i * Cout + co];
+    red[grp][co] = acc;
     __syncthreads();
     if (threadIdx.x < Cout) {
         float s = 0.f;
-        for (int w2 = 0; w2 < 8; ++w2) s += red[w2][threadIdx.x];
-        db[threadIdx.x] = s;
+        for (int g = 0; g < 8; ++g) s += red[g][threadIdx.x];
+        part[(size_t)blockIdx.x * Cout + threadIdx.x] = s;
+    }
+}
+
+// out[o] = sum over the chunks in order of part[chunk][o]
+__global__ void grad_chunks_sum_kernel(const float* __restrict__ part, int nchunk, int64_t per,
+                                       float* __restrict__ out) {
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < per; o += (int64_t)gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int c = 0; c < nchunk; ++c) s += part[(size_t)c * per + o];
+        out[o] = s;
     }
 }
 
@@ -472,12 +537,36 @@ cudaError_t conv_fwd(const float* in, int B, int H, int W, int Cin, const float*
     return cudaGetLastError();
 }
 
-static cudaError_t conv_bwd_weight(const float* in, const float* dz, int B, int H, int W, int Cin, int Cout, int k,
-                                   float* dw, cudaStream_t s) {
+// pixels per gradient chunk: a multiple of 32, at least 256, at most GRAD_MAX_CHUNKS chunks
+static int grad_chunk_px(int64_t n) {
+    int64_t c = (n + GRAD_MAX_CHUNKS - 1) / GRAD_MAX_CHUNKS;
+    c = std::max<int64_t>(256, (c + 31) / 32 * 32);
+    return (int)c;
+}
+
+static cudaError_t conv_bwd_weight(const Net& net, const float* in, const float* dz, int B, int H, int W, int Cin,
+                                   int Cout, int k, float* dw, cudaStream_t s) {
+    if (Cout == 32 && Cin <= 32 && k <= 5) {
+        const int64_t n = (int64_t)B * H * W;
+        const int chunk_px = grad_chunk_px(n);
+        const int nchunk = (int)((n + chunk_px - 1) / chunk_px);
+        conv_bwd_weight32_kernel<<<dim3(k * k, nchunk), 256, 0, s>>>(in, dz, B, H, W, Cin, k, chunk_px, net.gpart);
+        const int64_t per = (int64_t)Cin * k * k * 32;
+        grad_chunks_sum_kernel<<<grid_for(per, 256), 256, 0, s>>>(net.gpart, nchunk, per, dw);
+        return cudaGetLastError();
+    }
     const int blocks = Cin * k * k;
     if (Cout == 32) conv_bwd_weight_kernel<32><<<blocks, 256, 0, s>>>(in, dz, B, H, W, Cin, k, dw);
     else if (Cout == 1) conv_bwd_weight_kernel<1><<<blocks, 256, 0, s>>>(in, dz, B, H, W, Cin, k, dw);
     else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+static cudaError_t bias_grad(const Net& net, const float* dz, int64_t n, int Cout, float* db, cudaStream_t s) {
+    const int chunk_px = grad_chunk_px(n);
+    const int nchunk = (int)((n + chunk_px - 1) / chunk_px);
+    bias_grad_chunk_kernel<<<nchunk, 256, 0, s>>>(dz, n, Cout, chunk_px, net.gpart);
+    grad_chunks_sum_kernel<<<1, 32, 0, s>>>(net.gpart, nchunk, Cout, db);
     return cudaGetLastError();
 }
 
@@ -522,9 +611,10 @@ cudaError_t net_grad(Net& n, const float* x, const float* t, int B, int H, int W
     if (e != cudaSuccess) return e;
     mse_kernel<<<1, 1024, 0, s>>>(out, t, B, H, W, 7, dout, n.loss);
     // layer 4 (32 -> 1, 3x3)
-    e = conv_bwd_weight(a2, dout, B, H, W, 32, 1, 3, n.grad + n.woff[3], s);
+    e = conv_bwd_weight(n, a2, dout, B, H, W, 32, 1, 3, n.grad + n.woff[3], s);
     if (e != cudaSuccess) return e;
-    bias_grad_kernel<<<1, 256, 0, s>>>(dout, px, 1, n.grad + n.boff[3]);
+    if (e == cudaSuccess) e = bias_grad(n, dout, px, 1, n.grad + n.boff[3], s);
+    if (e != cudaSuccess) return e;
     flip_transpose_kernel<<<64, 256, 0, s>>>(n.wf + n.woff[3], 32, 1, 3, n.wt);
     e = conv_fwd(dout, B, H, W, 1, n.wt, nullptr, 32, 3, 0, nullptr, d0, s);
     if (e != cudaSuccess) return e;
@@ -534,9 +624,10 @@ cudaError_t net_grad(Net& n, const float* x, const float* t, int B, int H, int W
     float* dcur = d0;
     float* dnext = d1;
     for (int l = 2; l >= 1; --l) {
-        e = conv_bwd_weight(ins[l - 1], dcur, B, H, W, 32, 32, 5, n.grad + n.woff[l], s);
+        e = conv_bwd_weight(n, ins[l - 1], dcur, B, H, W, 32, 32, 5, n.grad + n.woff[l], s);
         if (e != cudaSuccess) return e;
-        bias_grad_kernel<<<1, 256, 0, s>>>(dcur, px, 32, n.grad + n.boff[l]);
+        if (e == cudaSuccess) e = bias_grad(n, dcur, px, 32, n.grad + n.boff[l], s);
+        if (e != cudaSuccess) return e;
         flip_transpose_kernel<<<256, 256, 0, s>>>(n.wf + n.woff[l], 32, 32, 5, n.wt);
         e = conv_fwd(dcur, B, H, W, 32, n.wt, nullptr, 32, 5, 0, nullptr, dnext, s);
         if (e != cudaSuccess) return e;
@@ -546,9 +637,10 @@ cudaError_t net_grad(Net& n, const float* x, const float* t, int B, int H, int W
         dnext = tmp;
     }
     // layer 1 (K -> 32, 5x5) on the normalised input
-    e = conv_bwd_weight(x, dcur, B, H, W, n.K, 32, 5, n.grad + n.woff[0], s);
+    e = conv_bwd_weight(n, x, dcur, B, H, W, n.K, 32, 5, n.grad + n.woff[0], s);
     if (e != cudaSuccess) return e;
-    bias_grad_kernel<<<1, 256, 0, s>>>(dcur, px, 32, n.grad + n.boff[0]);
+    if (e == cudaSuccess) e = bias_grad(n, dcur, px, 32, n.grad + n.boff[0], s);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

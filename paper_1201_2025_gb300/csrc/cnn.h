@@ -26,7 +26,12 @@ struct Net {
     float *cx = nullptr, *ct = nullptr;  // crop buffers
     __nv_bfloat16* wpk = nullptr;  // the two 32 -> 32 layers' weights packed for the tensor cores
     int* tcerr = nullptr;          // set by a tensor-core convolution that gave up waiting
+    float* gpart = nullptr;        // per-chunk partial weight and bias gradients (gpart_floats())
 };
+
+// pixel chunks of the gradient reductions: at least 256 pixels each, at most 64 chunks
+constexpr int GRAD_MAX_CHUNKS = 64;
+inline size_t gpart_floats() { return (size_t)GRAD_MAX_CHUNKS * 32 * 25 * 32; }
 
 void layer_dims(int K, int l, int* cin, int* cout, int* k);
 void param_layout(int K, size_t woff[4], size_t boff[4], size_t* total);
