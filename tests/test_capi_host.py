@@ -77,6 +77,7 @@ def test_null_handle_is_an_argument_error(wl):
     lib = wl.lib()
     p = wl.wdad_default_params()
     assert lib.wdad_detect(None, None, 4, 4, 224, 0, 1, ctypes.byref(p), None, None, None) == wl.WDAD_ERR_ARG
+    assert lib.wdad_detect_sequence(None, 1, None, 4, 4, 224, 1, ctypes.byref(p), None, None, None) == wl.WDAD_ERR_ARG
     assert lib.wdad_destroy(None) == wl.WDAD_ERR_ARG
 
 
