@@ -1,5 +1,6 @@
 // Launchers and kernels of the reduced-band detectors (device code in reduced_dev.cuh).
 #include <algorithm>
+#include <mutex>
 
 #include "reduced_dev.cuh"
 
@@ -7,7 +8,7 @@ namespace wdad {
 
 template <int D>
 __global__ void __launch_bounds__(512) detect_small_kernel(DetectArgs a, int th) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     detect_tile<D>(a, th, blockIdx.x, blockIdx.y, smem_raw);
 }
 
@@ -16,6 +17,8 @@ __global__ void __launch_bounds__(512) detect_small_kernel(DetectArgs a, int th)
 // memory and runs the same tile code (whose results do not depend on the block size), so
 // every window's scores equal its own launch's.  One grid leaves no tail between windows.
 struct MultiArgs {
+    CUtensorMap tmap[kMaxWindowsPerLaunch];  // each window's halo box over the 4-band cube (when use_tma)
+    int use_tma;
     DetectArgs a[kMaxWindowsPerLaunch];
     int th[kMaxWindowsPerLaunch];
     int tiles_x[kMaxWindowsPerLaunch];
@@ -25,11 +28,16 @@ struct MultiArgs {
 };
 
 template <int D>
-__global__ void __launch_bounds__(512) detect_multi_kernel(MultiArgs m) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+__global__ void __launch_bounds__(512) detect_multi_kernel(const __grid_constant__ MultiArgs m) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ DetectArgs s_args;
     __shared__ int s_w;
+    __shared__ __align__(8) uint64_t s_bar;
     if (threadIdx.x == 0) {
+        if (m.use_tma) {
+            tc::mbar_init(&s_bar, 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
         int w = 0;
         while (w + 1 < m.n && (int)blockIdx.x >= m.first[w + 1]) ++w;
         s_w = w;
@@ -43,13 +51,13 @@ __global__ void __launch_bounds__(512) detect_multi_kernel(MultiArgs m) {
     const int w = s_w;
     const int t = (int)blockIdx.x - m.first[w];
     const int tx = m.tiles_x[w];
-    detect_tile<D>(s_args, m.th[w], t % tx, m.ty0[w] + t / tx, smem_raw);
+    detect_tile<D>(s_args, m.th[w], t % tx, m.ty0[w] + t / tx, smem_raw, m.use_tma ? &m.tmap[w] : nullptr, &s_bar);
 }
 
 // ---------------------------------------------------------------- census kernel
 __global__ void __launch_bounds__(512) census_kernel(int H, int W, int inner, int outer, int border, int th,
                                                      long long* __restrict__ out) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     census_tile(H, W, inner, outer, border, th, blockIdx.x, blockIdx.y, out, smem_raw);
 }
 
@@ -130,6 +138,40 @@ static cudaError_t launch_multi_d(const MultiArgs& m, size_t smem, int blocks, c
     return cudaGetLastError();
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (looked up once)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled() {
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// The halo box of a window over the 4-band cube x [H][W][4] as a 2-D float32 tensor (W * 4
+// elements per row, H rows): HR rows of XP pixels.  False (no tensor copies) when the driver
+// entry point or the encoding refuses, or the box does not fit the tensor-copy limits.
+static bool encode_halo_map(CUtensorMap* m, const float* x, int H, int W, int HR, int XP) {
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc || (reinterpret_cast<uintptr_t>(x) & 15) || XP * 4 > 256 || HR > 256 || HR < 1 || XP < 1) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)W * 4, (cuuint64_t)H};
+    const cuuint64_t strides[1] = {(cuuint64_t)W * 4 * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)XP * 4, (cuuint32_t)HR};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(x), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 cudaError_t launch_detect_small_multi(const DetectArgs* a, int n, cudaStream_t s) {
     return launch_detect_small_multi_rows(a, n, 0, a[0].H, s);
 }
@@ -162,6 +204,16 @@ cudaError_t launch_detect_small_multi_rows(const DetectArgs* a, int n, int row0,
     }
     m.first[n] = (int)blocks;
     if (blocks == 0) return cudaSuccess;
+    // interior tiles take their halo by tensor copies (4-band cubes)
+    m.use_tma = 0;
+    if (a[0].D == 4) {
+        bool ok = true;
+        for (int j = 0; j < n && ok; ++j) {
+            const int ro = m.a[j].outer / 2;
+            ok = encode_halo_map(&m.tmap[j], m.a[j].x, m.a[j].H, m.a[j].W, m.th[j] + 2 * ro, halo_pitch(TW + 2 * ro));
+        }
+        m.use_tma = ok ? 1 : 0;
+    }
     if (blocks > INT32_MAX) return cudaErrorInvalidValue;
     switch (a[0].D) {
         case 1: return launch_multi_d<1>(m, smem, (int)blocks, s);

@@ -34,7 +34,10 @@
 #pragma once
 #include <float.h>
 
+#include <cuda.h>
+
 #include "internal.h"
+#include "tc.cuh"
 
 namespace wdad {
 
@@ -183,6 +186,53 @@ __device__ __forceinline__ void store_shifted(float* dst, const float (&v)[D], c
 // every warp's first kHeld rows are fetched before the barrier that publishes the tile
 // reference, so their latency overlaps warp 0's reference sum; the rest after it.
 constexpr int kHeld = 2;
+// Halo of an interior tile (no reflected row or column) of the 4-band cube by one 2-D tensor
+// copy: thread 0 issues the box (HR rows of XP pixels, XP * 16 bytes each, the extra column past
+// WR unused) into xs through the tile's mbarrier; the tile reference (the middle row's mean,
+// summed in tile_reference's order, so the same value) and the shift (x - reference) then run
+// in shared memory.  Returns false if the copy did not land within the bounded wait (then xs
+// must not be used).
+constexpr uint32_t kHaloWait = 1u << 24;
+__device__ __forceinline__ bool load_halo_tma(const TileGeom& g, const CUtensorMap* tm, float* xs, float* cref,
+                                              uint64_t* bar) {
+    const uint32_t bytes = (uint32_t)(g.HR * g.XP * 16);
+    if (threadIdx.x == 0) {
+        tc::mbar_arrive_expect_tx(bar, bytes);
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+            ::"r"(tc::smem_u32(xs)), "l"(reinterpret_cast<uint64_t>(tm)), "r"((g.tx0 - g.ro) * 4), "r"(g.ty0 - g.ro),
+              "r"(tc::smem_u32(bar))
+            : "memory");
+    }
+    bool ok = tc::mbar_wait_bounded(bar, 0u, kHaloWait);
+    if (!ok) ok = tc::mbar_wait_bounded(bar, 0u, 16u * kHaloWait);  // a late copy must land before exit
+    if (__syncthreads_and(ok) == 0) return false;
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x < 32) {
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        const float* row = xs + (size_t)(g.HR / 2) * g.XP * 4;
+        for (int c = lane; c < g.WR; c += 32) {
+            const float4 v = *reinterpret_cast<const float4*>(row + c * 4);
+            acc[0] += v.x; acc[1] += v.y; acc[2] += v.z; acc[3] += v.w;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float t = acc[k];
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == 0) cref[k] = t / (float)g.WR;
+        }
+    }
+    __syncthreads();
+    const float4 c = make_float4(cref[0], cref[1], cref[2], cref[3]);
+    for (int q = threadIdx.x; q < g.HR * g.XP; q += blockDim.x) {
+        float4* p = reinterpret_cast<float4*>(xs) + q;
+        const float4 v = *p;
+        *p = make_float4(v.x - c.x, v.y - c.y, v.z - c.z, v.w - c.w);
+    }
+    return true;
+}
+
 template <int D>
 __device__ __forceinline__ void load_halo_spec(const TileGeom& g, const float* __restrict__ x, float* xs, float* cref) {
     using P = SpecPayload<D>;
@@ -632,8 +682,11 @@ __device__ __forceinline__ void jacobi_inplace(float (&A)[D][D], float (&V)[D][D
 // ---------------------------------------------------------------- detector tile
 // One output tile (tile_x, tile_y) of height th; any block size that is a multiple of 32
 // and at most 512 gives the same results (every reduction has a fixed order).
+// tm (nullable, D = 4): the cube's tensor map for this window's halo box; interior tiles then
+// take their halo by one tensor copy (load_halo_tma, mbarrier `bar`), the others as before.
 template <int D>
-__device__ void detect_tile(const DetectArgs& a, int th, int tile_x, int tile_y, unsigned char* smem_raw) {
+__device__ void detect_tile(const DetectArgs& a, int th, int tile_x, int tile_y, unsigned char* smem_raw,
+                            const CUtensorMap* tm = nullptr, uint64_t* bar = nullptr) {
     using P = SpecPayload<D>;
     constexpr int NC = P::NC;
     const TileGeom g(a.H, a.W, a.inner, a.outer, th, tile_x, tile_y);
@@ -642,7 +695,26 @@ __device__ void detect_tile(const DetectArgs& a, int th, int tile_x, int tile_y,
     float* Vo = reinterpret_cast<float*>(smem_raw + xs_bytes);
     float* Vi = Vo + NC * th * g.VP;
     float* cref = Vi + NC * th * g.VPI;  // [8]
-    load_halo_spec<D>(g, a.x, xs, cref);
+    bool interior = false;
+    if constexpr (D == 4) {
+        const int y0 = g.ty0 - g.ro, x0 = g.tx0 - g.ro;
+        interior = tm != nullptr && (tc::smem_u32(xs) & 127u) == 0 && y0 >= 0 && y0 + g.HR <= g.H && x0 >= 0 &&
+                   x0 + g.WR <= g.W;
+    }
+    if (interior) {
+        if (!load_halo_tma(g, tm, xs, cref, bar)) {  // the copy never landed: no scores from this tile
+            for (int pix = threadIdx.x; pix < th * TW; pix += blockDim.x) {
+                const int y = g.ty0 + pix / TW, xq = g.tx0 + pix % TW;
+                if (y >= a.H || xq >= a.W) continue;
+#pragma unroll
+                for (int t = 0; t < 3; ++t)
+                    if (a.out[t]) a.out[t][(size_t)y * a.W + xq] = __int_as_float(0x7fc00000);
+            }
+            return;
+        }
+    } else {
+        load_halo_spec<D>(g, a.x, xs, cref);
+    }
     __syncthreads();
     tile_sums<P>(g, xs, Vo, Vi);
 
