@@ -114,9 +114,10 @@ def _check_scene(wd, cube, win, loading=1e-3, dwest_mode=0, label="", taps=8):
     want, aux = oracle.detect(a, 2, win[0], win[1], dwest_mode=dwest_mode, want_aux=True)
     ok = dwest_ok_mask(aux)
     e = dwest_relerr(got[2], want, aux)
-    # (other filters leave more pixels with an eigenvalue near the selection cut-off)
-    # db4: 2.4-3.2% of the pixels are undetermined on the scenes of these tests
-    assert ok.mean() >= (0.95 if taps == 8 else 0.5), f"{label}: only {ok.mean():.3f} of DWEST pixels are well determined"
+    # db4: 2.4-3.2% of the pixels are undetermined on the scenes of these tests; other filters
+    # leave more pixels with an eigenvalue near the selection cut-off (2, 12, 20 taps at 3/11:
+    # 10%, 32%, 30%)
+    assert ok.mean() >= (0.95 if taps == 8 else 0.6), f"{label}: only {ok.mean():.3f} of DWEST pixels are well determined"
     assert e[ok].max() <= TOL_SCORE, f"{label} DWEST win {win}: max rel err {e[ok].max():.3g} ({(~ok).sum()} excluded)"
     return got
 
@@ -229,7 +230,7 @@ def test_widest_windows_match_oracle(wd):
         # (3721 pixels), a rounding about 30 times that of a 3 x 3 window's
         tol = 1e-3 if win[0] > 31 else TOL_SCORE
         e = dwest_relerr(got[2], want, aux)[ok]
-        assert ok.mean() >= 0.5 and e.max() <= tol, (win, e.max())
+        assert ok.mean() >= 0.95 and e.max() <= tol, (win, e.max())  # 0.99 of the pixels are determined
 
 
 def test_auc_matches_oracle_and_paper_direction(wd, scene48):

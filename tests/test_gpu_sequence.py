@@ -70,7 +70,9 @@ def test_sequence_against_oracle(wd):
                 assert (e <= tol).all(), (w, d, e.max(), tol[np.unravel_index(e.argmax(), e.shape)])
             want, aux = oracle.detect(a, 2, *win, want_aux=True)
             ok = dwest_ok_mask(aux)
-            assert ok.mean() >= 0.5  # undetermined: near-tau eigenvalues, close gaps, sign ties
+            # undetermined (near-tau eigenvalues, close gaps, sign ties): 6-23% of these
+            # 40 x 52 scenes, most of it eigenvalues near the cut-off at 3/9
+            assert ok.mean() >= 0.7
             assert dwest_relerr(got[w, 2], want, aux)[ok].max() <= TOL_SCORE
 
 
