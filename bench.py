@@ -692,7 +692,7 @@ def run_c3_table():
     """The precision workload at its own size: a 1024x1024x224 cube with band-to-band AR(1)
     noise (rho 0.98).  LRX and DWRX on every pixel, DWEST on a 128-row strip (its FP64 path takes
     minutes on the whole map), windows (3,11) and (7,21), loading 1e-3, gate 1e6.  The GPU FP64
-    path (held to 1e-6 of the oracle by the tests) is the judge: per detector and precision the
+    path (held to 1e-6 of the oracle by the tests) is the yardstick: per detector and precision the
     median and 99th-percentile relative error against it, the AUC change against it, the
     throughput and the FP64 re-solved fraction of MIXED.  Prints one JSON object."""
     import torch
@@ -704,7 +704,7 @@ def run_c3_table():
     xs = x[:strip_rows].contiguous()
     mask_s = sc.mask[:strip_rows]
     res = {"workload": "1024x1024x224 f32, AR(1) rho 0.98, 209 targets (1-3 px, f 0.1-0.5); LRX/DWRX whole map, "
-                       f"DWEST on rows 0..{strip_rows - 1}; judge: GPU FP64 path", "windows": {}}
+                       f"DWEST on rows 0..{strip_rows - 1}; errors against the GPU FP64 path", "windows": {}}
     for wi, wo in ((3, 11), (7, 21)):
         ent = {}
         for det, dn in enumerate(("lrx", "dwrx", "dwest")):
